@@ -1,0 +1,136 @@
+"""Seeded synthetic inputs shaped like the paper's workloads.
+
+This module only draws and renders data: stars, point-spread functions, sky, noise and
+masks.  It holds none of the fit or subtraction arithmetic and imports nothing else from
+the package, so both the CUDA path and the CPU oracle can take their inputs from it.
+
+The paper's images are OpenUniverse 2024 Roman simulations (Sec. "Statement of need"),
+which are not available here; these generators stand in for them, using the Roman frame
+size 4088 x 4088 (Sec. "GPU acceleration and performance") and cutouts no smaller than the
+1000 x 1000 px the paper still calls high quality (same section).
+
+Recipes (seed fixes everything, numpy PCG64):
+  * ``gaussian_pair``  -- 64 x 64 float64: template = 30 Gaussian stars (sigma 1.2 px,
+    lognormal flux mu=8, sigma=1, uniform positions) + sky 100 + N(0, 3) noise;
+    science = template cyclically convolved with a fixed 5 x 5 positive unit-sum kernel
+    + 2.5 + N(0, 3).
+  * ``roman_pair``     -- float32 frames with Moffat (beta=2.5) stars whose FWHM varies
+    linearly 1.8 -> 2.4 px along x in the template and along y in the science image,
+    Poisson(sky 80 e- + stars) with the known sky subtracted afterwards, and a union of two
+    Bernoulli(0.005) masks (byte 1 = masked).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+MOFFAT_BETA = 2.5
+
+
+def moffat_alpha(fwhm: float, beta: float = MOFFAT_BETA) -> float:
+    """Moffat core width alpha for a given FWHM: FWHM = 2 alpha sqrt(2^(1/beta) - 1)."""
+    return fwhm / (2.0 * np.sqrt(2.0 ** (1.0 / beta) - 1.0))
+
+
+def _render(ny, nx, xs, ys, flux, profile, radius):
+    """Sum unit-normalised stamps (pixel-centre sampling) into a cyclic ny x nx frame."""
+    img = np.zeros(ny * nx, dtype=np.float64)
+    off = np.arange(-radius, radius + 1)
+    oy, ox = np.meshgrid(off, off, indexing="ij")
+    batch = 256
+    for s in range(0, len(xs), batch):
+        x = xs[s:s + batch, None, None]
+        y = ys[s:s + batch, None, None]
+        cx = np.floor(x + 0.5).astype(np.int64)
+        cy = np.floor(y + 0.5).astype(np.int64)
+        px = cx + ox[None]
+        py = cy + oy[None]
+        r2x = (px - x) ** 2
+        r2y = (py - y) ** 2
+        prof = profile(r2x, r2y, s, s + batch)
+        prof /= prof.sum(axis=(1, 2), keepdims=True)
+        prof *= flux[s:s + batch, None, None]
+        flat = (np.mod(py, ny) * nx + np.mod(px, nx)).ravel()
+        np.add.at(img, flat, prof.ravel())
+    return img.reshape(ny, nx)
+
+
+def fixed_kernel5() -> np.ndarray:
+    """The fixed 5 x 5 positive, unit-sum kernel used to make the small science image."""
+    off = np.arange(-2, 3)
+    dy, dx = np.meshgrid(off, off, indexing="ij")
+    k = np.exp(-((dx - 0.3) ** 2 + (dy + 0.2) ** 2) / (2.0 * 0.9 ** 2))
+    return k / k.sum()
+
+
+def _cyclic_convolve(img, kern):
+    """out(u) = sum_d kern(d) img((u - d) mod N), d centred on the kernel's middle."""
+    h = kern.shape[0] // 2
+    out = np.zeros_like(img)
+    for dy in range(-h, h + 1):
+        for dx in range(-h, h + 1):
+            out += kern[dy + h, dx + h] * np.roll(img, shift=(dy, dx), axis=(0, 1))
+    return out
+
+
+def gaussian_pair(seed: int = 0, size: int = 64, n_stars: int = 30):
+    """Small float64 pair: returns (sci, tmpl, kernel5, background)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    xs = rng.uniform(0, size, n_stars)
+    ys = rng.uniform(0, size, n_stars)
+    flux = np.exp(rng.normal(8.0, 1.0, n_stars))
+    sig = 1.2
+
+    def gauss(r2x, r2y, a, b):
+        return np.exp(-(r2x + r2y) / (2 * sig * sig))
+
+    stars = _render(size, size, xs, ys, flux, gauss, radius=6)
+    tmpl = stars + 100.0 + rng.normal(0.0, 3.0, (size, size))
+    kern = fixed_kernel5()
+    bg = 2.5
+    sci = _cyclic_convolve(tmpl, kern) + bg + rng.normal(0.0, 3.0, (size, size))
+    return sci.astype(np.float64), tmpl.astype(np.float64), kern, bg
+
+
+def roman_pair(ny: int = 4088, nx: int = 4088, seed: int = 1000, n_stars: int | None = None,
+               fwhm=(1.8, 2.4), sky: float = 80.0, mask_frac: float = 0.005,
+               flux_mode: str = "lognormal", dtype=np.float32, radius: int = 12):
+    """Roman-like pair: returns (sci, tmpl, mask) with mask bytes 1 = masked.
+
+    ``n_stars`` defaults to 3000 per 4088^2 frame, scaled by area.  ``flux_mode`` is
+    "lognormal" (exp N(8, 1) e-) or "dynamic" (log-uniform over 1e2..1e7 e-, a 1e5 range).
+    """
+    rng = np.random.Generator(np.random.PCG64(seed))
+    if n_stars is None:
+        n_stars = max(1, int(round(3000 * ny * nx / 4088.0 ** 2)))
+    xs = rng.uniform(0, nx, n_stars)
+    ys = rng.uniform(0, ny, n_stars)
+    if flux_mode == "lognormal":
+        flux = np.exp(rng.normal(8.0, 1.0, n_stars))
+    elif flux_mode == "dynamic":
+        flux = 10.0 ** rng.uniform(2.0, 7.0, n_stars)
+    else:
+        raise ValueError(flux_mode)
+    f0, f1 = fwhm
+    ax_t = moffat_alpha(f0 + (f1 - f0) * xs / max(nx - 1, 1))  # template: varies along x
+    ax_s = moffat_alpha(f0 + (f1 - f0) * ys / max(ny - 1, 1))  # science: varies along y
+
+    def moffat(alpha):
+        def prof(r2x, r2y, a, b):
+            al = alpha[a:b, None, None]
+            return (1.0 + (r2x + r2y) / (al * al)) ** (-MOFFAT_BETA)
+        return prof
+
+    tmpl_model = _render(ny, nx, xs, ys, flux, moffat(ax_t), radius)
+    sci_model = _render(ny, nx, xs, ys, flux, moffat(ax_s), radius)
+    tmpl = rng.poisson(tmpl_model + sky).astype(np.float64) - sky
+    sci = rng.poisson(sci_model + sky).astype(np.float64) - sky
+    m1 = rng.random((ny, nx)) < mask_frac
+    m2 = rng.random((ny, nx)) < mask_frac
+    mask = (m1 | m2).astype(np.uint8)
+    return sci.astype(dtype), tmpl.astype(dtype), mask
+
+
+def cutout_sizes(n: int, seed: int, choices=(512, 1024, 1536, 2048)):
+    """Square cutout sizes drawn uniformly from ``choices``."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return [int(c) for c in rng.choice(np.asarray(choices), size=n)]
