@@ -1,0 +1,150 @@
+/*
+ * sfft.h -- C ABI of libsfft, a GB300 (sm_103a) implementation of the SFFT fit and
+ * subtraction: the difference-imaging step that fits a spatially varying delta-basis
+ * matching kernel plus a polynomial background to a science/template pair and subtracts
+ * the convolved template (the SFFT subtraction step, Sec. "Pipeline steps", step 6; the
+ * delta basis that follows a spatially varying PSF, Sec. "Statement of need"; the linear
+ * system it solves, Sec. "Future development").
+ *
+ * Problem statement (the paper gives no formulas, so this is the least-squares problem
+ * written out; the CPU oracle in oracle/ states the same thing):
+ *   frame Ny x Nx, row-major, pixel u = (y, x); xh = 2x/(Nx-1) - 1, yh = 2y/(Ny-1) - 1
+ *   (0 on an axis of length 1); monomials w_pq = xh^p yh^q, p+q <= D, ordered by total
+ *   degree, then q ascending; mask byte != 0 means "bad pixel" (m = 0), else m = 1;
+ *   X_m = m X; cyclic shifts X(u - d) taken modulo the frame.
+ *   Unknowns theta = [a_{pq,d}, p+q <= DK, d in [-h,h]^2 (h = (L-1)/2, row-major, dy
+ *   outer), pq-major blocks of L^2 lags;  b_rs, r+s <= DB]; n = L^2 nP(DK) + nP(DB),
+ *   nP(D) = (D+1)(D+2)/2.
+ *   Fit:      theta minimises || S_m - sum a_{pq,d} (w_pq T_m)(u - d) - sum b_rs m w_rs ||^2,
+ *             i.e. N theta = b with N, b the normal equations of that design.
+ *   Subtract: D(u) = S(u) - sum a_{pq,d} (w_pq T)(u - d) - sum b_rs w_rs(u)  on the
+ *             unmasked frames.
+ *
+ * Conventions for every call:
+ *   - Image, mask, coefficient and matrix pointers are caller-owned DEVICE memory on the
+ *     plan's device.  Images are row-major with a row pitch of `pitch` elements
+ *     (pitch >= nx; 0 means nx); their base pointers must be 16-byte aligned.  Masks are
+ *     one byte per pixel with the same pitch.
+ *   - The plan owns only its workspace.  All work is issued on the plan's stream and
+ *     is stream-ordered; a call returns once its work is queued unless it says it
+ *     synchronises.  A plan is not thread-safe; distinct plans on distinct streams are.
+ *   - Errors are returned as sfft_status; nothing aborts or traps.  Argument errors are
+ *     detected on the host before any work is queued.  Device-side failures (a
+ *     non-positive Cholesky pivot, a solver that does not converge) are recorded in a
+ *     device status word that sfft_fit reports when it is given an info struct (which
+ *     synchronises the stream) and that sfft_sync_status reads otherwise.
+ */
+#ifndef SFFT_H
+#define SFFT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* A cudaStream_t; NULL selects the legacy default stream. */
+typedef struct CUstream_st *sfft_stream_t;
+typedef struct sfft_plan_s *sfft_plan_t;
+
+typedef enum {
+    SFFT_OK = 0,
+    SFFT_ERR_INVALID_ARG = 1,   /* bad descriptor, pointer, size or alignment */
+    SFFT_ERR_CUDA = 2,          /* a CUDA runtime call failed; see sfft_last_error */
+    SFFT_ERR_OOM = 3,           /* workspace allocation failed or exceeds workspace_cap */
+    SFFT_ERR_NOT_SPD = 4,       /* normal matrix not positive definite (rank-deficient design) */
+    SFFT_ERR_NO_CONVERGENCE = 5,/* iterative solver hit max_iter (reported, then fell back) */
+    SFFT_ERR_TIMEOUT = 6,       /* a bounded device-side wait gave up */
+    SFFT_ERR_UNSUPPORTED = 7    /* valid request this build does not implement */
+} sfft_status;
+
+enum { SFFT_F32 = 0, SFFT_F64 = 1 };                              /* input element type */
+enum { SFFT_PREC_FP32 = 0, SFFT_PREC_SPLIT = 1, SFFT_PREC_FP64 = 2 }; /* arithmetic */
+enum { SFFT_SOLVE_CHOLESKY = 0, SFFT_SOLVE_PCG = 1 };
+
+typedef struct {
+    int32_t ny, nx;        /* frame size, ny, nx >= L */
+    int32_t pitch;         /* row pitch in elements (>= nx); 0 = nx */
+    int32_t L;             /* kernel size, odd, >= 1 */
+    int32_t dk;            /* kernel spatial polynomial degree, >= 0 */
+    int32_t db;            /* background polynomial degree, >= 0 */
+    int32_t dtype;         /* SFFT_F32 or SFFT_F64 (science, template and difference image) */
+    int32_t precision;     /* SFFT_PREC_FP32: FP32 products/FFTs/correlations, FP64 from the
+                              lag tables on; SFFT_PREC_FP64: FP64 throughout */
+    int32_t solver;        /* SFFT_SOLVE_CHOLESKY (FP64 Cholesky + one refinement step) */
+    int32_t max_iter;      /* PCG iteration cap (0 = default) */
+    double tol;            /* PCG relative-residual tolerance (0 = default 1e-12) */
+    size_t workspace_cap;  /* bytes the plan may allocate; 0 = no cap */
+    int32_t seg;           /* row-segment FFT length P (0 = default 256); P >= 2(L-1)+1 */
+    int32_t reserved[7];   /* zero */
+} sfft_desc;
+
+typedef struct {
+    int32_t status;        /* sfft_status of the solve */
+    int32_t n;             /* number of unknowns */
+    int32_t iterations;    /* solver iterations (refinement steps for Cholesky) */
+    int32_t fallback;      /* 1 when PCG fell back to Cholesky */
+    double rel_residual;   /* ||b - N theta||_2 / ||b||_2 after the last step */
+    double reserved[3];
+} sfft_fit_info;
+
+/* Create a plan for one frame geometry and basis.  Validates the descriptor, chooses the
+ * segment FFT length, allocates the workspace and uploads FP64-derived twiddle tables.
+ * Returns SFFT_ERR_INVALID_ARG (bad descriptor), SFFT_ERR_OOM (allocation or cap),
+ * SFFT_ERR_CUDA.  On error *plan is NULL. */
+sfft_status sfft_plan(sfft_plan_t *plan, const sfft_desc *desc, sfft_stream_t stream);
+
+/* Release the plan and its workspace (synchronises the plan's stream). NULL is a no-op. */
+void sfft_destroy(sfft_plan_t plan);
+
+/* Number of unknowns n = L^2 nP(dk) + nP(db). */
+sfft_status sfft_n_unknowns(sfft_plan_t plan, int32_t *n);
+
+/* Workspace bytes a plan for this descriptor allocates (host-only, no allocation). */
+sfft_status sfft_workspace_size(const sfft_desc *desc, size_t *bytes);
+
+/* Change the stream later calls are issued on. */
+sfft_status sfft_set_stream(sfft_plan_t plan, sfft_stream_t stream);
+
+/* Assemble the normal equations of the fit: N (n x n, row-major, FP64, full symmetric
+ * matrix) and b (n, FP64), both device pointers written by the call.  mask may be NULL
+ * (no bad pixels).  Order of unknowns as in the header comment. */
+sfft_status sfft_normal(sfft_plan_t plan, const void *sci, const void *tmpl, const uint8_t *mask,
+                        double *N, double *b);
+
+/* Fit: assemble N, b and solve N theta = b into coeffs (device, n doubles).  x0 (device,
+ * n doubles, nullable) is a warm start for SFFT_SOLVE_PCG and ignored by Cholesky.  When
+ * info (host) is non-NULL the call synchronises the stream and fills it; the return
+ * value then also carries the device-side status (e.g. SFFT_ERR_NOT_SPD). */
+sfft_status sfft_fit(sfft_plan_t plan, const void *sci, const void *tmpl, const uint8_t *mask,
+                     const double *x0, double *coeffs, sfft_fit_info *info);
+
+/* Difference image diff = S - (fitted kernel applied to the unmasked template) - background,
+ * using coeffs (device, n doubles).  diff has the plan's dtype and pitch; it may not alias
+ * sci or tmpl. */
+sfft_status sfft_subtract(sfft_plan_t plan, const void *sci, const void *tmpl, const double *coeffs,
+                          void *diff);
+
+/* Synchronise the plan's stream and return (and clear) the device status word. */
+sfft_status sfft_sync_status(sfft_plan_t plan);
+
+/* All S x T science/template pairs (the pairing of Sec. "Pipeline steps", step 1): pair
+ * (i, j) has index i*n_tmpl + j (science-major).  sci[i], tmpl[j], masks (nullable array,
+ * or per-pair NULL entries) are device pointers; every frame of pair (i, j) has size
+ * ny[i*n_tmpl+j] x nx[...] with pitch = nx.  base supplies L, dk, db, dtype, precision,
+ * solver.  coeffs[p] (n doubles) and diff[p] are device outputs; infos (host, nullable,
+ * S*T entries) forces a final synchronisation.  Pairs run on the given stream. */
+sfft_status sfft_batch(const sfft_desc *base, int32_t n_sci, int32_t n_tmpl, const void *const *sci,
+                       const void *const *tmpl, const uint8_t *const *masks, const int32_t *ny,
+                       const int32_t *nx, double *const *coeffs, void *const *diff,
+                       sfft_fit_info *infos, sfft_stream_t stream);
+
+const char *sfft_status_string(sfft_status s);
+/* Last error message recorded on this plan (or the process-wide one for plan == NULL). */
+const char *sfft_last_error(sfft_plan_t plan);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SFFT_H */

@@ -1,0 +1,395 @@
+// C ABI of libsfft: descriptor validation, plan geometry, workspace, twiddle tables and
+// the call sequences of sfft_normal / sfft_fit / sfft_subtract / sfft_batch.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <map>
+#include <new>
+#include <tuple>
+#include <vector>
+
+#include "sfft_internal.cuh"
+
+namespace {
+
+thread_local char g_last_error[512] = "";
+
+void set_err(sfft_plan_t p, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    snprintf(g_last_error, sizeof g_last_error, "%s", buf);
+    if (p) snprintf(p->err, sizeof p->err, "%s", buf);
+}
+
+sfft_status cuda_fail(sfft_plan_t p, cudaError_t e, const char *where) {
+    set_err(p, "%s: %s", where, cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? SFFT_ERR_OOM : SFFT_ERR_CUDA;
+}
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+}  // namespace
+
+namespace sfft {
+
+bool make_geometry(const sfft_desc &d, Geometry &g, char *err, size_t errlen) {
+    memset(&g, 0, sizeof g);
+    if (d.ny < 1 || d.nx < 1) return snprintf(err, errlen, "ny, nx must be >= 1"), false;
+    if (d.L < 1 || d.L % 2 == 0) return snprintf(err, errlen, "L must be odd and >= 1 (got %d)", d.L), false;
+    if (d.ny < d.L || d.nx < d.L) return snprintf(err, errlen, "frame %dx%d smaller than L=%d", d.ny, d.nx, d.L), false;
+    if (d.dk < 0 || d.db < 0) return snprintf(err, errlen, "dk, db must be >= 0"), false;
+    if (d.dtype != SFFT_F32 && d.dtype != SFFT_F64) return snprintf(err, errlen, "unknown dtype %d", d.dtype), false;
+    if (d.precision != SFFT_PREC_FP32 && d.precision != SFFT_PREC_SPLIT && d.precision != SFFT_PREC_FP64)
+        return snprintf(err, errlen, "unknown precision %d", d.precision), false;
+    if (d.solver != SFFT_SOLVE_CHOLESKY && d.solver != SFFT_SOLVE_PCG)
+        return snprintf(err, errlen, "unknown solver %d", d.solver), false;
+    g.pitch = d.pitch ? d.pitch : d.nx;
+    if (g.pitch < d.nx) return snprintf(err, errlen, "pitch %d < nx %d", g.pitch, d.nx), false;
+    g.ny = d.ny;
+    g.nx = d.nx;
+    g.L = d.L;
+    g.h = (d.L - 1) / 2;
+    g.dk = d.dk;
+    g.db = d.db;
+    g.nk = npoly(d.dk);
+    g.nb = npoly(d.db);
+    g.nker = g.nk * d.L * d.L;
+    g.n = g.nker + g.nb;
+    g.P = d.seg ? d.seg : 256;
+    if (g.P != 256) return snprintf(err, errlen, "segment FFT length %d not supported (256 only)", g.P), false;
+    g.G = d.L - 1;
+    g.U = g.P - 2 * g.G;
+    if (g.U < 1) return snprintf(err, errlen, "L=%d too large for segment length %d", d.L, g.P), false;
+    g.nseg = (d.nx + g.U - 1) / g.U;
+    g.nkf = g.P / 2 + 1;
+    g.nimg = 2 * g.nk + g.nb + 1;
+    g.nimg_pad = (g.nimg + 1) & ~1;
+    g.nfft = g.nimg_pad / 2;
+    if (g.nfft > 16) return snprintf(err, errlen, "dk=%d, db=%d give %d images per segment (max 32)", d.dk, d.db, g.nimg), false;
+    g.npair = g.nk * (g.nk + 1) / 2;
+    g.nent = g.npair * (2 * d.L - 1) + g.nk * (g.nb + 1) * d.L;
+    g.C = d.L;
+    if (g.C > 15) return snprintf(err, errlen, "L=%d > 15 not supported", d.L), false;
+    g.items_per_k = 2 * g.npair + g.nk * (g.nb + 1);
+    if (g.items_per_k > 256) return snprintf(err, errlen, "dk=%d, db=%d need %d work items per frequency (max 256)", d.dk, d.db, g.items_per_k), false;
+    g.ytile = 64;
+    {
+        const size_t cpx_sz = d.precision == SFFT_PREC_FP64 ? 16 : 8;
+        const size_t row_bytes = (size_t)(g.ytile + 2 * g.G) * g.nimg_pad * cpx_sz;
+        int kg = 256 / g.items_per_k;
+        int kg_smem = (int)((96 * 1024) / row_bytes);
+        if (kg > kg_smem) kg = kg_smem;
+        if (kg > g.nkf) kg = g.nkf;
+        if (kg < 1) kg = 1;
+        g.kg = kg;
+    }
+    if (d.db > 4) return snprintf(err, errlen, "db=%d > 4 not supported", d.db), false;
+    g.mom_rows = 128;
+    g.mom_ctas = ((d.nx + 255) / 256) * ((d.ny + g.mom_rows - 1) / g.mom_rows);
+    g.nmom = npoly(2 * d.db) + npoly(d.db);
+    if (d.precision == SFFT_PREC_SPLIT) return snprintf(err, errlen, "split precision not built yet"), false;
+    if (d.solver == SFFT_SOLVE_PCG) return snprintf(err, errlen, "PCG solver not built yet"), false;
+    return true;
+}
+
+struct Carve {
+    size_t off = 0;
+    template <class T>
+    T *take(void *base, size_t count) {
+        off = align_up(off, 256);
+        T *p = base ? reinterpret_cast<T *>(static_cast<char *>(base) + off) : nullptr;
+        off += sizeof(T) * count;
+        return p;
+    }
+};
+
+static size_t carve(const Geometry &g, int precision, void *base, Workspace *w) {
+    Carve c;
+    const size_t cpx_sz = precision == SFFT_PREC_FP64 ? 16 : 8;
+    Workspace tmp;
+    Workspace &o = w ? *w : tmp;
+    o.spec = c.take<char>(base, (size_t)g.nseg * g.nkf * g.ny * g.nimg_pad * cpx_sz);
+    o.ypart = c.take<double>(base, (size_t)g.nseg * g.nkf * g.nent * 2);
+    o.ysum = c.take<double>(base, (size_t)g.nkf * g.nent * 2);
+    o.lagww = c.take<double>(base, (size_t)g.npair * (2 * g.L - 1) * (2 * g.L - 1));
+    o.lagwg = c.take<double>(base, (size_t)g.nk * g.nb * g.L * g.L);
+    o.lagws = c.take<double>(base, (size_t)g.nk * g.L * g.L);
+    o.mom_part = c.take<double>(base, (size_t)g.mom_ctas * g.nmom);
+    o.mom = c.take<double>(base, (size_t)g.nmom);
+    o.N = c.take<double>(base, (size_t)g.n * g.n);
+    o.b = c.take<double>(base, (size_t)g.n);
+    o.R = c.take<double>(base, (size_t)g.n * g.n);
+    o.x = c.take<double>(base, (size_t)g.n);
+    o.r = c.take<double>(base, (size_t)g.n);
+    o.z = c.take<double>(base, (size_t)g.n);
+    o.p = c.take<double>(base, (size_t)g.n);
+    o.q = c.take<double>(base, (size_t)g.n);
+    o.scal = c.take<double>(base, 16);
+    o.status = c.take<int>(base, 16);
+    o.tw_fft = c.take<char>(base, (size_t)g.P * cpx_sz);
+    o.tw_x = c.take<double>(base, (size_t)g.nkf * (2 * g.G + 1) * 2);
+    return align_up(c.off, 256);
+}
+
+size_t workspace_bytes(const Geometry &g, int precision) { return carve(g, precision, nullptr, nullptr); }
+
+}  // namespace sfft
+
+using namespace sfft;
+
+extern "C" {
+
+const char *sfft_status_string(sfft_status s) {
+    switch (s) {
+        case SFFT_OK: return "ok";
+        case SFFT_ERR_INVALID_ARG: return "invalid argument";
+        case SFFT_ERR_CUDA: return "CUDA error";
+        case SFFT_ERR_OOM: return "out of memory";
+        case SFFT_ERR_NOT_SPD: return "normal matrix not positive definite";
+        case SFFT_ERR_NO_CONVERGENCE: return "solver did not converge";
+        case SFFT_ERR_TIMEOUT: return "device wait timed out";
+        case SFFT_ERR_UNSUPPORTED: return "unsupported";
+    }
+    return "unknown status";
+}
+
+const char *sfft_last_error(sfft_plan_t plan) { return plan ? plan->err : g_last_error; }
+
+sfft_status sfft_workspace_size(const sfft_desc *desc, size_t *bytes) {
+    if (!desc || !bytes) return set_err(nullptr, "null argument"), SFFT_ERR_INVALID_ARG;
+    Geometry g;
+    char err[256];
+    if (!make_geometry(*desc, g, err, sizeof err)) return set_err(nullptr, "%s", err), SFFT_ERR_INVALID_ARG;
+    *bytes = workspace_bytes(g, desc->precision);
+    return SFFT_OK;
+}
+
+sfft_status sfft_plan(sfft_plan_t *plan, const sfft_desc *desc, sfft_stream_t stream) {
+    if (!plan) return set_err(nullptr, "null plan pointer"), SFFT_ERR_INVALID_ARG;
+    *plan = nullptr;
+    if (!desc) return set_err(nullptr, "null descriptor"), SFFT_ERR_INVALID_ARG;
+    Geometry g;
+    char err[256];
+    if (!make_geometry(*desc, g, err, sizeof err)) {
+        bool unsup = strstr(err, "not supported") || strstr(err, "not built");
+        set_err(nullptr, "%s", err);
+        return unsup ? SFFT_ERR_UNSUPPORTED : SFFT_ERR_INVALID_ARG;
+    }
+    size_t bytes = workspace_bytes(g, desc->precision);
+    if (desc->workspace_cap && bytes > desc->workspace_cap) {
+        set_err(nullptr, "workspace %zu bytes exceeds cap %zu", bytes, desc->workspace_cap);
+        return SFFT_ERR_OOM;
+    }
+    sfft_plan_t p = new (std::nothrow) sfft_plan_s();
+    if (!p) return set_err(nullptr, "host allocation failed"), SFFT_ERR_OOM;
+    p->desc = *desc;
+    p->g = g;
+    p->stream = reinterpret_cast<cudaStream_t>(stream);
+    p->err[0] = 0;
+    cudaError_t e = cudaGetDevice(&p->device);
+    if (e != cudaSuccess) {
+        sfft_status s = cuda_fail(nullptr, e, "cudaGetDevice");
+        delete p;
+        return s;
+    }
+    e = cudaMalloc(&p->ws.base, bytes);
+    if (e != cudaSuccess) {
+        sfft_status s = cuda_fail(nullptr, e, "workspace allocation");
+        delete p;
+        return s;
+    }
+    p->ws.bytes = bytes;
+    carve(g, desc->precision, p->ws.base, &p->ws);
+
+    // twiddles from FP64 trigonometry: forward FFT exp(-2 pi i m / P), and the x-direction
+    // inverse-DFT weights w_k exp(+2 pi i k m / P) / P for m in [0, 2G], w_0 = w_{P/2} = 1, else 2
+    const double two_pi = 6.283185307179586476925286766559;
+    std::vector<double> twx((size_t)g.nkf * (2 * g.G + 1) * 2);
+    for (int k = 0; k < g.nkf; k++) {
+        double wk = (k == 0 || 2 * k == g.P) ? 1.0 : 2.0;
+        for (int m = 0; m <= 2 * g.G; m++) {
+            long km = ((long)k * m) % g.P;
+            double ang = two_pi * (double)km / g.P;
+            twx[((size_t)k * (2 * g.G + 1) + m) * 2] = wk * cos(ang) / g.P;
+            twx[((size_t)k * (2 * g.G + 1) + m) * 2 + 1] = wk * sin(ang) / g.P;
+        }
+    }
+    e = cudaMemcpyAsync(p->ws.tw_x, twx.data(), twx.size() * sizeof(double), cudaMemcpyHostToDevice, p->stream);
+    if (e == cudaSuccess) {
+        if (desc->precision == SFFT_PREC_FP64) {
+            std::vector<double> tw((size_t)g.P * 2);
+            for (int m = 0; m < g.P; m++) {
+                tw[2 * m] = cos(two_pi * m / g.P);
+                tw[2 * m + 1] = -sin(two_pi * m / g.P);
+            }
+            e = cudaMemcpyAsync(p->ws.tw_fft, tw.data(), tw.size() * sizeof(double), cudaMemcpyHostToDevice, p->stream);
+        } else {
+            std::vector<float> tw((size_t)g.P * 2);
+            for (int m = 0; m < g.P; m++) {
+                tw[2 * m] = (float)cos(two_pi * m / g.P);
+                tw[2 * m + 1] = (float)-sin(two_pi * m / g.P);
+            }
+            e = cudaMemcpyAsync(p->ws.tw_fft, tw.data(), tw.size() * sizeof(float), cudaMemcpyHostToDevice, p->stream);
+        }
+    }
+    if (e == cudaSuccess) e = cudaMemsetAsync(p->ws.status, 0, 16 * sizeof(int), p->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);  // host staging vectors die here
+    if (e != cudaSuccess) {
+        sfft_status s = cuda_fail(nullptr, e, "plan set-up");
+        cudaFree(p->ws.base);
+        delete p;
+        return s;
+    }
+    *plan = p;
+    return SFFT_OK;
+}
+
+void sfft_destroy(sfft_plan_t plan) {
+    if (!plan) return;
+    cudaStreamSynchronize(plan->stream);
+    cudaFree(plan->ws.base);
+    delete plan;
+}
+
+sfft_status sfft_n_unknowns(sfft_plan_t plan, int32_t *n) {
+    if (!plan || !n) return set_err(plan, "null argument"), SFFT_ERR_INVALID_ARG;
+    *n = plan->g.n;
+    return SFFT_OK;
+}
+
+sfft_status sfft_set_stream(sfft_plan_t plan, sfft_stream_t stream) {
+    if (!plan) return set_err(nullptr, "null plan"), SFFT_ERR_INVALID_ARG;
+    plan->stream = reinterpret_cast<cudaStream_t>(stream);
+    return SFFT_OK;
+}
+
+static bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+static sfft_status check_images(sfft_plan_t plan, const void *sci, const void *tmpl) {
+    if (!plan) return set_err(nullptr, "null plan"), SFFT_ERR_INVALID_ARG;
+    if (!sci || !tmpl) return set_err(plan, "null image pointer"), SFFT_ERR_INVALID_ARG;
+    if (!aligned16(sci) || !aligned16(tmpl)) return set_err(plan, "image pointers must be 16-byte aligned"), SFFT_ERR_INVALID_ARG;
+    return SFFT_OK;
+}
+
+// queue the assembly of N, b into the given device arrays
+static sfft_status queue_normal(sfft_plan_t p, const void *sci, const void *tmpl, const uint8_t *mask, double *N,
+                                double *b) {
+    const Geometry &g = p->g;
+    Workspace &w = p->ws;
+    cudaStream_t st = p->stream;
+    cudaError_t e;
+    if ((e = launch_segment_fft(g, p->desc.dtype, p->desc.precision, sci, tmpl, mask, w.tw_fft, w.spec, st)) != cudaSuccess)
+        return cuda_fail(p, e, "segment FFT launch");
+    if ((e = launch_moments(g, p->desc.dtype, p->desc.precision, sci, mask, w.mom_part, st)) != cudaSuccess)
+        return cuda_fail(p, e, "moments launch");
+    if ((e = launch_ycorr(g, p->desc.precision, w.spec, w.ypart, st)) != cudaSuccess)
+        return cuda_fail(p, e, "y-correlation launch");
+    if ((e = launch_lag_tables(g, w.ypart, w.ysum, w.tw_x, w.lagww, w.lagwg, w.lagws, w.mom_part, w.mom, st)) != cudaSuccess)
+        return cuda_fail(p, e, "lag-table launch");
+    if ((e = launch_assemble(g, w.lagww, w.lagwg, w.lagws, w.mom, N, b, st)) != cudaSuccess)
+        return cuda_fail(p, e, "assembly launch");
+    return SFFT_OK;
+}
+
+sfft_status sfft_normal(sfft_plan_t plan, const void *sci, const void *tmpl, const uint8_t *mask, double *N,
+                        double *b) {
+    sfft_status s = check_images(plan, sci, tmpl);
+    if (s != SFFT_OK) return s;
+    if (!N || !b) return set_err(plan, "null output pointer"), SFFT_ERR_INVALID_ARG;
+    return queue_normal(plan, sci, tmpl, mask, N, b);
+}
+
+static sfft_status read_status(sfft_plan_t p, sfft_fit_info *info) {
+    int st_h = 0;
+    double scal[2] = {0.0, 0.0};
+    cudaError_t e = cudaMemcpyAsync(&st_h, p->ws.status, sizeof(int), cudaMemcpyDeviceToHost, p->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(scal, p->ws.scal, 2 * sizeof(double), cudaMemcpyDeviceToHost, p->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+    if (e != cudaSuccess) return cuda_fail(p, e, "status read-back");
+    if (info) {
+        memset(info, 0, sizeof *info);
+        info->status = st_h;
+        info->n = p->g.n;
+        info->iterations = 1;
+        info->rel_residual = scal[1] > 0 ? sqrt(scal[0] / scal[1]) : 0.0;
+    }
+    if (st_h != 0) {
+        set_err(p, "device status: %s", sfft_status_string((sfft_status)st_h));
+        cudaMemsetAsync(p->ws.status, 0, sizeof(int), p->stream);
+    }
+    return (sfft_status)st_h;
+}
+
+sfft_status sfft_fit(sfft_plan_t plan, const void *sci, const void *tmpl, const uint8_t *mask, const double *x0,
+                     double *coeffs, sfft_fit_info *info) {
+    (void)x0;
+    sfft_status s = check_images(plan, sci, tmpl);
+    if (s != SFFT_OK) return s;
+    if (!coeffs) return set_err(plan, "null coeffs"), SFFT_ERR_INVALID_ARG;
+    Workspace &w = plan->ws;
+    cudaError_t e = cudaMemsetAsync(w.status, 0, sizeof(int), plan->stream);
+    if (e != cudaSuccess) return cuda_fail(plan, e, "status reset");
+    s = queue_normal(plan, sci, tmpl, mask, w.N, w.b);
+    if (s != SFFT_OK) return s;
+    e = launch_cholesky_solve(plan->g, w.N, w.b, w.R, coeffs, w.r, w.z, w.scal, w.status, plan->stream);
+    if (e != cudaSuccess) return cuda_fail(plan, e, "solver launch");
+    if (info) return read_status(plan, info);
+    return SFFT_OK;
+}
+
+sfft_status sfft_subtract(sfft_plan_t plan, const void *sci, const void *tmpl, const double *coeffs, void *diff) {
+    sfft_status s = check_images(plan, sci, tmpl);
+    if (s != SFFT_OK) return s;
+    if (!coeffs || !diff) return set_err(plan, "null coeffs or diff"), SFFT_ERR_INVALID_ARG;
+    if (diff == sci || diff == tmpl) return set_err(plan, "diff may not alias the inputs"), SFFT_ERR_INVALID_ARG;
+    cudaError_t e = launch_subtract(plan->g, plan->desc.dtype, plan->desc.precision, sci, tmpl, coeffs, diff, plan->stream);
+    if (e != cudaSuccess) return cuda_fail(plan, e, "subtract launch");
+    return SFFT_OK;
+}
+
+sfft_status sfft_sync_status(sfft_plan_t plan) {
+    if (!plan) return set_err(nullptr, "null plan"), SFFT_ERR_INVALID_ARG;
+    return read_status(plan, nullptr);
+}
+
+sfft_status sfft_batch(const sfft_desc *base, int32_t n_sci, int32_t n_tmpl, const void *const *sci,
+                       const void *const *tmpl, const uint8_t *const *masks, const int32_t *ny, const int32_t *nx,
+                       double *const *coeffs, void *const *diff, sfft_fit_info *infos, sfft_stream_t stream) {
+    if (!base || n_sci < 0 || n_tmpl < 0 || !sci || !tmpl || !ny || !nx || !coeffs || !diff)
+        return set_err(nullptr, "null or negative batch argument"), SFFT_ERR_INVALID_ARG;
+    const int npairs = n_sci * n_tmpl;
+    // one plan per distinct frame size, reused across pairs
+    std::map<std::pair<int, int>, sfft_plan_t> plans;
+    sfft_status result = SFFT_OK;
+    for (int pi = 0; pi < npairs && result == SFFT_OK; pi++) {
+        auto key = std::make_pair(ny[pi], nx[pi]);
+        if (!plans.count(key)) {
+            sfft_desc d = *base;
+            d.ny = ny[pi];
+            d.nx = nx[pi];
+            d.pitch = 0;
+            sfft_plan_t p = nullptr;
+            result = sfft_plan(&p, &d, stream);
+            if (result != SFFT_OK) break;
+            plans[key] = p;
+        }
+    }
+    for (int pi = 0; pi < npairs && result == SFFT_OK; pi++) {
+        sfft_plan_t p = plans[std::make_pair(ny[pi], nx[pi])];
+        int i = pi / (n_tmpl ? n_tmpl : 1), j = pi % (n_tmpl ? n_tmpl : 1);
+        const uint8_t *m = masks ? masks[pi] : nullptr;
+        result = sfft_fit(p, sci[i], tmpl[j], m, nullptr, coeffs[pi], infos ? &infos[pi] : nullptr);
+        if (result == SFFT_ERR_NOT_SPD && infos) result = SFFT_OK;  // reported per pair
+        if (result == SFFT_OK) result = sfft_subtract(p, sci[i], tmpl[j], coeffs[pi], diff[pi]);
+    }
+    for (auto &kv : plans) sfft_destroy(kv.second);
+    return result;
+}
+
+}  // extern "C"

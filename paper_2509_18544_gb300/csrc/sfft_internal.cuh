@@ -1,0 +1,123 @@
+// Internal declarations of libsfft: complex arithmetic, the plan object and the kernel
+// launchers.  Every launcher queues work on the given stream and returns the launch status.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "sfft.h"
+
+namespace sfft {
+
+// ------------------------------------------------------------------ complex arithmetic
+template <class R>
+struct alignas(2 * sizeof(R)) cpx {
+    R re, im;
+};
+
+template <class R>
+__host__ __device__ __forceinline__ cpx<R> operator+(cpx<R> a, cpx<R> b) { return {a.re + b.re, a.im + b.im}; }
+template <class R>
+__host__ __device__ __forceinline__ cpx<R> operator-(cpx<R> a, cpx<R> b) { return {a.re - b.re, a.im - b.im}; }
+template <class R>
+__host__ __device__ __forceinline__ cpx<R> cmul(cpx<R> a, cpx<R> b) {
+    return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
+}
+
+// number of monomials of total degree <= d
+__host__ __device__ __forceinline__ int npoly(int d) { return d < 0 ? 0 : (d + 1) * (d + 2) / 2; }
+
+// exponents of monomial idx: total degree first, then q ascending
+__host__ __device__ __forceinline__ void mono_pq(int idx, int &p, int &q) {
+    int d = 0;
+    while (idx > d) {
+        idx -= d + 1;
+        d++;
+    }
+    q = idx;
+    p = d - idx;
+}
+
+// ------------------------------------------------------------------ geometry of a plan
+// The lag correlations are computed per row segment: segment s owns the columns
+// [s*U, s*U + U) of every row ("A" side, zero-padded to P) and reads the cyclic window
+// [s*U - G, s*U - G + P) ("B" side); G = L - 1 is the largest |lag|, U = P - 2G.
+struct Geometry {
+    int ny, nx, pitch, L, h, dk, db;
+    int nk, nb, nker, n;       // monomials of kernel / background, unknowns
+    int P, U, G, nseg, nkf;    // segment FFT length, useful length, halo, segments, half-spectrum bins
+    int nimg, nimg_pad, nfft;  // real images per segment row (A then B), padded to even, complex FFTs
+    int npair, nent;           // W-W pairs (i <= j), (pair, dy) entries per frequency
+    int C, items_per_k, kg;    // y-correlation: dy chunk, work items per frequency, frequencies per CTA
+    int ytile;                 // y-correlation rows per staged tile
+    int mom_rows, mom_ctas;    // background-moment reduction geometry
+    int nmom;                  // moments: npoly(2 db) mask moments + npoly(db) science moments
+};
+
+bool make_geometry(const sfft_desc &d, Geometry &g, char *err, size_t errlen);
+
+// ------------------------------------------------------------------ plan
+struct Workspace {
+    void *base = nullptr;
+    size_t bytes = 0;
+    void *spec = nullptr;        // [nseg][nkf][ny][nimg_pad] complex (R)
+    double *ypart = nullptr;     // [nseg][nkf][nent] complex FP64 (re, im interleaved)
+    double *ysum = nullptr;      // [nkf][nent] complex FP64
+    double *lagww = nullptr;     // [npair][2L-1][2L-1]
+    double *lagwg = nullptr;     // [nk][nb][L][L]
+    double *lagws = nullptr;     // [nk][L][L]
+    double *mom_part = nullptr;  // [mom_ctas][nmom]
+    double *mom = nullptr;       // [nmom]
+    double *N = nullptr;         // [n][n]
+    double *b = nullptr;         // [n]
+    double *R = nullptr;         // [n][n] Cholesky factor (lower triangle used)
+    double *x = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr;  // [n] solver vectors
+    double *scal = nullptr;      // [16] solver scalars
+    int *status = nullptr;       // device status word(s)
+    void *tw_fft = nullptr;      // [P] complex (R): exp(-2 pi i m / P)
+    double *tw_x = nullptr;      // [nkf][2G+1] complex FP64: w_k exp(+2 pi i k m / P) / P
+};
+
+size_t workspace_bytes(const Geometry &g, int precision);
+
+}  // namespace sfft
+
+struct sfft_plan_s {
+    sfft_desc desc;
+    sfft::Geometry g;
+    sfft::Workspace ws;
+    cudaStream_t stream;
+    int device;
+    char err[512];
+};
+
+namespace sfft {
+
+// ------------------------------------------------------------------ launchers
+// K1: products + row-segment real FFTs -> spec
+cudaError_t launch_segment_fft(const Geometry &g, int dtype, int precision, const void *sci,
+                               const void *tmpl, const uint8_t *mask, const void *tw_fft, void *spec,
+                               cudaStream_t st);
+// background moments (mask and masked science times monomials) -> mom_part
+cudaError_t launch_moments(const Geometry &g, int dtype, int precision, const void *sci,
+                           const uint8_t *mask, double *mom_part, cudaStream_t st);
+// K2: y-direction correlations at the kernel lags, per segment and frequency -> ypart
+cudaError_t launch_ycorr(const Geometry &g, int precision, const void *spec, double *ypart,
+                         cudaStream_t st);
+// K3: segment sum + x-direction inverse DFT at the kernel lags -> lag tables
+cudaError_t launch_lag_tables(const Geometry &g, const double *ypart, double *ysum, const double *tw_x,
+                              double *lagww, double *lagwg, double *lagws, const double *mom_part,
+                              double *mom, cudaStream_t st);
+// K4: normal-matrix and right-hand-side assembly from the lag tables and moments
+cudaError_t launch_assemble(const Geometry &g, const double *lagww, const double *lagwg,
+                            const double *lagws, const double *mom, double *N, double *b,
+                            cudaStream_t st);
+// solve N x = b (FP64 Cholesky + one refinement step); writes status on failure
+cudaError_t launch_cholesky_solve(const Geometry &g, const double *N, const double *b, double *R,
+                                  double *x, double *r, double *z, double *scal, int *status,
+                                  cudaStream_t st);
+// difference image
+cudaError_t launch_subtract(const Geometry &g, int dtype, int precision, const void *sci,
+                            const void *tmpl, const double *coeffs, void *diff, cudaStream_t st);
+
+}  // namespace sfft

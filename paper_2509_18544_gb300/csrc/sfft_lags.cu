@@ -1,0 +1,272 @@
+// K3 / K4: lag tables and normal-equation assembly (FP64).
+//
+//   ysum[k][e]        = sum_s ypart[s][k][e]                         (segments)
+//   C(e, dx)          = sum_k Re(ysum[k][e] * tw_x[k][G + dx])       (x-direction inverse DFT
+//                       restricted to the kernel lags, tw_x = w_k e^{2 pi i k m / P} / P)
+//   background block  = mask moments  sum_u m xh^a yh^b  (a + b <= 2 DB)
+//   background rhs    = science moments sum_u m S xh^a yh^b (a + b <= DB)
+// and the assembly of the normal equations of the delta-basis least-squares fit:
+//   N[(i,d),(j,d')] = C_{W_i,W_j}(d - d'),  N[(i,d), r] = C_{W_i,Psi_r}(d),
+//   N[r, r'] = <Psi_r, Psi_r'>,  b[(i,d)] = C_{W_i,S_m}(d),  b[r] = <Psi_r, S_m>.
+#include "sfft_internal.cuh"
+
+namespace sfft {
+namespace {
+
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = a + b;
+    float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+template <class R>
+__device__ __forceinline__ R coordv(int i, int n) {
+    return n > 1 ? (R)(2 * i - (n - 1)) / (R)(n - 1) : (R)0;
+}
+
+constexpr int kMaxDB = 4;
+
+// Column sums over a band of rows, folded into FP64 products with x powers, reduced per CTA.
+template <class R, class In>
+__global__ void __launch_bounds__(256) k_moments(const In *__restrict__ sci, const uint8_t *__restrict__ mask,
+                                                Geometry g, double *__restrict__ part) {
+    __shared__ double red[8][64];
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int ya = blockIdx.y * g.mom_rows, yb = min(g.ny, ya + g.mom_rows);
+    const int db2 = 2 * g.db;
+    // hi/lo column sums: cm[b] = sum m yh^b (b <= 2 db), cs[b] = sum m S yh^b (b <= db)
+    R cmh[2 * kMaxDB + 1], cml[2 * kMaxDB + 1], csh[kMaxDB + 1], csl[kMaxDB + 1];
+    R cma[2 * kMaxDB + 1], csa[kMaxDB + 1];
+#pragma unroll
+    for (int b = 0; b <= 2 * kMaxDB; b++) cmh[b] = cml[b] = cma[b] = (R)0;
+#pragma unroll
+    for (int b = 0; b <= kMaxDB; b++) csh[b] = csl[b] = csa[b] = (R)0;
+    if (x < g.nx) {
+        int cnt = 0;
+        for (int y = ya; y < yb; y++) {
+            size_t u = (size_t)y * g.pitch + x;
+            R m = (mask && mask[u]) ? (R)0 : (R)1;
+            R sm = m * (R)sci[u];
+            R yh = coordv<R>(y, g.ny), w = (R)1;
+#pragma unroll
+            for (int b = 0; b <= 2 * kMaxDB; b++) {
+                if (b <= db2) cma[b] += m * w;
+                if (b <= g.db) csa[b] += sm * w;
+                w *= yh;
+            }
+            if (++cnt == 16 || y == yb - 1) {
+                cnt = 0;
+#pragma unroll
+                for (int b = 0; b <= 2 * kMaxDB; b++) {
+                    if constexpr (sizeof(R) == 4) {
+                        float s, e;
+                        two_sum(cmh[b], cma[b], s, e);
+                        cmh[b] = s;
+                        cml[b] += e;
+                    } else {
+                        cmh[b] += cma[b];
+                    }
+                    cma[b] = (R)0;
+                }
+#pragma unroll
+                for (int b = 0; b <= kMaxDB; b++) {
+                    if constexpr (sizeof(R) == 4) {
+                        float s, e;
+                        two_sum(csh[b], csa[b], s, e);
+                        csh[b] = s;
+                        csl[b] += e;
+                    } else {
+                        csh[b] += csa[b];
+                    }
+                    csa[b] = (R)0;
+                }
+            }
+        }
+    }
+    const double xh = x < g.nx ? coordv<double>(x, g.nx) : 0.0;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nmask = npoly(db2);
+    for (int j = 0; j < g.nmom; j++) {
+        int a, b;
+        double v = 0.0;
+        if (x < g.nx) {
+            if (j < nmask) {
+                mono_pq(j, a, b);
+                double cs = 0.0;
+#pragma unroll
+                for (int bb = 0; bb <= 2 * kMaxDB; bb++)
+                    if (bb == b) cs = (double)cmh[bb] + (double)cml[bb];
+                double xa = 1.0;
+                for (int e = 0; e < a; e++) xa *= xh;
+                v = xa * cs;
+            } else {
+                mono_pq(j - nmask, a, b);
+                double cs = 0.0;
+#pragma unroll
+                for (int bb = 0; bb <= kMaxDB; bb++)
+                    if (bb == b) cs = (double)csh[bb] + (double)csl[bb];
+                double xa = 1.0;
+                for (int e = 0; e < a; e++) xa *= xh;
+                v = xa * cs;
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) red[warp][j & 63] = v;
+        if ((j & 63) == 63 || j == g.nmom - 1) {
+            __syncthreads();
+            int jbase = j & ~63;
+            for (int jj = threadIdx.x; jj <= (j & 63); jj += blockDim.x) {
+                double s = 0.0;
+                for (int w = 0; w < (int)(blockDim.x >> 5); w++) s += red[w][jj];
+                part[((size_t)blockIdx.y * gridDim.x + blockIdx.x) * g.nmom + jbase + jj] = s;
+            }
+            __syncthreads();
+        }
+    }
+}
+
+__global__ void k_mom_reduce(const double *__restrict__ part, int nparts, int nmom, double *__restrict__ mom) {
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= nmom) return;
+    double s = 0.0, c = 0.0;  // Neumaier
+    for (int p = 0; p < nparts; p++) {
+        double v = part[(size_t)p * nmom + j];
+        double t = s + v;
+        c += fabs(s) >= fabs(v) ? (s - t) + v : (v - t) + s;
+        s = t;
+    }
+    mom[j] = s + c;
+}
+
+__global__ void k_ysum(const double2 *__restrict__ ypart, Geometry g, double2 *__restrict__ ysum) {
+    size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    size_t total = (size_t)g.nkf * g.nent;
+    if (idx >= total) return;
+    double2 s = make_double2(0.0, 0.0);
+    for (int sg = 0; sg < g.nseg; sg++) {
+        double2 v = ypart[(size_t)sg * total + idx];
+        s.x += v.x;
+        s.y += v.y;
+    }
+    ysum[idx] = s;
+}
+
+__global__ void k_lagx(const double2 *__restrict__ ysum, const double2 *__restrict__ tw_x, Geometry g,
+                       double *__restrict__ lagww, double *__restrict__ lagwg, double *__restrict__ lagws) {
+    const int L = g.L, h = g.h, Lw = 2 * L - 1, G = g.G;
+    const int nww = g.npair * Lw * Lw;
+    const int nrest = g.nk * (g.nb + 1) * L * L;
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nww + nrest) return;
+    int ent, dx;
+    double *out;
+    if (t < nww) {
+        ent = t / Lw;  // = pr * Lw + dyi
+        int dxi = t - ent * Lw;
+        dx = dxi - (L - 1);
+        out = lagww + t;  // [pr][dyi][dxi]
+    } else {
+        int u = t - nww;
+        int e2 = u / L, dxi = u - e2 * L;  // e2 = qd * L + dyi
+        ent = g.npair * Lw + e2;
+        dx = dxi - h;
+        int qd = e2 / L, dyi = e2 - qd * L;
+        int i = qd / (g.nb + 1), r = qd - i * (g.nb + 1);
+        if (r < g.nb)
+            out = lagwg + (((size_t)i * g.nb + r) * L + dyi) * L + dxi;
+        else
+            out = lagws + ((size_t)i * L + dyi) * L + dxi;
+    }
+    const int m = G + dx;
+    const int W = 2 * G + 1;
+    double acc = 0.0;
+    for (int k = 0; k < g.nkf; k++) {
+        double2 y = ysum[(size_t)k * g.nent + ent];
+        double2 w = tw_x[(size_t)k * W + m];
+        acc = fma(y.x, w.x, acc);
+        acc = fma(-y.y, w.y, acc);
+    }
+    *out = acc;
+}
+
+__global__ void k_assemble(const double *__restrict__ lagww, const double *__restrict__ lagwg,
+                           const double *__restrict__ lagws, const double *__restrict__ mom, Geometry g,
+                           double *__restrict__ N, double *__restrict__ b) {
+    const int n = g.n, L = g.L, h = g.h, Lw = 2 * L - 1, ns = L * L, nker = g.nker, nk = g.nk;
+    size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    size_t total = (size_t)n * n;
+    if (idx < total) {
+        int row = (int)(idx / n), col = (int)(idx - (size_t)row * n);
+        double v;
+        if (row < nker && col < nker) {
+            int i = row / ns, l = row - i * ns, j = col / ns, l2 = col - j * ns;
+            int dy = l / L - h, dx = l % L - h, dy2 = l2 / L - h, dx2 = l2 % L - h;
+            if (i <= j) {
+                int pr = i * nk - i * (i - 1) / 2 + (j - i);
+                v = lagww[((size_t)pr * Lw + (dy - dy2 + L - 1)) * Lw + (dx - dx2 + L - 1)];
+            } else {
+                int pr = j * nk - j * (j - 1) / 2 + (i - j);
+                v = lagww[((size_t)pr * Lw + (dy2 - dy + L - 1)) * Lw + (dx2 - dx + L - 1)];
+            }
+        } else if (row < nker) {
+            int i = row / ns, l = row - i * ns, r = col - nker;
+            v = lagwg[((size_t)i * g.nb + r) * ns + l];
+        } else if (col < nker) {
+            int j = col / ns, l2 = col - j * ns, r = row - nker;
+            v = lagwg[((size_t)j * g.nb + r) * ns + l2];
+        } else {
+            int r = row - nker, r2 = col - nker, p1, q1, p2, q2;
+            mono_pq(r, p1, q1);
+            mono_pq(r2, p2, q2);
+            int q = q1 + q2, d = p1 + p2 + q;
+            v = mom[d * (d + 1) / 2 + q];
+        }
+        N[idx] = v;
+    }
+    if (idx < (size_t)n) {
+        int row = (int)idx;
+        b[row] = row < nker ? lagws[row] : mom[npoly(2 * g.db) + (row - nker)];
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_moments(const Geometry &g, int dtype, int precision, const void *sci, const uint8_t *mask,
+                           double *mom_part, cudaStream_t st) {
+    if (g.db > kMaxDB) return cudaErrorInvalidValue;
+    dim3 grid((g.nx + 255) / 256, (g.ny + g.mom_rows - 1) / g.mom_rows);
+    if (precision == SFFT_PREC_FP64) {
+        if (dtype == SFFT_F64)
+            k_moments<double, double><<<grid, 256, 0, st>>>((const double *)sci, mask, g, mom_part);
+        else
+            k_moments<double, float><<<grid, 256, 0, st>>>((const float *)sci, mask, g, mom_part);
+    } else {
+        if (dtype == SFFT_F64)
+            k_moments<float, double><<<grid, 256, 0, st>>>((const double *)sci, mask, g, mom_part);
+        else
+            k_moments<float, float><<<grid, 256, 0, st>>>((const float *)sci, mask, g, mom_part);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lag_tables(const Geometry &g, const double *ypart, double *ysum, const double *tw_x,
+                              double *lagww, double *lagwg, double *lagws, const double *mom_part, double *mom,
+                              cudaStream_t st) {
+    size_t total = (size_t)g.nkf * g.nent;
+    k_ysum<<<(unsigned)((total + 255) / 256), 256, 0, st>>>((const double2 *)ypart, g, (double2 *)ysum);
+    int nout = g.npair * (2 * g.L - 1) * (2 * g.L - 1) + g.nk * (g.nb + 1) * g.L * g.L;
+    k_lagx<<<(nout + 127) / 128, 128, 0, st>>>((const double2 *)ysum, (const double2 *)tw_x, g, lagww, lagwg,
+                                               lagws);
+    k_mom_reduce<<<(g.nmom + 63) / 64, 64, 0, st>>>(mom_part, g.mom_ctas, g.nmom, mom);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_assemble(const Geometry &g, const double *lagww, const double *lagwg, const double *lagws,
+                            const double *mom, double *N, double *b, cudaStream_t st) {
+    size_t total = (size_t)g.n * g.n;
+    k_assemble<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(lagww, lagwg, lagws, mom, g, N, b);
+    return cudaGetLastError();
+}
+
+}  // namespace sfft

@@ -1,0 +1,180 @@
+// Difference image:  D(u) = S(u) - sum_{i,d} a_{i,d} (w_i T)((u - d) mod N) - sum_r b_r w_r(u)
+// on the unmasked frames, with w_i = xh^p yh^q evaluated at the source pixel u - d.
+//
+// Grouping the kernel monomials by their x power p folds the y power into per-row
+// coefficients:  sum_i a_{i,d} xh_s^p yh_s^q T_s = sum_p xh_s^p T_s c_p(d, y_s),
+// c_p(d, y_s) = sum_{i: p_i = p} a_{i,d} yh_s^q_i, so each output pixel costs
+// (DK+1) L^2 multiply-adds instead of nP(DK) L^2.
+//
+// CTA: 8 output rows x 256 columns; a warp per row, 8 consecutive pixels per thread.
+// Shared memory holds the cyclic template window (rows y0-h.., columns x0-h..), the x
+// powers of its columns and the folded coefficients for the CTA's rows.
+#include "sfft_internal.cuh"
+
+namespace sfft {
+namespace {
+
+constexpr int kRowsO = 8, kRX = 8, kColsO = 32 * kRX;
+
+template <class R>
+__device__ __forceinline__ R coordv(int i, int n) {
+    return n > 1 ? (R)(2 * i - (n - 1)) / (R)(n - 1) : (R)0;
+}
+
+template <class R, class In, int LL>
+__global__ void __launch_bounds__(256) k_subtract(const In *__restrict__ sci, const In *__restrict__ tmpl,
+                                                 Geometry g, const double *__restrict__ coeffs,
+                                                 In *__restrict__ diff) {
+    constexpr int h = LL / 2;
+    constexpr int WC = kColsO + 2 * h;  // window columns
+    constexpr int WR = kRowsO + 2 * h;  // window rows
+    constexpr int NW = kRX + LL - 1;    // register window per thread
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int dk = g.dk, np = dk + 1;
+    R *Tw = reinterpret_cast<R *>(smem_raw);  // [WR][WC]
+    R *xp = Tw + WR * WC;                      // [np][WC]
+    R *cf = xp + np * WC;                      // [kRowsO][LL][np][LL]
+    R *byp = cf + kRowsO * LL * np * LL;       // [kRowsO][db+1]  background per x power
+
+    const int x0 = blockIdx.x * kColsO, y0 = blockIdx.y * kRowsO;
+    const int tid = threadIdx.x;
+    const int nx = g.nx, ny = g.ny;
+
+    for (int e = tid; e < WR * WC; e += blockDim.x) {
+        int r = e / WC, c = e - r * WC;
+        int yy = ((y0 - h + r) % ny + ny) % ny;
+        int xx = ((x0 - h + c) % nx + nx) % nx;
+        Tw[e] = (R)tmpl[(size_t)yy * g.pitch + xx];
+    }
+    for (int c = tid; c < WC; c += blockDim.x) {
+        int xx = ((x0 - h + c) % nx + nx) % nx;
+        R xh = coordv<R>(xx, nx), v = (R)1;
+        for (int p = 0; p < np; p++) {
+            xp[p * WC + c] = v;
+            v *= xh;
+        }
+    }
+    // folded kernel coefficients c_p(d, y - dy) for each of the CTA's output rows
+    const int ncf = kRowsO * LL * np * LL;
+    for (int e = tid; e < ncf; e += blockDim.x) {
+        int dxi = e % LL, rest = e / LL;
+        int p = rest % np;
+        rest /= np;
+        int dyi = rest % LL, ry = rest / LL;
+        int ys = (((y0 + ry) - (dyi - h)) % ny + ny) % ny;  // source row y - dy
+        double yh = coordv<double>(ys, ny);
+        double acc = 0.0;
+        for (int i = 0; i < g.nk; i++) {
+            int pi, qi;
+            mono_pq(i, pi, qi);
+            if (pi != p) continue;
+            double w = 1.0;
+            for (int q = 0; q < qi; q++) w *= yh;
+            acc += coeffs[(size_t)i * LL * LL + dyi * LL + dxi] * w;
+        }
+        cf[e] = (R)acc;
+    }
+    for (int e = tid; e < kRowsO * (g.db + 1); e += blockDim.x) {
+        int ry = e / (g.db + 1), p = e % (g.db + 1);
+        double yh = coordv<double>(min(y0 + ry, ny - 1), ny);
+        double acc = 0.0;
+        for (int r = 0; r < g.nb; r++) {
+            int pr, qr;
+            mono_pq(r, pr, qr);
+            if (pr != p) continue;
+            double w = 1.0;
+            for (int q = 0; q < qr; q++) w *= yh;
+            acc += coeffs[g.nker + r] * w;
+        }
+        byp[e] = (R)acc;
+    }
+    __syncthreads();
+
+    const int ty = tid >> 5, lane = tid & 31;
+    const int y = y0 + ty;
+    const int cx = lane * kRX;  // first output column of this thread within the tile
+    R out[kRX];
+#pragma unroll
+    for (int r = 0; r < kRX; r++) out[r] = (R)0;
+    for (int dyi = 0; dyi < LL; dyi++) {
+        // source row y - dy sits at window row ty + h - dy = ty + (LL - 1) - dyi
+        const R *trow = Tw + (ty + (LL - 1) - dyi) * WC + cx;
+        R wv[NW];
+#pragma unroll
+        for (int m = 0; m < NW; m++) wv[m] = trow[m];
+        for (int p = 0; p < np; p++) {
+            R wp[NW];
+            const R *xr = xp + p * WC + cx;
+#pragma unroll
+            for (int m = 0; m < NW; m++) wp[m] = wv[m] * xr[m];
+            const R *c = cf + ((ty * LL + dyi) * np + p) * LL;
+#pragma unroll
+            for (int dxi = 0; dxi < LL; dxi++) {
+                R cc = c[dxi];
+                // source column x - dx -> window index (r - dx + h) = r + (LL - 1) - dxi
+#pragma unroll
+                for (int r = 0; r < kRX; r++) out[r] += cc * wp[r + (LL - 1) - dxi];
+            }
+        }
+    }
+    if (y < ny) {
+        const R *bp = byp + ty * (g.db + 1);
+#pragma unroll
+        for (int r = 0; r < kRX; r++) {
+            int x = x0 + cx + r;
+            if (x < nx) {
+                R xv = coordv<R>(x, nx), bg = (R)0, pw = (R)1;
+                for (int p = 0; p <= g.db; p++) {
+                    bg += bp[p] * pw;
+                    pw *= xv;
+                }
+                size_t u = (size_t)y * g.pitch + x;
+                diff[u] = (In)((R)sci[u] - out[r] - bg);
+            }
+        }
+    }
+}
+
+template <class R, class In, int LL>
+cudaError_t run(const Geometry &g, const void *sci, const void *tmpl, const double *coeffs, void *diff,
+                cudaStream_t st) {
+    constexpr int h = LL / 2;
+    const int np = g.dk + 1;
+    size_t sm = sizeof(R) * ((size_t)(kRowsO + 2 * h) * (kColsO + 2 * h) + (size_t)np * (kColsO + 2 * h) +
+                             (size_t)kRowsO * LL * np * LL + (size_t)kRowsO * (g.db + 1));
+    auto kern = k_subtract<R, In, LL>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    dim3 grid((g.nx + kColsO - 1) / kColsO, (g.ny + kRowsO - 1) / kRowsO);
+    kern<<<grid, 256, sm, st>>>((const In *)sci, (const In *)tmpl, g, coeffs, (In *)diff);
+    return cudaGetLastError();
+}
+
+template <class R, class In>
+cudaError_t dispatch_L(const Geometry &g, const void *sci, const void *tmpl, const double *coeffs, void *diff,
+                       cudaStream_t st) {
+    switch (g.L) {
+        case 1: return run<R, In, 1>(g, sci, tmpl, coeffs, diff, st);
+        case 3: return run<R, In, 3>(g, sci, tmpl, coeffs, diff, st);
+        case 5: return run<R, In, 5>(g, sci, tmpl, coeffs, diff, st);
+        case 7: return run<R, In, 7>(g, sci, tmpl, coeffs, diff, st);
+        case 9: return run<R, In, 9>(g, sci, tmpl, coeffs, diff, st);
+        case 11: return run<R, In, 11>(g, sci, tmpl, coeffs, diff, st);
+        case 13: return run<R, In, 13>(g, sci, tmpl, coeffs, diff, st);
+        case 15: return run<R, In, 15>(g, sci, tmpl, coeffs, diff, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_subtract(const Geometry &g, int dtype, int precision, const void *sci, const void *tmpl,
+                            const double *coeffs, void *diff, cudaStream_t st) {
+    if (precision == SFFT_PREC_FP64)
+        return dtype == SFFT_F64 ? dispatch_L<double, double>(g, sci, tmpl, coeffs, diff, st)
+                                 : dispatch_L<double, float>(g, sci, tmpl, coeffs, diff, st);
+    return dtype == SFFT_F64 ? dispatch_L<float, double>(g, sci, tmpl, coeffs, diff, st)
+                             : dispatch_L<float, float>(g, sci, tmpl, coeffs, diff, st);
+}
+
+}  // namespace sfft

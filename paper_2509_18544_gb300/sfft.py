@@ -1,0 +1,208 @@
+"""Python binding of libsfft (``include/sfft.h``): argument marshalling only.
+
+Every function here has the name of the C entry point it wraps and passes device pointers
+(``torch.Tensor.data_ptr()`` or plain integers) straight through; all arithmetic runs in
+the CUDA kernels of ``libsfft.so``.  If the library has not been built this module raises
+``SfftError`` on first use -- there is no CPU path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "lib", "libsfft.so")
+
+OK, ERR_INVALID_ARG, ERR_CUDA, ERR_OOM, ERR_NOT_SPD, ERR_NO_CONVERGENCE, ERR_TIMEOUT, ERR_UNSUPPORTED = range(8)
+F32, F64 = 0, 1
+PREC_FP32, PREC_SPLIT, PREC_FP64 = 0, 1, 2
+SOLVE_CHOLESKY, SOLVE_PCG = 0, 1
+
+EXPORTED = ("sfft_plan", "sfft_destroy", "sfft_n_unknowns", "sfft_workspace_size", "sfft_set_stream",
+            "sfft_normal", "sfft_fit", "sfft_subtract", "sfft_sync_status", "sfft_batch",
+            "sfft_status_string", "sfft_last_error")
+
+
+class SfftError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s (status %d)" % (msg, status))
+        self.status = status
+
+
+class sfft_desc(ctypes.Structure):
+    _fields_ = [("ny", ctypes.c_int32), ("nx", ctypes.c_int32), ("pitch", ctypes.c_int32),
+                ("L", ctypes.c_int32), ("dk", ctypes.c_int32), ("db", ctypes.c_int32),
+                ("dtype", ctypes.c_int32), ("precision", ctypes.c_int32), ("solver", ctypes.c_int32),
+                ("max_iter", ctypes.c_int32), ("tol", ctypes.c_double), ("workspace_cap", ctypes.c_size_t),
+                ("seg", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
+
+
+class sfft_fit_info(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("n", ctypes.c_int32), ("iterations", ctypes.c_int32),
+                ("fallback", ctypes.c_int32), ("rel_residual", ctypes.c_double),
+                ("reserved", ctypes.c_double * 3)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libsfft.so (built by ``paper_2509_18544_gb300.build``); raise if it is missing."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(path):
+            raise SfftError(ERR_UNSUPPORTED, "libsfft.so not built at %s (run __graft_entry__.build())" % path)
+        lib = ctypes.CDLL(path)
+        P, I32 = ctypes.c_void_p, ctypes.c_int32
+        lib.sfft_plan.argtypes = [ctypes.POINTER(P), ctypes.POINTER(sfft_desc), P]
+        lib.sfft_destroy.argtypes = [P]
+        lib.sfft_destroy.restype = None
+        lib.sfft_n_unknowns.argtypes = [P, ctypes.POINTER(I32)]
+        lib.sfft_workspace_size.argtypes = [ctypes.POINTER(sfft_desc), ctypes.POINTER(ctypes.c_size_t)]
+        lib.sfft_set_stream.argtypes = [P, P]
+        lib.sfft_normal.argtypes = [P, P, P, P, P, P]
+        lib.sfft_fit.argtypes = [P, P, P, P, P, P, ctypes.POINTER(sfft_fit_info)]
+        lib.sfft_subtract.argtypes = [P, P, P, P, P]
+        lib.sfft_sync_status.argtypes = [P]
+        lib.sfft_batch.argtypes = [ctypes.POINTER(sfft_desc), I32, I32, P, P, P, P, P, P, P,
+                                   ctypes.POINTER(sfft_fit_info), P]
+        lib.sfft_status_string.argtypes = [I32]
+        lib.sfft_status_string.restype = ctypes.c_char_p
+        lib.sfft_last_error.argtypes = [P]
+        lib.sfft_last_error.restype = ctypes.c_char_p
+        for name in EXPORTED:
+            if name not in ("sfft_destroy", "sfft_status_string", "sfft_last_error"):
+                getattr(lib, name).restype = ctypes.c_int
+        _lib = lib
+        return lib
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    return x.data_ptr()
+
+
+def _stream(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream or None
+    return stream.cuda_stream or None
+
+
+def _check(rc, handle=None):
+    if rc != OK:
+        lib = load_library()
+        msg = lib.sfft_last_error(handle).decode(errors="replace") or lib.sfft_status_string(rc).decode()
+        raise SfftError(rc, msg)
+
+
+class Plan:
+    """Owns one ``sfft_plan_t``; created by :func:`sfft_plan`."""
+
+    def __init__(self, handle, desc):
+        self.handle = handle
+        self.desc = desc
+
+    @property
+    def n(self) -> int:
+        return sfft_n_unknowns(self)
+
+    def close(self):
+        if self.handle:
+            load_library().sfft_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def make_desc(ny, nx, L, dk, db, dtype=F32, precision=PREC_FP32, solver=SOLVE_CHOLESKY, pitch=0,
+              max_iter=0, tol=0.0, workspace_cap=0, seg=0) -> sfft_desc:
+    d = sfft_desc()
+    d.ny, d.nx, d.pitch, d.L, d.dk, d.db = ny, nx, pitch, L, dk, db
+    d.dtype, d.precision, d.solver = dtype, precision, solver
+    d.max_iter, d.tol, d.workspace_cap, d.seg = max_iter, tol, workspace_cap, seg
+    return d
+
+
+def sfft_plan(desc: sfft_desc, stream=None) -> Plan:
+    lib = load_library()
+    h = ctypes.c_void_p()
+    _check(lib.sfft_plan(ctypes.byref(h), ctypes.byref(desc), _stream(stream)))
+    return Plan(h.value, desc)
+
+
+def sfft_destroy(plan: Plan):
+    plan.close()
+
+
+def sfft_n_unknowns(plan: Plan) -> int:
+    n = ctypes.c_int32()
+    _check(load_library().sfft_n_unknowns(plan.handle, ctypes.byref(n)), plan.handle)
+    return n.value
+
+
+def sfft_workspace_size(desc: sfft_desc) -> int:
+    v = ctypes.c_size_t()
+    _check(load_library().sfft_workspace_size(ctypes.byref(desc), ctypes.byref(v)))
+    return v.value
+
+
+def sfft_set_stream(plan: Plan, stream):
+    _check(load_library().sfft_set_stream(plan.handle, _stream(stream)), plan.handle)
+
+
+def sfft_normal(plan: Plan, sci, tmpl, mask, N, b):
+    _check(load_library().sfft_normal(plan.handle, _ptr(sci), _ptr(tmpl), _ptr(mask), _ptr(N), _ptr(b)),
+           plan.handle)
+
+
+def sfft_fit(plan: Plan, sci, tmpl, mask, x0, coeffs, want_info: bool = True):
+    """Queue the fit; with ``want_info`` synchronise and return the sfft_fit_info (raises on
+    a device-side failure such as a non-positive-definite normal matrix)."""
+    info = sfft_fit_info() if want_info else None
+    rc = load_library().sfft_fit(plan.handle, _ptr(sci), _ptr(tmpl), _ptr(mask), _ptr(x0), _ptr(coeffs),
+                                 ctypes.byref(info) if info is not None else None)
+    _check(rc, plan.handle)
+    return info
+
+
+def sfft_subtract(plan: Plan, sci, tmpl, coeffs, diff):
+    _check(load_library().sfft_subtract(plan.handle, _ptr(sci), _ptr(tmpl), _ptr(coeffs), _ptr(diff)),
+           plan.handle)
+
+
+def sfft_sync_status(plan: Plan):
+    _check(load_library().sfft_sync_status(plan.handle), plan.handle)
+
+
+def sfft_batch(desc: sfft_desc, n_sci, n_tmpl, sci, tmpl, masks, ny, nx, coeffs, diff, want_info=True,
+               stream=None):
+    """All S x T pairs; lists of device tensors (science-major pairs for masks/coeffs/diff)."""
+    npairs = n_sci * n_tmpl
+    P = ctypes.c_void_p
+    arr = lambda xs: (P * len(xs))(*[_ptr(x) for x in xs])
+    i32 = lambda xs: (ctypes.c_int32 * len(xs))(*xs)
+    infos = (sfft_fit_info * npairs)() if want_info else None
+    rc = load_library().sfft_batch(ctypes.byref(desc), n_sci, n_tmpl, arr(sci), arr(tmpl),
+                                   arr(masks) if masks is not None else None, i32(ny), i32(nx),
+                                   arr(coeffs), arr(diff), infos, _stream(stream))
+    _check(rc)
+    return list(infos) if infos is not None else None
