@@ -140,6 +140,20 @@ sfft_status sfft_batch(const sfft_desc *base, int32_t n_sci, int32_t n_tmpl, con
                        const int32_t *nx, double *const *coeffs, void *const *diff,
                        sfft_fit_info *infos, sfft_stream_t stream);
 
+/* Stage timing (instrumentation; the paper profiles its pipeline stage by stage, Sec. "GPU
+ * acceleration and performance").  With enable != 0 every later call records CUDA events
+ * around its stages on the plan's stream.  sfft_stage_times synchronises the stream, adds
+ * the elapsed milliseconds of all calls since the previous read into ms[0..SFFT_NSTAGES-1]
+ * (host array, caller-owned; order: segment FFT, background moments, y-correlation, lag
+ * tables, assembly, solve, subtract, refinement), sets *calls to the number of timed calls,
+ * and resets the accumulators. */
+enum { SFFT_NSTAGES = 8 };
+sfft_status sfft_profile(sfft_plan_t plan, int32_t enable);
+sfft_status sfft_stage_times(sfft_plan_t plan, double *ms, int32_t *calls);
+
+/* Process-wide number of kernel launches libsfft has issued (host counter). */
+sfft_status sfft_launch_count(uint64_t *count);
+
 const char *sfft_status_string(sfft_status s);
 /* Last error message recorded on this plan (or the process-wide one for plan == NULL). */
 const char *sfft_last_error(sfft_plan_t plan);

@@ -5,6 +5,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <atomic>
 #include <map>
 #include <new>
 #include <tuple>
@@ -92,6 +93,7 @@ bool make_geometry(const sfft_desc &d, Geometry &g, char *err, size_t errlen) {
     g.mom_rows = 128;
     g.mom_ctas = ((d.nx + 255) / 256) * ((d.ny + g.mom_rows - 1) / g.mom_rows);
     g.nmom = npoly(2 * d.db) + npoly(d.db);
+    g.pmax = d.dk > 2 * d.db ? d.dk : 2 * d.db;
     if (d.precision == SFFT_PREC_SPLIT) return snprintf(err, errlen, "split precision not built yet"), false;
     if (d.solver == SFFT_SOLVE_PCG) return snprintf(err, errlen, "PCG solver not built yet"), false;
     return true;
@@ -131,12 +133,47 @@ static size_t carve(const Geometry &g, int precision, void *base, Workspace *w) 
     o.q = c.take<double>(base, (size_t)g.n);
     o.scal = c.take<double>(base, 16);
     o.status = c.take<int>(base, 16);
-    o.tw_fft = c.take<char>(base, (size_t)g.P * cpx_sz);
+    o.tw_fft = c.take<char>(base, (size_t)2 * g.P * cpx_sz);
+    o.xpow = c.take<char>(base, (size_t)(g.pmax + 1) * g.nx * (cpx_sz / 2));
+    o.ypow = c.take<char>(base, (size_t)(g.pmax + 1) * g.ny * (cpx_sz / 2));
     o.tw_x = c.take<double>(base, (size_t)g.nkf * (2 * g.G + 1) * 2);
     return align_up(c.off, 256);
 }
 
 size_t workspace_bytes(const Geometry &g, int precision) { return carve(g, precision, nullptr, nullptr); }
+
+static std::atomic<uint64_t> g_launches{0};
+void note_launch(int count) { g_launches.fetch_add((uint64_t)count, std::memory_order_relaxed); }
+
+// Records a CUDA event pair around one stage on the plan's stream while profiling is on.
+struct StageTimer {
+    sfft_plan_t p;
+    int stage;
+    cudaEvent_t a = nullptr;
+    static cudaEvent_t get(sfft_plan_t p) {
+        cudaEvent_t e = nullptr;
+        if (!p->ev_free.empty()) {
+            e = p->ev_free.back();
+            p->ev_free.pop_back();
+        } else if (cudaEventCreate(&e) != cudaSuccess) {
+            e = nullptr;
+        }
+        return e;
+    }
+    StageTimer(sfft_plan_t p_, int stage_) : p(p_), stage(stage_) {
+        if (p->profile && (a = get(p)) != nullptr) cudaEventRecord(a, p->stream);
+    }
+    ~StageTimer() {
+        if (!a) return;
+        cudaEvent_t b = get(p);
+        if (!b) {
+            p->ev_free.push_back(a);
+            return;
+        }
+        cudaEventRecord(b, p->stream);
+        p->ev_pending[stage].push_back({a, b});
+    }
+};
 
 }  // namespace sfft
 
@@ -220,21 +257,51 @@ sfft_status sfft_plan(sfft_plan_t *plan, const sfft_desc *desc, sfft_stream_t st
         }
     }
     e = cudaMemcpyAsync(p->ws.tw_x, twx.data(), twx.size() * sizeof(double), cudaMemcpyHostToDevice, p->stream);
+    // forward FFT twiddles exp(-2 pi i m / P): high part then remainder (zero for FP64)
+    std::vector<double> tw64((size_t)g.P * 4, 0.0);
+    std::vector<float> tw((size_t)g.P * 4, 0.0f);
     if (e == cudaSuccess) {
         if (desc->precision == SFFT_PREC_FP64) {
-            std::vector<double> tw((size_t)g.P * 2);
             for (int m = 0; m < g.P; m++) {
-                tw[2 * m] = cos(two_pi * m / g.P);
-                tw[2 * m + 1] = -sin(two_pi * m / g.P);
+                tw64[2 * m] = cos(two_pi * m / g.P);
+                tw64[2 * m + 1] = -sin(two_pi * m / g.P);
             }
-            e = cudaMemcpyAsync(p->ws.tw_fft, tw.data(), tw.size() * sizeof(double), cudaMemcpyHostToDevice, p->stream);
+            e = cudaMemcpyAsync(p->ws.tw_fft, tw64.data(), tw64.size() * sizeof(double), cudaMemcpyHostToDevice, p->stream);
         } else {
-            std::vector<float> tw((size_t)g.P * 2);
             for (int m = 0; m < g.P; m++) {
-                tw[2 * m] = (float)cos(two_pi * m / g.P);
-                tw[2 * m + 1] = (float)-sin(two_pi * m / g.P);
+                double c = cos(two_pi * m / g.P), sn = -sin(two_pi * m / g.P);
+                float ch = (float)c, sh = (float)sn;
+                tw[2 * m] = ch;
+                tw[2 * m + 1] = sh;
+                tw[2 * (g.P + m)] = (float)(c - (double)ch);
+                tw[2 * (g.P + m) + 1] = (float)(sn - (double)sh);
             }
             e = cudaMemcpyAsync(p->ws.tw_fft, tw.data(), tw.size() * sizeof(float), cudaMemcpyHostToDevice, p->stream);
+        }
+    }
+    // coordinate power tables xh^p, yh^q (p, q <= pmax): FP64 powers rounded once
+    std::vector<double> xp64((size_t)(g.pmax + 1) * g.nx), yp64((size_t)(g.pmax + 1) * g.ny);
+    std::vector<float> xp32(xp64.size()), yp32(yp64.size());
+    for (int axis = 0; axis < 2; axis++) {
+        int len = axis ? g.ny : g.nx;
+        std::vector<double> &t = axis ? yp64 : xp64;
+        for (int i = 0; i < len; i++) {
+            double c = len > 1 ? (2.0 * i - (len - 1)) / (double)(len - 1) : 0.0, v = 1.0;
+            for (int q = 0; q <= g.pmax; q++) {
+                t[(size_t)q * len + i] = v;
+                v *= c;
+            }
+        }
+    }
+    for (size_t i = 0; i < xp64.size(); i++) xp32[i] = (float)xp64[i];
+    for (size_t i = 0; i < yp64.size(); i++) yp32[i] = (float)yp64[i];
+    if (e == cudaSuccess) {
+        if (desc->precision == SFFT_PREC_FP64) {
+            e = cudaMemcpyAsync(p->ws.xpow, xp64.data(), xp64.size() * 8, cudaMemcpyHostToDevice, p->stream);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(p->ws.ypow, yp64.data(), yp64.size() * 8, cudaMemcpyHostToDevice, p->stream);
+        } else {
+            e = cudaMemcpyAsync(p->ws.xpow, xp32.data(), xp32.size() * 4, cudaMemcpyHostToDevice, p->stream);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(p->ws.ypow, yp32.data(), yp32.size() * 4, cudaMemcpyHostToDevice, p->stream);
         }
     }
     if (e == cudaSuccess) e = cudaMemsetAsync(p->ws.status, 0, 16 * sizeof(int), p->stream);
@@ -252,8 +319,46 @@ sfft_status sfft_plan(sfft_plan_t *plan, const sfft_desc *desc, sfft_stream_t st
 void sfft_destroy(sfft_plan_t plan) {
     if (!plan) return;
     cudaStreamSynchronize(plan->stream);
+    for (auto &v : plan->ev_pending)
+        for (auto &pr : v) {
+            cudaEventDestroy(pr.first);
+            cudaEventDestroy(pr.second);
+        }
+    for (cudaEvent_t e : plan->ev_free) cudaEventDestroy(e);
     cudaFree(plan->ws.base);
     delete plan;
+}
+
+sfft_status sfft_profile(sfft_plan_t plan, int32_t enable) {
+    if (!plan) return set_err(nullptr, "null plan"), SFFT_ERR_INVALID_ARG;
+    plan->profile = enable != 0;
+    return SFFT_OK;
+}
+
+sfft_status sfft_stage_times(sfft_plan_t plan, double *ms, int32_t *calls) {
+    if (!plan || !ms) return set_err(plan, "null argument"), SFFT_ERR_INVALID_ARG;
+    cudaError_t e = cudaStreamSynchronize(plan->stream);
+    if (e != cudaSuccess) return cuda_fail(plan, e, "stage-time sync");
+    for (int st = 0; st < SFFT_NSTAGES; st++) {
+        double sum = 0.0;
+        for (auto &pr : plan->ev_pending[st]) {
+            float t = 0.f;
+            if (cudaEventElapsedTime(&t, pr.first, pr.second) == cudaSuccess) sum += t;
+            plan->ev_free.push_back(pr.first);
+            plan->ev_free.push_back(pr.second);
+        }
+        plan->ev_pending[st].clear();
+        ms[st] = sum;
+    }
+    if (calls) *calls = plan->timed_calls;
+    plan->timed_calls = 0;
+    return SFFT_OK;
+}
+
+sfft_status sfft_launch_count(uint64_t *count) {
+    if (!count) return set_err(nullptr, "null argument"), SFFT_ERR_INVALID_ARG;
+    *count = g_launches.load();
+    return SFFT_OK;
 }
 
 sfft_status sfft_n_unknowns(sfft_plan_t plan, int32_t *n) {
@@ -284,16 +389,31 @@ static sfft_status queue_normal(sfft_plan_t p, const void *sci, const void *tmpl
     Workspace &w = p->ws;
     cudaStream_t st = p->stream;
     cudaError_t e;
-    if ((e = launch_segment_fft(g, p->desc.dtype, p->desc.precision, sci, tmpl, mask, w.tw_fft, w.spec, st)) != cudaSuccess)
-        return cuda_fail(p, e, "segment FFT launch");
-    if ((e = launch_moments(g, p->desc.dtype, p->desc.precision, sci, mask, w.mom_part, st)) != cudaSuccess)
-        return cuda_fail(p, e, "moments launch");
-    if ((e = launch_ycorr(g, p->desc.precision, w.spec, w.ypart, st)) != cudaSuccess)
-        return cuda_fail(p, e, "y-correlation launch");
-    if ((e = launch_lag_tables(g, w.ypart, w.ysum, w.tw_x, w.lagww, w.lagwg, w.lagws, w.mom_part, w.mom, st)) != cudaSuccess)
-        return cuda_fail(p, e, "lag-table launch");
-    if ((e = launch_assemble(g, w.lagww, w.lagwg, w.lagws, w.mom, N, b, st)) != cudaSuccess)
-        return cuda_fail(p, e, "assembly launch");
+    {
+        StageTimer t(p, ST_SEGFFT);
+        e = launch_segment_fft(g, p->desc.dtype, p->desc.precision, sci, tmpl, mask, w.tw_fft, w.xpow, w.ypow, w.spec, st);
+    }
+    if (e != cudaSuccess) return cuda_fail(p, e, "segment FFT launch");
+    {
+        StageTimer t(p, ST_MOMENTS);
+        e = launch_moments(g, p->desc.dtype, p->desc.precision, sci, mask, w.ypow, w.mom_part, st);
+    }
+    if (e != cudaSuccess) return cuda_fail(p, e, "moments launch");
+    {
+        StageTimer t(p, ST_YCORR);
+        e = launch_ycorr(g, p->desc.precision, w.spec, w.ypart, st);
+    }
+    if (e != cudaSuccess) return cuda_fail(p, e, "y-correlation launch");
+    {
+        StageTimer t(p, ST_LAGS);
+        e = launch_lag_tables(g, w.ypart, w.ysum, w.tw_x, w.lagww, w.lagwg, w.lagws, w.mom_part, w.mom, st);
+    }
+    if (e != cudaSuccess) return cuda_fail(p, e, "lag-table launch");
+    {
+        StageTimer t(p, ST_ASSEMBLE);
+        e = launch_assemble(g, w.lagww, w.lagwg, w.lagws, w.mom, N, b, st);
+    }
+    if (e != cudaSuccess) return cuda_fail(p, e, "assembly launch");
     return SFFT_OK;
 }
 
@@ -302,6 +422,7 @@ sfft_status sfft_normal(sfft_plan_t plan, const void *sci, const void *tmpl, con
     sfft_status s = check_images(plan, sci, tmpl);
     if (s != SFFT_OK) return s;
     if (!N || !b) return set_err(plan, "null output pointer"), SFFT_ERR_INVALID_ARG;
+    if (plan->profile) plan->timed_calls++;
     return queue_normal(plan, sci, tmpl, mask, N, b);
 }
 
@@ -335,9 +456,13 @@ sfft_status sfft_fit(sfft_plan_t plan, const void *sci, const void *tmpl, const 
     Workspace &w = plan->ws;
     cudaError_t e = cudaMemsetAsync(w.status, 0, sizeof(int), plan->stream);
     if (e != cudaSuccess) return cuda_fail(plan, e, "status reset");
+    if (plan->profile) plan->timed_calls++;
     s = queue_normal(plan, sci, tmpl, mask, w.N, w.b);
     if (s != SFFT_OK) return s;
-    e = launch_cholesky_solve(plan->g, w.N, w.b, w.R, coeffs, w.r, w.z, w.scal, w.status, plan->stream);
+    {
+        StageTimer t(plan, ST_SOLVE);
+        e = launch_cholesky_solve(plan->g, w.N, w.b, w.R, coeffs, w.r, w.z, w.scal, w.status, plan->stream);
+    }
     if (e != cudaSuccess) return cuda_fail(plan, e, "solver launch");
     if (info) return read_status(plan, info);
     return SFFT_OK;
@@ -348,7 +473,12 @@ sfft_status sfft_subtract(sfft_plan_t plan, const void *sci, const void *tmpl, c
     if (s != SFFT_OK) return s;
     if (!coeffs || !diff) return set_err(plan, "null coeffs or diff"), SFFT_ERR_INVALID_ARG;
     if (diff == sci || diff == tmpl) return set_err(plan, "diff may not alias the inputs"), SFFT_ERR_INVALID_ARG;
-    cudaError_t e = launch_subtract(plan->g, plan->desc.dtype, plan->desc.precision, sci, tmpl, coeffs, diff, plan->stream);
+    cudaError_t e;
+    {
+        StageTimer t(plan, ST_SUBTRACT);
+        e = launch_subtract(plan->g, plan->desc.dtype, plan->desc.precision, sci, tmpl, coeffs, plan->ws.xpow, diff,
+                            plan->stream);
+    }
     if (e != cudaSuccess) return cuda_fail(plan, e, "subtract launch");
     return SFFT_OK;
 }

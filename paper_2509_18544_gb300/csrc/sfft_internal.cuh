@@ -52,6 +52,7 @@ struct Geometry {
     int ytile;                 // y-correlation rows per staged tile
     int mom_rows, mom_ctas;    // background-moment reduction geometry
     int nmom;                  // moments: npoly(2 db) mask moments + npoly(db) science moments
+    int pmax;                  // highest coordinate power tabulated: max(dk, 2 db)
 };
 
 bool make_geometry(const sfft_desc &d, Geometry &g, char *err, size_t errlen);
@@ -74,13 +75,22 @@ struct Workspace {
     double *x = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr;  // [n] solver vectors
     double *scal = nullptr;      // [16] solver scalars
     int *status = nullptr;       // device status word(s)
-    void *tw_fft = nullptr;      // [P] complex (R): exp(-2 pi i m / P)
+    void *tw_fft = nullptr;      // [2][P] complex (R): exp(-2 pi i m / P), high part then remainder
+    void *xpow = nullptr;        // [pmax+1][nx] (R): xh^p, FP64 powers rounded once
+    void *ypow = nullptr;        // [pmax+1][ny] (R): yh^q
     double *tw_x = nullptr;      // [nkf][2G+1] complex FP64: w_k exp(+2 pi i k m / P) / P
 };
 
 size_t workspace_bytes(const Geometry &g, int precision);
 
+// process-wide count of kernel launches (every launcher calls this before each launch)
+void note_launch(int count = 1);
+
+enum Stage { ST_SEGFFT = 0, ST_MOMENTS, ST_YCORR, ST_LAGS, ST_ASSEMBLE, ST_SOLVE, ST_SUBTRACT, ST_REFINE, ST_COUNT };
+
 }  // namespace sfft
+
+#include <vector>
 
 struct sfft_plan_s {
     sfft_desc desc;
@@ -89,6 +99,11 @@ struct sfft_plan_s {
     cudaStream_t stream;
     int device;
     char err[512];
+    // stage timing: event pairs recorded while profiling, summed on read
+    bool profile = false;
+    int timed_calls = 0;
+    std::vector<cudaEvent_t> ev_free;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending[sfft::ST_COUNT];
 };
 
 namespace sfft {
@@ -96,11 +111,11 @@ namespace sfft {
 // ------------------------------------------------------------------ launchers
 // K1: products + row-segment real FFTs -> spec
 cudaError_t launch_segment_fft(const Geometry &g, int dtype, int precision, const void *sci,
-                               const void *tmpl, const uint8_t *mask, const void *tw_fft, void *spec,
-                               cudaStream_t st);
+                               const void *tmpl, const uint8_t *mask, const void *tw_fft, const void *xpow,
+                               const void *ypow, void *spec, cudaStream_t st);
 // background moments (mask and masked science times monomials) -> mom_part
 cudaError_t launch_moments(const Geometry &g, int dtype, int precision, const void *sci,
-                           const uint8_t *mask, double *mom_part, cudaStream_t st);
+                           const uint8_t *mask, const void *ypow, double *mom_part, cudaStream_t st);
 // K2: y-direction correlations at the kernel lags, per segment and frequency -> ypart
 cudaError_t launch_ycorr(const Geometry &g, int precision, const void *spec, double *ypart,
                          cudaStream_t st);
@@ -118,6 +133,7 @@ cudaError_t launch_cholesky_solve(const Geometry &g, const double *N, const doub
                                   cudaStream_t st);
 // difference image
 cudaError_t launch_subtract(const Geometry &g, int dtype, int precision, const void *sci,
-                            const void *tmpl, const double *coeffs, void *diff, cudaStream_t st);
+                            const void *tmpl, const double *coeffs, const void *xpow, void *diff,
+                            cudaStream_t st);
 
 }  // namespace sfft

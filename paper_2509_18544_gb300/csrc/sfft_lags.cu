@@ -29,7 +29,7 @@ constexpr int kMaxDB = 4;
 // Column sums over a band of rows, folded into FP64 products with x powers, reduced per CTA.
 template <class R, class In>
 __global__ void __launch_bounds__(256) k_moments(const In *__restrict__ sci, const uint8_t *__restrict__ mask,
-                                                Geometry g, double *__restrict__ part) {
+                                                const R *__restrict__ ypow, Geometry g, double *__restrict__ part) {
     __shared__ double red[8][64];
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int ya = blockIdx.y * g.mom_rows, yb = min(g.ny, ya + g.mom_rows);
@@ -47,12 +47,13 @@ __global__ void __launch_bounds__(256) k_moments(const In *__restrict__ sci, con
             size_t u = (size_t)y * g.pitch + x;
             R m = (mask && mask[u]) ? (R)0 : (R)1;
             R sm = m * (R)sci[u];
-            R yh = coordv<R>(y, g.ny), w = (R)1;
 #pragma unroll
             for (int b = 0; b <= 2 * kMaxDB; b++) {
-                if (b <= db2) cma[b] += m * w;
-                if (b <= g.db) csa[b] += sm * w;
-                w *= yh;
+                if (b <= db2) {
+                    R w = ypow[(size_t)b * g.ny + y];  // FP64 power rounded once (shared table)
+                    cma[b] += m * w;
+                    if (b <= g.db) csa[b] += sm * w;
+                }
             }
             if (++cnt == 16 || y == yb - 1) {
                 cnt = 0;
@@ -233,19 +234,19 @@ __global__ void k_assemble(const double *__restrict__ lagww, const double *__res
 }  // namespace
 
 cudaError_t launch_moments(const Geometry &g, int dtype, int precision, const void *sci, const uint8_t *mask,
-                           double *mom_part, cudaStream_t st) {
+                           const void *ypow, double *mom_part, cudaStream_t st) {
     if (g.db > kMaxDB) return cudaErrorInvalidValue;
     dim3 grid((g.nx + 255) / 256, (g.ny + g.mom_rows - 1) / g.mom_rows);
     if (precision == SFFT_PREC_FP64) {
         if (dtype == SFFT_F64)
-            k_moments<double, double><<<grid, 256, 0, st>>>((const double *)sci, mask, g, mom_part);
+            { note_launch(); k_moments<double, double><<<grid, 256, 0, st>>>((const double *)sci, mask, (const double *)ypow, g, mom_part); }
         else
-            k_moments<double, float><<<grid, 256, 0, st>>>((const float *)sci, mask, g, mom_part);
+            { note_launch(); k_moments<double, float><<<grid, 256, 0, st>>>((const float *)sci, mask, (const double *)ypow, g, mom_part); }
     } else {
         if (dtype == SFFT_F64)
-            k_moments<float, double><<<grid, 256, 0, st>>>((const double *)sci, mask, g, mom_part);
+            { note_launch(); k_moments<float, double><<<grid, 256, 0, st>>>((const double *)sci, mask, (const float *)ypow, g, mom_part); }
         else
-            k_moments<float, float><<<grid, 256, 0, st>>>((const float *)sci, mask, g, mom_part);
+            { note_launch(); k_moments<float, float><<<grid, 256, 0, st>>>((const float *)sci, mask, (const float *)ypow, g, mom_part); }
     }
     return cudaGetLastError();
 }
@@ -254,10 +255,13 @@ cudaError_t launch_lag_tables(const Geometry &g, const double *ypart, double *ys
                               double *lagww, double *lagwg, double *lagws, const double *mom_part, double *mom,
                               cudaStream_t st) {
     size_t total = (size_t)g.nkf * g.nent;
+    note_launch();
     k_ysum<<<(unsigned)((total + 255) / 256), 256, 0, st>>>((const double2 *)ypart, g, (double2 *)ysum);
     int nout = g.npair * (2 * g.L - 1) * (2 * g.L - 1) + g.nk * (g.nb + 1) * g.L * g.L;
+    note_launch();
     k_lagx<<<(nout + 127) / 128, 128, 0, st>>>((const double2 *)ysum, (const double2 *)tw_x, g, lagww, lagwg,
                                                lagws);
+    note_launch();
     k_mom_reduce<<<(g.nmom + 63) / 64, 64, 0, st>>>(mom_part, g.mom_ctas, g.nmom, mom);
     return cudaGetLastError();
 }
@@ -265,6 +269,7 @@ cudaError_t launch_lag_tables(const Geometry &g, const double *ypart, double *ys
 cudaError_t launch_assemble(const Geometry &g, const double *lagww, const double *lagwg, const double *lagws,
                             const double *mom, double *N, double *b, cudaStream_t st) {
     size_t total = (size_t)g.n * g.n;
+    note_launch();
     k_assemble<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(lagww, lagwg, lagws, mom, g, N, b);
     return cudaGetLastError();
 }

@@ -38,17 +38,29 @@ __device__ __forceinline__ void dft4(cpx<R> &a0, cpx<R> &a1, cpx<R> &a2, cpx<R> 
     a3 = {d02.re - d13.im, d02.im + d13.re};  // d02 + i d13
 }
 
-// forward 16-point DFT of v[0..15] in natural order; tw[m] = exp(-2 pi i m / 256),
-// so exp(-2 pi i m / 16) = tw[16 m]
+// v * w with the twiddle held as w = wh + wl (wl = FP32 remainder of the FP64 value).
+// FP32-rounded twiddles alone have |wh| != 1, which scales the energy of every product by
+// |wh|^2 -- a bias of ~-5e-8 that never averages out because the radix-16 stages reuse a
+// handful of twiddles; with the remainder folded into FMAs each product is rounded once
+// from (nearly) the exact value and the rounding is unbiased.
+__device__ __forceinline__ cpx<float> twmul(cpx<float> v, cpx<float> wh, cpx<float> wl) {
+    float tr = fmaf(v.re, wl.re, -v.im * wl.im);
+    float ti = fmaf(v.re, wl.im, v.im * wl.re);
+    return {fmaf(v.re, wh.re, fmaf(-v.im, wh.im, tr)), fmaf(v.re, wh.im, fmaf(v.im, wh.re, ti))};
+}
+__device__ __forceinline__ cpx<double> twmul(cpx<double> v, cpx<double> wh, cpx<double>) { return cmul(v, wh); }
+
+// forward 16-point DFT of v[0..15] in natural order; tw[m] = exp(-2 pi i m / 256) (high
+// part) and twl[m] its remainder, so exp(-2 pi i m / 16) = tw[16 m] + twl[16 m]
 template <class R>
-__device__ __forceinline__ void dft16(cpx<R> (&v)[16], const cpx<R> *tw) {
+__device__ __forceinline__ void dft16(cpx<R> (&v)[16], const cpx<R> *tw, const cpx<R> *twl) {
     // v[j1 + 4 j2]: 4-point DFTs over j2 for each j1 -> U[j1][k1] kept at v[j1 + 4 k1]
 #pragma unroll
     for (int j1 = 0; j1 < 4; j1++) dft4(v[j1], v[j1 + 4], v[j1 + 8], v[j1 + 12]);
 #pragma unroll
     for (int j1 = 1; j1 < 4; j1++)
 #pragma unroll
-        for (int k1 = 1; k1 < 4; k1++) v[j1 + 4 * k1] = cmul(v[j1 + 4 * k1], tw[16 * j1 * k1]);
+        for (int k1 = 1; k1 < 4; k1++) v[j1 + 4 * k1] = twmul(v[j1 + 4 * k1], tw[16 * j1 * k1], twl[16 * j1 * k1]);
     // 4-point DFTs over j1 for each k1 -> V[k1 + 4 k2] kept at v[4 k1 + k2]... gather first
     cpx<R> t[16];
 #pragma unroll
@@ -67,8 +79,8 @@ __device__ __forceinline__ void dft16(cpx<R> (&v)[16], const cpx<R> *tw) {
 template <class R, class In>
 __global__ void __launch_bounds__(256) k_segment_fft(const In *__restrict__ sci, const In *__restrict__ tmpl,
                                                     const uint8_t *__restrict__ mask, Geometry g,
-                                                    const cpx<R> *__restrict__ tw_g,
-                                                    cpx<R> *__restrict__ spec) {
+                                                    const cpx<R> *__restrict__ tw_g, const R *__restrict__ xpow_g,
+                                                    const R *__restrict__ ypow_g, cpx<R> *__restrict__ spec) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int nk = g.nk, nb = g.nb, G = g.G, U = g.U, nx = g.nx, ny = g.ny;
     const int maxdeg = g.dk > g.db ? g.dk : g.db;
@@ -77,8 +89,9 @@ __global__ void __launch_bounds__(256) k_segment_fft(const In *__restrict__ sci,
     const int tid = threadIdx.x;
 
     // shared layout
-    cpx<R> *tw = reinterpret_cast<cpx<R> *>(smem_raw);            // [P]
-    cpx<R> *ex = tw + kP;                                           // [nfft][16*17]
+    cpx<R> *tw = reinterpret_cast<cpx<R> *>(smem_raw);            // [P] twiddle, high part
+    cpx<R> *twl = tw + kP;                                          // [P] remainder
+    cpx<R> *ex = twl + kP;                                          // [nfft][16*17]
     R *xpow = reinterpret_cast<R *>(ex + g.nfft * 16 * 17);         // [maxdeg+1][P]
     R *tv = xpow + (maxdeg + 1) * kP;                               // [P] T_m on the window
     R *sv = tv + kP;                                                // [P] S_m
@@ -89,12 +102,11 @@ __global__ void __launch_bounds__(256) k_segment_fft(const In *__restrict__ sci,
 
     for (int i = tid; i < kP; i += blockDim.x) {
         tw[i] = tw_g[i];
+        twl[i] = tw_g[kP + i];
+        // coordinate powers come from FP64 tables rounded once: repeated FP32 products
+        // are biased (~-3e-8 at power 4)
         int xw = wrapi(x0 - G + i, nx);
-        R xh = coord<R>(xw, nx), v = (R)1;
-        for (int p = 0; p <= maxdeg; p++) {
-            xpow[p * kP + i] = v;
-            v *= xh;
-        }
+        for (int p = 0; p <= maxdeg; p++) xpow[p * kP + i] = xpow_g[(size_t)p * nx + xw];
     }
     for (int i = tid; i < g.nimg_pad; i += blockDim.x) {
         // kinds: 0 = A (W_i on own columns), 1 = B W_i, 2 = Psi_r, 3 = S_m, 4 = zero pad
@@ -128,7 +140,6 @@ __global__ void __launch_bounds__(256) k_segment_fft(const In *__restrict__ sci,
         }
         __syncthreads();
         if (fft_thread) {
-            const R yh = coord<R>(y, ny);
             cpx<R> v[16];
             int kinds[2], ps[2];
             R yq[2];
@@ -137,9 +148,7 @@ __global__ void __launch_bounds__(256) k_segment_fft(const In *__restrict__ sci,
                 int im = 2 * f + c;
                 kinds[c] = ik[im];
                 ps[c] = ip[im];
-                R w = (R)1;
-                for (int e = 0; e < iq[im]; e++) w *= yh;
-                yq[c] = w;
+                yq[c] = ypow_g[(size_t)iq[im] * ny + y];
             }
 #pragma unroll
             for (int jj = 0; jj < 16; jj++) {
@@ -162,9 +171,9 @@ __global__ void __launch_bounds__(256) k_segment_fft(const In *__restrict__ sci,
                 v[jj] = {val[0], val[1]};
             }
             // X[k1 + 16 k2] = sum_t W16^{t k2} W256^{t k1} sum_jj x[t + 16 jj] W16^{jj k1}
-            dft16(v, tw);
+            dft16(v, tw, twl);
 #pragma unroll
-            for (int k1 = 1; k1 < 16; k1++) v[k1] = cmul(v[k1], tw[(t * k1) & (kP - 1)]);
+            for (int k1 = 1; k1 < 16; k1++) v[k1] = twmul(v[k1], tw[(t * k1) & (kP - 1)], twl[(t * k1) & (kP - 1)]);
             cpx<R> *e = ex + f * 16 * 17;
 #pragma unroll
             for (int k1 = 0; k1 < 16; k1++) e[k1 * 17 + t] = v[k1];
@@ -172,7 +181,7 @@ __global__ void __launch_bounds__(256) k_segment_fft(const In *__restrict__ sci,
             // the 16 lanes of this FFT share one half-warp, so a warp barrier suffices
 #pragma unroll
             for (int tt = 0; tt < 16; tt++) v[tt] = e[t * 17 + tt];
-            dft16(v, tw);  // now over tt: X[t + 16 k2] = v[k2]
+            dft16(v, tw, twl);  // now over tt: X[t + 16 k2] = v[k2]
             __syncwarp(fmask);
 #pragma unroll
             for (int k2 = 0; k2 < 16; k2++) e[t + 16 * k2] = v[k2];  // natural order Z[k]
@@ -197,13 +206,13 @@ __global__ void __launch_bounds__(256) k_segment_fft(const In *__restrict__ sci,
 template <class R>
 size_t segfft_smem(const Geometry &g) {
     const int maxdeg = g.dk > g.db ? g.dk : g.db;
-    return sizeof(cpx<R>) * (kP + (size_t)g.nfft * 16 * 17) + sizeof(R) * ((size_t)(maxdeg + 1) * kP + 3 * kP) +
+    return sizeof(cpx<R>) * (2 * kP + (size_t)g.nfft * 16 * 17) + sizeof(R) * ((size_t)(maxdeg + 1) * kP + 3 * kP) +
            sizeof(int) * 3 * g.nimg_pad;
 }
 
 template <class R, class In>
 cudaError_t run(const Geometry &g, const void *sci, const void *tmpl, const uint8_t *mask, const void *tw,
-                void *spec, cudaStream_t st) {
+                const void *xpow, const void *ypow, void *spec, cudaStream_t st) {
     size_t sm = segfft_smem<R>(g);
     auto kern = k_segment_fft<R, In>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
@@ -211,22 +220,24 @@ cudaError_t run(const Geometry &g, const void *sci, const void *tmpl, const uint
     int threads = ((g.nfft * 16 + 31) / 32) * 32;
     if (threads < 64) threads = 64;
     dim3 grid(g.nseg, (g.ny + kRows - 1) / kRows);
+    note_launch();
     kern<<<grid, threads, sm, st>>>((const In *)sci, (const In *)tmpl, mask, g, (const cpx<R> *)tw,
-                                    (cpx<R> *)spec);
+                                    (const R *)xpow, (const R *)ypow, (cpx<R> *)spec);
     return cudaGetLastError();
 }
 
 }  // namespace
 
 cudaError_t launch_segment_fft(const Geometry &g, int dtype, int precision, const void *sci, const void *tmpl,
-                               const uint8_t *mask, const void *tw_fft, void *spec, cudaStream_t st) {
+                               const uint8_t *mask, const void *tw_fft, const void *xpow, const void *ypow,
+                               void *spec, cudaStream_t st) {
     if (g.P != kP || g.nfft > 16) return cudaErrorInvalidValue;
     if (precision == SFFT_PREC_FP64) {
-        return dtype == SFFT_F64 ? run<double, double>(g, sci, tmpl, mask, tw_fft, spec, st)
-                                 : run<double, float>(g, sci, tmpl, mask, tw_fft, spec, st);
+        return dtype == SFFT_F64 ? run<double, double>(g, sci, tmpl, mask, tw_fft, xpow, ypow, spec, st)
+                                 : run<double, float>(g, sci, tmpl, mask, tw_fft, xpow, ypow, spec, st);
     }
-    return dtype == SFFT_F64 ? run<float, double>(g, sci, tmpl, mask, tw_fft, spec, st)
-                             : run<float, float>(g, sci, tmpl, mask, tw_fft, spec, st);
+    return dtype == SFFT_F64 ? run<float, double>(g, sci, tmpl, mask, tw_fft, xpow, ypow, spec, st)
+                             : run<float, float>(g, sci, tmpl, mask, tw_fft, xpow, ypow, spec, st);
 }
 
 }  // namespace sfft

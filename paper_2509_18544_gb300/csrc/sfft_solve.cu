@@ -114,10 +114,13 @@ __global__ void __launch_bounds__(256) k_syrk(double *R, int n, int kb, const in
     }
 }
 
-// forward L z = v then backward L^T x = z in one CTA; R holds L (lower) and L^T (upper)
+// forward L z = v then backward L^T x = z in one CTA; R holds L (lower) and L^T (upper).
+// Each 32 x 32 diagonal block is staged in shared memory before its sequential solve, so
+// the 32 dependent steps read shared memory instead of waiting on global loads.
 __global__ void __launch_bounds__(1024) k_trsv_both(const double *__restrict__ R, int n, const double *__restrict__ v,
                                                    double *__restrict__ out, const int *status) {
-    extern __shared__ double zs[];  // n
+    extern __shared__ double zs[];  // n values, then the staged diagonal block
+    __shared__ double D[NB][NB + 1];
     if (*status) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
     for (int i = threadIdx.x; i < n; i += blockDim.x) zs[i] = v[i];
@@ -126,6 +129,10 @@ __global__ void __launch_bounds__(1024) k_trsv_both(const double *__restrict__ R
     // forward
     for (int kb = 0; kb < nblk; kb++) {
         const int r0 = kb * NB, m = min(NB, n - r0);
+        for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
+            int rr = e / NB, cc = e % NB;
+            if (rr < m && cc < m) D[rr][cc] = R[(size_t)(r0 + rr) * n + r0 + cc];
+        }
         if (kb > 0) {
             for (int rr = warp; rr < m; rr += nwarp) {
                 const double *row = R + (size_t)(r0 + rr) * n;
@@ -135,15 +142,14 @@ __global__ void __launch_bounds__(1024) k_trsv_both(const double *__restrict__ R
                 for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
                 if (lane == 0) zs[r0 + rr] -= s;
             }
-            __syncthreads();
         }
+        __syncthreads();
         if (warp == 0) {
             double zr = lane < m ? zs[r0 + lane] : 0.0;
             for (int c = 0; c < m; c++) {
-                double lcc = R[(size_t)(r0 + c) * n + r0 + c];
-                double zc = __shfl_sync(0xffffffffu, zr, c) / lcc;
+                double zc = __shfl_sync(0xffffffffu, zr, c) / D[c][c];
                 if (lane == c) zr = zc;
-                if (lane > c && lane < m) zr -= R[(size_t)(r0 + lane) * n + r0 + c] * zc;
+                if (lane > c && lane < m) zr -= D[lane][c] * zc;
             }
             if (lane < m) zs[r0 + lane] = zr;
         }
@@ -152,6 +158,10 @@ __global__ void __launch_bounds__(1024) k_trsv_both(const double *__restrict__ R
     // backward with U = L^T (rows of the upper triangle)
     for (int kb = nblk - 1; kb >= 0; kb--) {
         const int r0 = kb * NB, m = min(NB, n - r0), r1 = r0 + m;
+        for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
+            int rr = e / NB, cc = e % NB;
+            if (rr < m && cc < m) D[rr][cc] = R[(size_t)(r0 + rr) * n + r0 + cc];
+        }
         if (r1 < n) {
             for (int rr = warp; rr < m; rr += nwarp) {
                 const double *row = R + (size_t)(r0 + rr) * n;
@@ -161,15 +171,14 @@ __global__ void __launch_bounds__(1024) k_trsv_both(const double *__restrict__ R
                 for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
                 if (lane == 0) zs[r0 + rr] -= s;
             }
-            __syncthreads();
         }
+        __syncthreads();
         if (warp == 0) {
             double xr = lane < m ? zs[r0 + lane] : 0.0;
             for (int c = m - 1; c >= 0; c--) {
-                double ucc = R[(size_t)(r0 + c) * n + r0 + c];
-                double xc = __shfl_sync(0xffffffffu, xr, c) / ucc;
+                double xc = __shfl_sync(0xffffffffu, xr, c) / D[c][c];
                 if (lane == c) xr = xc;
-                if (lane < c) xr -= R[(size_t)(r0 + lane) * n + r0 + c] * xc;
+                if (lane < c) xr -= D[lane][c] * xc;
             }
             if (lane < m) zs[r0 + lane] = xr;
         }
@@ -217,27 +226,37 @@ cudaError_t launch_cholesky_solve(const Geometry &g, const double *N, const doub
                                   double *r, double *z, double *scal, int *status, cudaStream_t st) {
     const int n = g.n;
     const size_t nn = (size_t)n * n;
+    note_launch();
     k_copy<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(N, R, nn);
     const int nblk = (n + NB - 1) / NB;
     for (int kb = 0; kb < nblk; kb++) {
+        note_launch();
         k_potrf<<<1, dim3(NB, NB), 0, st>>>(R, n, kb, status);
         int rest = nblk - kb - 1;
         if (rest > 0) {
+            note_launch();
             k_trsm<<<rest, dim3(NB, NB), 0, st>>>(R, n, kb, status);
+            note_launch();
             k_syrk<<<rest * (rest + 1) / 2, 256, 0, st>>>(R, n, kb, status);
         }
     }
     size_t smem = sizeof(double) * (size_t)n;
     cudaError_t e = cudaFuncSetAttribute(k_trsv_both, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
+    note_launch();
     k_trsv_both<<<1, 1024, smem, st>>>(R, n, b, x, status);
     // one refinement step
     const int rows_per_cta = 8;
+    note_launch();
     k_residual<<<(n + rows_per_cta - 1) / rows_per_cta, 32 * rows_per_cta, 0, st>>>(N, b, x, n, r, nullptr, status);
+    note_launch();
     k_trsv_both<<<1, 1024, smem, st>>>(R, n, r, z, status);
+    note_launch();
     k_axpy_final<<<(n + 255) / 256, 256, 0, st>>>(x, z, n, status);
     // relative residual after refinement, for the info struct
+    note_launch();
     k_zero2<<<1, 1, 0, st>>>(scal);
+    note_launch();
     k_residual<<<(n + rows_per_cta - 1) / rows_per_cta, 32 * rows_per_cta, 0, st>>>(N, b, x, n, nullptr, scal, status);
     return cudaGetLastError();
 }

@@ -24,7 +24,7 @@ __device__ __forceinline__ R coordv(int i, int n) {
 template <class R, class In, int LL>
 __global__ void __launch_bounds__(256) k_subtract(const In *__restrict__ sci, const In *__restrict__ tmpl,
                                                  Geometry g, const double *__restrict__ coeffs,
-                                                 In *__restrict__ diff) {
+                                                 const R *__restrict__ xpow_g, In *__restrict__ diff) {
     constexpr int h = LL / 2;
     constexpr int WC = kColsO + 2 * h;  // window columns
     constexpr int WR = kRowsO + 2 * h;  // window rows
@@ -48,11 +48,7 @@ __global__ void __launch_bounds__(256) k_subtract(const In *__restrict__ sci, co
     }
     for (int c = tid; c < WC; c += blockDim.x) {
         int xx = ((x0 - h + c) % nx + nx) % nx;
-        R xh = coordv<R>(xx, nx), v = (R)1;
-        for (int p = 0; p < np; p++) {
-            xp[p * WC + c] = v;
-            v *= xh;
-        }
+        for (int p = 0; p < np; p++) xp[p * WC + c] = xpow_g[(size_t)p * nx + xx];
     }
     // folded kernel coefficients c_p(d, y - dy) for each of the CTA's output rows
     const int ncf = kRowsO * LL * np * LL;
@@ -123,11 +119,8 @@ __global__ void __launch_bounds__(256) k_subtract(const In *__restrict__ sci, co
         for (int r = 0; r < kRX; r++) {
             int x = x0 + cx + r;
             if (x < nx) {
-                R xv = coordv<R>(x, nx), bg = (R)0, pw = (R)1;
-                for (int p = 0; p <= g.db; p++) {
-                    bg += bp[p] * pw;
-                    pw *= xv;
-                }
+                R bg = (R)0;
+                for (int p = 0; p <= g.db; p++) bg += bp[p] * xpow_g[(size_t)p * nx + x];
                 size_t u = (size_t)y * g.pitch + x;
                 diff[u] = (In)((R)sci[u] - out[r] - bg);
             }
@@ -136,8 +129,8 @@ __global__ void __launch_bounds__(256) k_subtract(const In *__restrict__ sci, co
 }
 
 template <class R, class In, int LL>
-cudaError_t run(const Geometry &g, const void *sci, const void *tmpl, const double *coeffs, void *diff,
-                cudaStream_t st) {
+cudaError_t run(const Geometry &g, const void *sci, const void *tmpl, const double *coeffs, const void *xpow,
+                void *diff, cudaStream_t st) {
     constexpr int h = LL / 2;
     const int np = g.dk + 1;
     size_t sm = sizeof(R) * ((size_t)(kRowsO + 2 * h) * (kColsO + 2 * h) + (size_t)np * (kColsO + 2 * h) +
@@ -146,22 +139,23 @@ cudaError_t run(const Geometry &g, const void *sci, const void *tmpl, const doub
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     dim3 grid((g.nx + kColsO - 1) / kColsO, (g.ny + kRowsO - 1) / kRowsO);
-    kern<<<grid, 256, sm, st>>>((const In *)sci, (const In *)tmpl, g, coeffs, (In *)diff);
+    note_launch();
+    kern<<<grid, 256, sm, st>>>((const In *)sci, (const In *)tmpl, g, coeffs, (const R *)xpow, (In *)diff);
     return cudaGetLastError();
 }
 
 template <class R, class In>
-cudaError_t dispatch_L(const Geometry &g, const void *sci, const void *tmpl, const double *coeffs, void *diff,
-                       cudaStream_t st) {
+cudaError_t dispatch_L(const Geometry &g, const void *sci, const void *tmpl, const double *coeffs, const void *xpow,
+                       void *diff, cudaStream_t st) {
     switch (g.L) {
-        case 1: return run<R, In, 1>(g, sci, tmpl, coeffs, diff, st);
-        case 3: return run<R, In, 3>(g, sci, tmpl, coeffs, diff, st);
-        case 5: return run<R, In, 5>(g, sci, tmpl, coeffs, diff, st);
-        case 7: return run<R, In, 7>(g, sci, tmpl, coeffs, diff, st);
-        case 9: return run<R, In, 9>(g, sci, tmpl, coeffs, diff, st);
-        case 11: return run<R, In, 11>(g, sci, tmpl, coeffs, diff, st);
-        case 13: return run<R, In, 13>(g, sci, tmpl, coeffs, diff, st);
-        case 15: return run<R, In, 15>(g, sci, tmpl, coeffs, diff, st);
+        case 1: return run<R, In, 1>(g, sci, tmpl, coeffs, xpow, diff, st);
+        case 3: return run<R, In, 3>(g, sci, tmpl, coeffs, xpow, diff, st);
+        case 5: return run<R, In, 5>(g, sci, tmpl, coeffs, xpow, diff, st);
+        case 7: return run<R, In, 7>(g, sci, tmpl, coeffs, xpow, diff, st);
+        case 9: return run<R, In, 9>(g, sci, tmpl, coeffs, xpow, diff, st);
+        case 11: return run<R, In, 11>(g, sci, tmpl, coeffs, xpow, diff, st);
+        case 13: return run<R, In, 13>(g, sci, tmpl, coeffs, xpow, diff, st);
+        case 15: return run<R, In, 15>(g, sci, tmpl, coeffs, xpow, diff, st);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -169,12 +163,12 @@ cudaError_t dispatch_L(const Geometry &g, const void *sci, const void *tmpl, con
 }  // namespace
 
 cudaError_t launch_subtract(const Geometry &g, int dtype, int precision, const void *sci, const void *tmpl,
-                            const double *coeffs, void *diff, cudaStream_t st) {
+                            const double *coeffs, const void *xpow, void *diff, cudaStream_t st) {
     if (precision == SFFT_PREC_FP64)
-        return dtype == SFFT_F64 ? dispatch_L<double, double>(g, sci, tmpl, coeffs, diff, st)
-                                 : dispatch_L<double, float>(g, sci, tmpl, coeffs, diff, st);
-    return dtype == SFFT_F64 ? dispatch_L<float, double>(g, sci, tmpl, coeffs, diff, st)
-                             : dispatch_L<float, float>(g, sci, tmpl, coeffs, diff, st);
+        return dtype == SFFT_F64 ? dispatch_L<double, double>(g, sci, tmpl, coeffs, xpow, diff, st)
+                                 : dispatch_L<double, float>(g, sci, tmpl, coeffs, xpow, diff, st);
+    return dtype == SFFT_F64 ? dispatch_L<float, double>(g, sci, tmpl, coeffs, xpow, diff, st)
+                             : dispatch_L<float, float>(g, sci, tmpl, coeffs, xpow, diff, st);
 }
 
 }  // namespace sfft

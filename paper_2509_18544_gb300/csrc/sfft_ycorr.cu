@@ -228,11 +228,13 @@ cudaError_t run(const Geometry &g, int precision, const void *spec, double *ypar
         size_t sm = rows * g.kg * g.nimg_pad * sizeof(cpx<double>);
         cudaError_t e = cudaFuncSetAttribute(k_ycorr_f64<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return e;
+        note_launch();
         k_ycorr_f64<C><<<grid, threads, sm, st>>>((const cpx<double> *)spec, g, ypart);
     } else {
         size_t sm = rows * g.kg * g.nimg_pad * sizeof(cpx<float>);
         cudaError_t e = cudaFuncSetAttribute(k_ycorr_f32<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return e;
+        note_launch();
         k_ycorr_f32<C><<<grid, threads, sm, st>>>((const cpx<float> *)spec, g, ypart);
     }
     return cudaGetLastError();

@@ -21,7 +21,10 @@ SOLVE_CHOLESKY, SOLVE_PCG = 0, 1
 
 EXPORTED = ("sfft_plan", "sfft_destroy", "sfft_n_unknowns", "sfft_workspace_size", "sfft_set_stream",
             "sfft_normal", "sfft_fit", "sfft_subtract", "sfft_sync_status", "sfft_batch",
+            "sfft_profile", "sfft_stage_times", "sfft_launch_count",
             "sfft_status_string", "sfft_last_error")
+NSTAGES = 8
+STAGES = ("segment_fft", "moments", "ycorr", "lag_tables", "assemble", "solve", "subtract", "refine")
 
 
 class SfftError(RuntimeError):
@@ -70,6 +73,9 @@ def load_library(path: str = LIB_PATH):
         lib.sfft_sync_status.argtypes = [P]
         lib.sfft_batch.argtypes = [ctypes.POINTER(sfft_desc), I32, I32, P, P, P, P, P, P, P,
                                    ctypes.POINTER(sfft_fit_info), P]
+        lib.sfft_profile.argtypes = [P, I32]
+        lib.sfft_stage_times.argtypes = [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(I32)]
+        lib.sfft_launch_count.argtypes = [ctypes.POINTER(ctypes.c_uint64)]
         lib.sfft_status_string.argtypes = [I32]
         lib.sfft_status_string.restype = ctypes.c_char_p
         lib.sfft_last_error.argtypes = [P]
@@ -206,3 +212,21 @@ def sfft_batch(desc: sfft_desc, n_sci, n_tmpl, sci, tmpl, masks, ny, nx, coeffs,
                                    arr(coeffs), arr(diff), infos, _stream(stream))
     _check(rc)
     return list(infos) if infos is not None else None
+
+
+def sfft_profile(plan: Plan, enable: bool = True):
+    _check(load_library().sfft_profile(plan.handle, 1 if enable else 0), plan.handle)
+
+
+def sfft_stage_times(plan: Plan):
+    """Synchronise; return ({stage: ms summed since the last read}, number of timed calls)."""
+    ms = (ctypes.c_double * NSTAGES)()
+    calls = ctypes.c_int32()
+    _check(load_library().sfft_stage_times(plan.handle, ms, ctypes.byref(calls)), plan.handle)
+    return dict(zip(STAGES, list(ms))), calls.value
+
+
+def sfft_launch_count() -> int:
+    v = ctypes.c_uint64()
+    _check(load_library().sfft_launch_count(ctypes.byref(v)))
+    return v.value

@@ -127,18 +127,22 @@ def test_fp64_path_matches_oracle_tightly(ny, nx, L, dk, db, masked, dtype):
     th, D, _ = gpu_fit_subtract(S, T, M, L, dk, db, precision=sfft.PREC_FP64)
     assert np.linalg.norm(th - th_ref) <= 1e-10 * np.linalg.norm(th_ref)
     D_ref = oracle.subtract(S, T, th_ref, L, dk, db)
-    assert np.abs(D - D_ref).max() <= 1e-10 * np.abs(T).max()
+    # float32 frames carry a float32 difference image: allow its output rounding
+    out_ulp = np.finfo(dtype).eps * np.abs(D_ref).max()
+    assert np.abs(D - D_ref).max() <= 1e-10 * np.abs(T).max() + out_ulp
 
 
 def test_small_float64_pair_workload():
-    """64 x 64 float64 pair, fixed 5 x 5 kernel, L=5, DK=0, DB=0 (26 unknowns)."""
+    """64 x 64 float64 pair, fixed 5 x 5 kernel, L=5, DK=0, DB=0 (26 unknowns), FP64 path.
+    The template keeps its sky of 100, so the constant background and the kernel sum are
+    nearly collinear (cond(N) ~ 4e6): this workload needs the FP64 arithmetic mode."""
     S, T, k, bg = synth.gaussian_pair(seed=0)
     th_ref = oracle.fit(S, T, None, 5, 0, 0)
-    th, D, info = gpu_fit_subtract(S, T, None, 5, 0, 0)
+    th, D, info = gpu_fit_subtract(S, T, None, 5, 0, 0, precision=sfft.PREC_FP64)
     assert info.n == 26
-    assert np.linalg.norm(th - th_ref) <= 1e-6 * np.linalg.norm(th_ref)
+    assert np.linalg.norm(th - th_ref) <= 1e-8 * np.linalg.norm(th_ref)
     D_ref = oracle.subtract(S, T, th_ref, 5, 0, 0)
-    assert np.abs(D - D_ref).max() <= 1e-5 * np.abs(T).max()
+    assert np.abs(D - D_ref).max() <= 1e-9 * np.abs(T).max()
 
 
 def test_exact_recovery_through_gpu():
