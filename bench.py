@@ -41,6 +41,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--pairs", type=int, default=4, help="pairs per step per rank")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--solver", default="cholesky", choices=["cholesky", "pcg"])
     return ap.parse_args()
 
 
@@ -129,7 +130,8 @@ def run_ours(args, world, rank, local):
         pairs.append((S, T, M))
     dev_pairs = [tuple(torch.from_numpy(a).to(dev) for a in p) for p in pairs]
     stream = torch.cuda.current_stream(dev)
-    plan = sfft.sfft_plan(sfft.make_desc(NY, NX, L, DK, DB), stream=stream)
+    solver = sfft.SOLVE_PCG if args.solver == "pcg" else sfft.SOLVE_CHOLESKY
+    plan = sfft.sfft_plan(sfft.make_desc(NY, NX, L, DK, DB, solver=solver), stream=stream)
     n = plan.n
     coeffs = [torch.empty(n, dtype=torch.float64, device=dev) for _ in pairs]
     diffs = [torch.empty((NY, NX), dtype=torch.float32, device=dev) for _ in pairs]
@@ -243,7 +245,9 @@ def run_ours(args, world, rank, local):
         "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 3), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "frame": "%dx%d" % (NY, NX), "L": L, "dk": DK, "db": DB,
-                   "pairs_per_step_per_rank": args.pairs, "mode": "plain (FP32 spectra, FP64 Cholesky)",
+                   "pairs_per_step_per_rank": args.pairs,
+                   "mode": "plain (FP32 spectra, FP64 Cholesky)" if args.solver == "cholesky"
+                   else "FP32 spectra, cluster PCG (FP32 Cholesky preconditioner, FP64 residuals)",
                    "l2": "inputs larger than L2 (150 MB frames + 1.5 GB spectra per pair); no flush",
                    "parallelism": "replicas: independent pairs per GPU" if world > 1 else "1 GPU"},
         "roofline": roofline,

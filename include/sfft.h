@@ -77,7 +77,12 @@ typedef struct {
     double tol;            /* PCG relative-residual tolerance (0 = default 1e-12) */
     size_t workspace_cap;  /* bytes the plan may allocate; 0 = no cap */
     int32_t seg;           /* row-segment FFT length P (0 = default 256); P >= 2(L-1)+1 */
-    int32_t reserved[7];   /* zero */
+    int32_t refine;        /* residual refinement passes after the solve: 0 = default (1 for
+                              SFFT_PREC_FP32, none for SFFT_PREC_FP64), < 0 = none, > 0 = count.
+                              A pass forms the residual image of the fit on the masked frames,
+                              correlates it with the basis through the same segment spectra,
+                              and corrects theta with the existing factorisation. */
+    int32_t reserved[6];   /* zero */
 } sfft_desc;
 
 typedef struct {

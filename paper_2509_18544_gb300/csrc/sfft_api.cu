@@ -80,22 +80,42 @@ bool make_geometry(const sfft_desc &d, Geometry &g, char *err, size_t errlen) {
     if (g.items_per_k > 256) return snprintf(err, errlen, "dk=%d, db=%d need %d work items per frequency (max 256)", d.dk, d.db, g.items_per_k), false;
     g.ytile = 64;
     {
+        // frequencies per CTA: as many items as fit 256 threads, and two double-buffered
+        // tiles within the shared-memory budget (two CTAs per SM for FP32 spectra)
         const size_t cpx_sz = d.precision == SFFT_PREC_FP64 ? 16 : 8;
-        const size_t row_bytes = (size_t)(g.ytile + 2 * g.G) * g.nimg_pad * cpx_sz;
-        int kg = 256 / g.items_per_k;
-        int kg_smem = (int)((96 * 1024) / row_bytes);
-        if (kg > kg_smem) kg = kg_smem;
-        if (kg > g.nkf) kg = g.nkf;
-        if (kg < 1) kg = 1;
-        g.kg = kg;
+        const size_t per_k = 2 * (size_t)(g.ytile + 2 * g.G) * g.nimg_pad * cpx_sz;
+        const size_t per_k_ws = 2 * (size_t)(g.ytile + 2 * g.G) * (((g.nk + 1) & ~1) + 2) * cpx_sz;
+        const size_t budget = d.precision == SFFT_PREC_FP64 ? 200 * 1024 : 112 * 1024;
+        auto pick = [&](int items, size_t pk) {
+            int kg = 256 / items;
+            int kg_smem = (int)(budget / pk);
+            if (kg > kg_smem) kg = kg_smem;
+            if (kg > g.nkf) kg = g.nkf;
+            return kg < 1 ? 1 : kg;
+        };
+        g.kg = pick(g.items_per_k, per_k);
+        g.kg_ws = pick(g.nk, per_k_ws);
+        if (per_k > budget) return snprintf(err, errlen, "y-correlation tile does not fit shared memory"), false;
+        // row chunks so the grid covers several waves of 2 CTAs on each of 152 SMs
+        const int units = g.nseg * ((g.nkf + g.kg - 1) / g.kg);
+        int ys = (4 * 304 + units - 1) / units;
+        int max_ys = d.ny / (2 * g.ytile);
+        if (ys > max_ys) ys = max_ys;
+        g.ysplit = ys < 1 ? 1 : ys;
+        // refinement pass: one thread per (segment, chunk, frequency, W_i); ~200k threads
+        long per_chunk = (long)g.nseg * g.nkf * g.nk;
+        int yc = (int)((200000 + per_chunk - 1) / per_chunk);
+        int max_yc = d.ny / 32;
+        if (yc > max_yc) yc = max_yc;
+        g.ychunks_ws = yc < 1 ? 1 : yc;
     }
+    g.refine = d.refine < 0 ? 0 : (d.refine > 0 ? d.refine : (d.precision == SFFT_PREC_FP64 ? 0 : 1));
     if (d.db > 4) return snprintf(err, errlen, "db=%d > 4 not supported", d.db), false;
     g.mom_rows = 128;
     g.mom_ctas = ((d.nx + 255) / 256) * ((d.ny + g.mom_rows - 1) / g.mom_rows);
     g.nmom = npoly(2 * d.db) + npoly(d.db);
     g.pmax = d.dk > 2 * d.db ? d.dk : 2 * d.db;
     if (d.precision == SFFT_PREC_SPLIT) return snprintf(err, errlen, "split precision not built yet"), false;
-    if (d.solver == SFFT_SOLVE_PCG) return snprintf(err, errlen, "PCG solver not built yet"), false;
     return true;
 }
 
@@ -110,13 +130,20 @@ struct Carve {
     }
 };
 
-static size_t carve(const Geometry &g, int precision, void *base, Workspace *w) {
+static size_t carve(const Geometry &g, int precision, int dtype, void *base, Workspace *w) {
     Carve c;
+    const size_t dtype_size = dtype == SFFT_F64 ? 8 : 4;
     const size_t cpx_sz = precision == SFFT_PREC_FP64 ? 16 : 8;
     Workspace tmp;
     Workspace &o = w ? *w : tmp;
     o.spec = c.take<char>(base, (size_t)g.nseg * g.nkf * g.ny * g.nimg_pad * cpx_sz);
-    o.ypart = c.take<double>(base, (size_t)g.nseg * g.nkf * g.nent * 2);
+    {
+        // the y-correlation partials, or (refinement) the W x S_m partials: 16 bytes per value
+        size_t main_v = (size_t)g.nseg * g.ysplit * g.nkf * g.nent;
+        size_t ws_v = (size_t)g.nseg * g.ychunks_ws * g.nkf * g.nk * g.L;
+        o.ypart = c.take<double>(base, 2 * (main_v > ws_v ? main_v : ws_v));
+    }
+    o.resid = g.refine ? c.take<char>(base, (size_t)g.ny * g.pitch * (dtype_size)) : nullptr;
     o.ysum = c.take<double>(base, (size_t)g.nkf * g.nent * 2);
     o.lagww = c.take<double>(base, (size_t)g.npair * (2 * g.L - 1) * (2 * g.L - 1));
     o.lagwg = c.take<double>(base, (size_t)g.nk * g.nb * g.L * g.L);
@@ -131,8 +158,17 @@ static size_t carve(const Geometry &g, int precision, void *base, Workspace *w) 
     o.z = c.take<double>(base, (size_t)g.n);
     o.p = c.take<double>(base, (size_t)g.n);
     o.q = c.take<double>(base, (size_t)g.n);
+    o.b2 = c.take<double>(base, (size_t)g.n);
     o.scal = c.take<double>(base, 16);
+    o.dinv = c.take<double>(base, (size_t)g.n);
+    o.Rf = c.take<float>(base, (size_t)g.n * g.n);
+    o.dscale = c.take<double>(base, (size_t)g.n);
+    o.Lg = c.take<float>(base, pcg_factor_floats(g));
+    o.flags = c.take<int>(base, 16);
+    o.dinvf = c.take<float>(base, (size_t)g.n);
+    o.cfold = c.take<char>(base, (size_t)g.ny * g.L * (g.dk + 1) * g.L * (cpx_sz / 2) + (size_t)g.ny * (g.db + 1) * (cpx_sz / 2));
     o.status = c.take<int>(base, 16);
+    o.bar = c.take<unsigned>(base, 16);
     o.tw_fft = c.take<char>(base, (size_t)2 * g.P * cpx_sz);
     o.xpow = c.take<char>(base, (size_t)(g.pmax + 1) * g.nx * (cpx_sz / 2));
     o.ypow = c.take<char>(base, (size_t)(g.pmax + 1) * g.ny * (cpx_sz / 2));
@@ -140,7 +176,9 @@ static size_t carve(const Geometry &g, int precision, void *base, Workspace *w) 
     return align_up(c.off, 256);
 }
 
-size_t workspace_bytes(const Geometry &g, int precision) { return carve(g, precision, nullptr, nullptr); }
+size_t workspace_bytes(const Geometry &g, int precision, int dtype) {
+    return carve(g, precision, dtype, nullptr, nullptr);
+}
 
 static std::atomic<uint64_t> g_launches{0};
 void note_launch(int count) { g_launches.fetch_add((uint64_t)count, std::memory_order_relaxed); }
@@ -202,7 +240,7 @@ sfft_status sfft_workspace_size(const sfft_desc *desc, size_t *bytes) {
     Geometry g;
     char err[256];
     if (!make_geometry(*desc, g, err, sizeof err)) return set_err(nullptr, "%s", err), SFFT_ERR_INVALID_ARG;
-    *bytes = workspace_bytes(g, desc->precision);
+    *bytes = workspace_bytes(g, desc->precision, desc->dtype);
     return SFFT_OK;
 }
 
@@ -217,7 +255,7 @@ sfft_status sfft_plan(sfft_plan_t *plan, const sfft_desc *desc, sfft_stream_t st
         set_err(nullptr, "%s", err);
         return unsup ? SFFT_ERR_UNSUPPORTED : SFFT_ERR_INVALID_ARG;
     }
-    size_t bytes = workspace_bytes(g, desc->precision);
+    size_t bytes = workspace_bytes(g, desc->precision, desc->dtype);
     if (desc->workspace_cap && bytes > desc->workspace_cap) {
         set_err(nullptr, "workspace %zu bytes exceeds cap %zu", bytes, desc->workspace_cap);
         return SFFT_ERR_OOM;
@@ -241,7 +279,7 @@ sfft_status sfft_plan(sfft_plan_t *plan, const sfft_desc *desc, sfft_stream_t st
         return s;
     }
     p->ws.bytes = bytes;
-    carve(g, desc->precision, p->ws.base, &p->ws);
+    carve(g, desc->precision, desc->dtype, p->ws.base, &p->ws);
 
     // twiddles from FP64 trigonometry: forward FFT exp(-2 pi i m / P), and the x-direction
     // inverse-DFT weights w_k exp(+2 pi i k m / P) / P for m in [0, 2G], w_0 = w_{P/2} = 1, else 2
@@ -401,12 +439,13 @@ static sfft_status queue_normal(sfft_plan_t p, const void *sci, const void *tmpl
     if (e != cudaSuccess) return cuda_fail(p, e, "moments launch");
     {
         StageTimer t(p, ST_YCORR);
-        e = launch_ycorr(g, p->desc.precision, w.spec, w.ypart, st);
+        e = launch_ycorr(g, p->desc.precision, w.spec, w.ypart, false, st);
     }
     if (e != cudaSuccess) return cuda_fail(p, e, "y-correlation launch");
     {
         StageTimer t(p, ST_LAGS);
-        e = launch_lag_tables(g, w.ypart, w.ysum, w.tw_x, w.lagww, w.lagwg, w.lagws, w.mom_part, w.mom, st);
+        e = launch_lag_tables(g, w.ypart, w.ysum, w.tw_x, w.lagww, w.lagwg, w.lagws, w.mom_part, w.mom, false,
+                              p->desc.precision != SFFT_PREC_FP64, st);
     }
     if (e != cudaSuccess) return cuda_fail(p, e, "lag-table launch");
     {
@@ -415,6 +454,37 @@ static sfft_status queue_normal(sfft_plan_t p, const void *sci, const void *tmpl
     }
     if (e != cudaSuccess) return cuda_fail(p, e, "assembly launch");
     return SFFT_OK;
+}
+
+// One residual refinement pass: R = S_m - sum a (w T_m)(u - d) - m sum b w (the residual of
+// the fit on the masked frames), c = [Phi Psi]^T R through the same segment spectra (R is
+// transformed into the S_m slot; the W_i spectra of the main pass are still in place), then
+// theta += N^{-1} c with the existing Cholesky factor.
+static cudaError_t queue_refine(sfft_plan_t p, const void *sci, const void *tmpl, const uint8_t *mask,
+                                double *coeffs) {
+    const Geometry &g = p->g;
+    Workspace &w = p->ws;
+    cudaStream_t st = p->stream;
+    const int slot = 2 * g.nk + g.nb;
+    cudaError_t e = launch_subtract(g, p->desc.dtype, p->desc.precision, sci, tmpl, mask, true, coeffs, w.xpow,
+                                    w.ypow, w.cfold, w.resid, st);
+    if (e == cudaSuccess) e = launch_segment_fft_single(g, p->desc.dtype, p->desc.precision, w.resid, w.tw_fft, slot,
+                                                        w.spec, st);
+    if (e == cudaSuccess) e = launch_moments(g, p->desc.dtype, p->desc.precision, w.resid, mask, w.ypow, w.mom_part, st);
+    if (e == cudaSuccess) e = launch_ycorr(g, p->desc.precision, w.spec, w.ypart, true, st);
+    if (e == cudaSuccess)
+        e = launch_lag_tables(g, w.ypart, w.ysum, w.tw_x, w.lagww, w.lagwg, w.lagws, w.mom_part, w.mom, true,
+                              p->desc.precision != SFFT_PREC_FP64, st);
+    if (e == cudaSuccess) e = launch_refine_rhs(g, w.lagws, w.mom, w.q, st);
+    // correction x += N^{-1} c: with the cluster factor when the fast solver converged, else
+    // with the FP32 copy of the FP64 Cholesky factor (each launch checks the flag)
+    if (e == cudaSuccess && p->desc.solver == SFFT_SOLVE_PCG && pcg_cluster_size(g) > 0)
+        e = launch_pcg_cluster(g, w.N, w.q, nullptr, coeffs, w.r, w.p, w.b2, w.z, w.dscale, w.Lg, w.scal, w.flags,
+                               0, 0.0, true, st);
+    if (e == cudaSuccess)
+        e = launch_cholesky_solve(g, w.N, w.q, w.R, coeffs, w.r, w.z, w.scal, w.dinv, w.Rf, w.dinvf, w.bar, w.status,
+                                  false, p->desc.solver == SFFT_SOLVE_PCG ? w.flags : nullptr, st);
+    return e;
 }
 
 sfft_status sfft_normal(sfft_plan_t plan, const void *sci, const void *tmpl, const uint8_t *mask, double *N,
@@ -427,17 +497,20 @@ sfft_status sfft_normal(sfft_plan_t plan, const void *sci, const void *tmpl, con
 }
 
 static sfft_status read_status(sfft_plan_t p, sfft_fit_info *info) {
-    int st_h = 0;
+    int st_h = 0, fl[2] = {0, 0};
     double scal[2] = {0.0, 0.0};
     cudaError_t e = cudaMemcpyAsync(&st_h, p->ws.status, sizeof(int), cudaMemcpyDeviceToHost, p->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(scal, p->ws.scal, 2 * sizeof(double), cudaMemcpyDeviceToHost, p->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(fl, p->ws.flags, 2 * sizeof(int), cudaMemcpyDeviceToHost, p->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
     if (e != cudaSuccess) return cuda_fail(p, e, "status read-back");
     if (info) {
         memset(info, 0, sizeof *info);
         info->status = st_h;
         info->n = p->g.n;
-        info->iterations = 1;
+        const bool fast = p->desc.solver == SFFT_SOLVE_PCG;
+        info->iterations = fast && fl[0] ? fl[1] : 1;
+        info->fallback = fast && !fl[0] ? 1 : 0;
         info->rel_residual = scal[1] > 0 ? sqrt(scal[0] / scal[1]) : 0.0;
     }
     if (st_h != 0) {
@@ -461,7 +534,25 @@ sfft_status sfft_fit(sfft_plan_t plan, const void *sci, const void *tmpl, const 
     if (s != SFFT_OK) return s;
     {
         StageTimer t(plan, ST_SOLVE);
-        e = launch_cholesky_solve(plan->g, w.N, w.b, w.R, coeffs, w.r, w.z, w.scal, w.status, plan->stream);
+        const bool fast = plan->desc.solver == SFFT_SOLVE_PCG;
+        e = cudaMemsetAsync(w.flags, 0, 2 * sizeof(int), plan->stream);
+        if (e == cudaSuccess && fast && pcg_cluster_size(plan->g) > 0) {
+            const int max_iter = plan->desc.max_iter > 0 ? plan->desc.max_iter : 50;
+            const double tol = plan->desc.tol > 0.0 ? plan->desc.tol : 1e-12;
+            e = launch_pcg_cluster(plan->g, w.N, w.b, x0, coeffs, w.r, w.p, w.q, w.z, w.dscale, w.Lg, w.scal, w.flags,
+                                   max_iter, tol, false, plan->stream);
+        }
+        // FP64 Cholesky: the plain solver, or the fallback when PCG did not converge
+        if (e == cudaSuccess) e = cudaMemsetAsync(w.bar, 0, 2 * sizeof(unsigned), plan->stream);
+        if (e == cudaSuccess)
+            e = launch_cholesky_solve(plan->g, w.N, w.b, w.R, coeffs, w.r, w.z, w.scal, w.dinv, w.Rf, w.dinvf, w.bar,
+                                      w.status, true, fast ? w.flags : nullptr, plan->stream);
+    }
+    if (e != cudaSuccess) return cuda_fail(plan, e, "solver launch");
+    for (int pass = 0; pass < plan->g.refine; pass++) {
+        StageTimer t(plan, ST_REFINE);
+        e = queue_refine(plan, sci, tmpl, mask, coeffs);
+        if (e != cudaSuccess) return cuda_fail(plan, e, "refinement launch");
     }
     if (e != cudaSuccess) return cuda_fail(plan, e, "solver launch");
     if (info) return read_status(plan, info);
@@ -476,8 +567,8 @@ sfft_status sfft_subtract(sfft_plan_t plan, const void *sci, const void *tmpl, c
     cudaError_t e;
     {
         StageTimer t(plan, ST_SUBTRACT);
-        e = launch_subtract(plan->g, plan->desc.dtype, plan->desc.precision, sci, tmpl, coeffs, plan->ws.xpow, diff,
-                            plan->stream);
+        e = launch_subtract(plan->g, plan->desc.dtype, plan->desc.precision, sci, tmpl, nullptr, false, coeffs,
+                            plan->ws.xpow, plan->ws.ypow, plan->ws.cfold, diff, plan->stream);
     }
     if (e != cudaSuccess) return cuda_fail(plan, e, "subtract launch");
     return SFFT_OK;

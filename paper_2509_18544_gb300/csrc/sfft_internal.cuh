@@ -49,7 +49,11 @@ struct Geometry {
     int nimg, nimg_pad, nfft;  // real images per segment row (A then B), padded to even, complex FFTs
     int npair, nent;           // W-W pairs (i <= j), (pair, dy) entries per frequency
     int C, items_per_k, kg;    // y-correlation: dy chunk, work items per frequency, frequencies per CTA
+    int kg_ws;                 // frequencies per CTA when only the W x S_m items run (refinement)
     int ytile;                 // y-correlation rows per staged tile
+    int ysplit;                // y-correlation row chunks (partial sums per chunk)
+    int ychunks_ws;            // row chunks of the refinement (W x S_m) correlation pass
+    int refine;                // residual refinement passes after the solve
     int mom_rows, mom_ctas;    // background-moment reduction geometry
     int nmom;                  // moments: npoly(2 db) mask moments + npoly(db) science moments
     int pmax;                  // highest coordinate power tabulated: max(dk, 2 db)
@@ -61,8 +65,9 @@ bool make_geometry(const sfft_desc &d, Geometry &g, char *err, size_t errlen);
 struct Workspace {
     void *base = nullptr;
     size_t bytes = 0;
-    void *spec = nullptr;        // [nseg][nkf][ny][nimg_pad] complex (R)
-    double *ypart = nullptr;     // [nseg][nkf][nent] complex FP64 (re, im interleaved)
+    void *spec = nullptr;        // [nseg][ny][nkf][nimg_pad] complex (R)
+    double *ypart = nullptr;     // [nseg][ysplit][nkf][nent] complex FP64 (re, im interleaved)
+    void *resid = nullptr;       // [ny][nx] residual image of the refinement pass (input dtype)
     double *ysum = nullptr;      // [nkf][nent] complex FP64
     double *lagww = nullptr;     // [npair][2L-1][2L-1]
     double *lagwg = nullptr;     // [nk][nb][L][L]
@@ -72,16 +77,24 @@ struct Workspace {
     double *N = nullptr;         // [n][n]
     double *b = nullptr;         // [n]
     double *R = nullptr;         // [n][n] Cholesky factor (lower triangle used)
-    double *x = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr;  // [n] solver vectors
+    double *x = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr, *b2 = nullptr;  // [n] solver vectors
     double *scal = nullptr;      // [16] solver scalars
+    double *dinv = nullptr;      // [n] reciprocal diagonal of the Cholesky factor
+    float *Rf = nullptr;         // [n][n] FP32 copy of the factor (refinement corrections)
+    float *dinvf = nullptr;      // [n] FP32 reciprocal diagonal
+    double *dscale = nullptr;    // [n] Jacobi scaling diag(N)^{-1/2} of the fast solver
+    float *Lg = nullptr;         // packed FP32 factor tiles of the fast solver
+    int *flags = nullptr;        // fast solver: [0] converged, [1] iterations
+    void *cfold = nullptr;       // subtract: folded kernel coefficients [ny][L][dk+1][L] (R)
     int *status = nullptr;       // device status word(s)
+    unsigned *bar = nullptr;     // grid-barrier words of the cooperative solver [count, generation]
     void *tw_fft = nullptr;      // [2][P] complex (R): exp(-2 pi i m / P), high part then remainder
     void *xpow = nullptr;        // [pmax+1][nx] (R): xh^p, FP64 powers rounded once
     void *ypow = nullptr;        // [pmax+1][ny] (R): yh^q
     double *tw_x = nullptr;      // [nkf][2G+1] complex FP64: w_k exp(+2 pi i k m / P) / P
 };
 
-size_t workspace_bytes(const Geometry &g, int precision);
+size_t workspace_bytes(const Geometry &g, int precision, int dtype);
 
 // process-wide count of kernel launches (every launcher calls this before each launch)
 void note_launch(int count = 1);
@@ -116,24 +129,43 @@ cudaError_t launch_segment_fft(const Geometry &g, int dtype, int precision, cons
 // background moments (mask and masked science times monomials) -> mom_part
 cudaError_t launch_moments(const Geometry &g, int dtype, int precision, const void *sci,
                            const uint8_t *mask, const void *ypow, double *mom_part, cudaStream_t st);
+// K1 for one image (the refinement residual) written into image slot `slot` of spec
+cudaError_t launch_segment_fft_single(const Geometry &g, int dtype, int precision, const void *img,
+                                      const void *tw_fft, int slot, void *spec, cudaStream_t st);
 // K2: y-direction correlations at the kernel lags, per segment and frequency -> ypart
-cudaError_t launch_ycorr(const Geometry &g, int precision, const void *spec, double *ypart,
+// (ws_only: only the W x S_m items)
+cudaError_t launch_ycorr(const Geometry &g, int precision, const void *spec, double *ypart, bool ws_only,
                          cudaStream_t st);
-// K3: segment sum + x-direction inverse DFT at the kernel lags -> lag tables
+// K3: segment sum + x-direction inverse DFT at the kernel lags -> lag tables (ws_only: W x S_m only)
 cudaError_t launch_lag_tables(const Geometry &g, const double *ypart, double *ysum, const double *tw_x,
                               double *lagww, double *lagwg, double *lagws, const double *mom_part,
-                              double *mom, cudaStream_t st);
+                              double *mom, bool ws_only, bool pairs, cudaStream_t st);
+// refinement right-hand side c = [lagws ; science-moment part of mom]
+cudaError_t launch_refine_rhs(const Geometry &g, const double *lagws, const double *mom, double *c,
+                              cudaStream_t st);
 // K4: normal-matrix and right-hand-side assembly from the lag tables and moments
 cudaError_t launch_assemble(const Geometry &g, const double *lagww, const double *lagwg,
                             const double *lagws, const double *mom, double *N, double *b,
                             cudaStream_t st);
-// solve N x = b (FP64 Cholesky + one refinement step); writes status on failure
+// solve N x = b (FP64 Cholesky + one refinement step); writes status on failure.
+// factor == false: reuse the factor in R and update x += N^{-1} b instead.
+// skip (nullable): device flag; when it reads 1 every kernel of this solve returns at once
+// (the fast solver converged and this is its fallback)
 cudaError_t launch_cholesky_solve(const Geometry &g, const double *N, const double *b, double *R,
-                                  double *x, double *r, double *z, double *scal, int *status,
+                                  double *x, double *r, double *z, double *scal, double *dinv, float *Rf,
+                                  float *dinvf, unsigned *bar, int *status, bool factor, const int *skip,
                                   cudaStream_t st);
-// difference image
+// PCG preconditioned by an FP32 Cholesky factor held in one thread-block cluster; flags[0] = 1
+// on convergence.  correction: x += M^{-1} b with the stored factor (only if flags[0] == 1).
+int pcg_cluster_size(const Geometry &g);  // 0 when the fast solver cannot run this size
+size_t pcg_factor_floats(const Geometry &g);
+cudaError_t launch_pcg_cluster(const Geometry &g, const double *N, const double *b, const double *x0, double *x,
+                               double *r, double *p, double *q, double *z, double *d, float *Lg, double *scal,
+                               int *flags, int max_iter, double tol, bool correction, cudaStream_t st);
+// difference image (mask == nullptr), or with a mask the residual of the fit on the
+// masked frames: S_m - sum a (w T_m)(u - d) - m sum b w
 cudaError_t launch_subtract(const Geometry &g, int dtype, int precision, const void *sci,
-                            const void *tmpl, const double *coeffs, const void *xpow, void *diff,
-                            cudaStream_t st);
+                            const void *tmpl, const uint8_t *mask, bool residual, const double *coeffs,
+                            const void *xpow, const void *ypow, void *cfold, void *diff, cudaStream_t st);
 
 }  // namespace sfft

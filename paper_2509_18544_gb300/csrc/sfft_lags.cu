@@ -127,38 +127,72 @@ __global__ void __launch_bounds__(256) k_moments(const In *__restrict__ sci, con
     }
 }
 
-__global__ void k_mom_reduce(const double *__restrict__ part, int nparts, int nmom, double *__restrict__ mom) {
-    int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= nmom) return;
-    double s = 0.0, c = 0.0;  // Neumaier
-    for (int p = 0; p < nparts; p++) {
-        double v = part[(size_t)p * nmom + j];
-        double t = s + v;
-        c += fabs(s) >= fabs(v) ? (s - t) + v : (v - t) + s;
-        s = t;
+// one CTA per moment: strided partial sums, then a fixed-order tree (deterministic)
+__global__ void __launch_bounds__(256) k_mom_reduce(const double *__restrict__ part, int nparts, int nmom,
+                                                   double *__restrict__ mom) {
+    __shared__ double red[256];
+    const int j = blockIdx.x;
+    double s = 0.0;
+    for (int p = threadIdx.x; p < nparts; p += blockDim.x) s += part[(size_t)p * nmom + j];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
     }
-    mom[j] = s + c;
+    if (threadIdx.x == 0) mom[j] = red[0];
 }
 
-__global__ void k_ysum(const double2 *__restrict__ ypart, Geometry g, double2 *__restrict__ ysum) {
+// partial sums of the segments and row chunks: FP64 values (FP64 spectra) or (hi, lo)
+// float pairs (FP32 spectra), both 16 bytes per complex entry
+__global__ void k_ysum(const double2 *__restrict__ ypart, Geometry g, bool pairs, double2 *__restrict__ ysum) {
     size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     size_t total = (size_t)g.nkf * g.nent;
     if (idx >= total) return;
     double2 s = make_double2(0.0, 0.0);
-    for (int sg = 0; sg < g.nseg; sg++) {
-        double2 v = ypart[(size_t)sg * total + idx];
-        s.x += v.x;
-        s.y += v.y;
+    for (int sg = 0; sg < g.nseg * g.ysplit; sg++) {
+        if (pairs) {
+            float4 v = reinterpret_cast<const float4 *>(ypart)[(size_t)sg * total + idx];
+            s.x += (double)v.x + (double)v.z;
+            s.y += (double)v.y + (double)v.w;
+        } else {
+            double2 v = ypart[(size_t)sg * total + idx];
+            s.x += v.x;
+            s.y += v.y;
+        }
     }
     ysum[idx] = s;
 }
 
-__global__ void k_lagx(const double2 *__restrict__ ysum, const double2 *__restrict__ tw_x, Geometry g,
+// refinement pass: sum the W_i x S_m partials of every segment and row chunk into ysum
+__global__ void k_ysum_ws(const float4 *__restrict__ wspart, Geometry g, double2 *__restrict__ ysum) {
+    const int L = g.L;
+    size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;  // (k, i, c)
+    size_t per = (size_t)g.nkf * g.nk * L;
+    if (idx >= per) return;
+    const int c = (int)(idx % L), i = (int)((idx / L) % g.nk), k = (int)(idx / ((size_t)L * g.nk));
+    double2 s = make_double2(0.0, 0.0);
+    for (int sy = 0; sy < g.nseg * g.ychunks_ws; sy++) {
+        float4 v = wspart[(size_t)sy * per + idx];
+        s.x += (double)v.x + (double)v.z;
+        s.y += (double)v.y + (double)v.w;
+    }
+    const int ent = g.npair * (2 * L - 1) + (i * (g.nb + 1) + g.nb) * L + c;
+    ysum[(size_t)k * g.nent + ent] = s;
+}
+
+__global__ void k_lagx(const double2 *__restrict__ ysum, const double2 *__restrict__ tw_x, Geometry g, bool ws_only,
                        double *__restrict__ lagww, double *__restrict__ lagwg, double *__restrict__ lagws) {
     const int L = g.L, h = g.h, Lw = 2 * L - 1, G = g.G;
     const int nww = g.npair * Lw * Lw;
     const int nrest = g.nk * (g.nb + 1) * L * L;
     int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (ws_only) {
+        // thread -> (i, dyi, dxi) of the W_i x S_m table, mapped into the full numbering
+        if (t >= g.nk * L * L) return;
+        int i = t / (L * L), l = t - i * L * L;
+        t = nww + ((i * (g.nb + 1) + g.nb) * L * L) + l;
+    }
     if (t >= nww + nrest) return;
     int ent, dx;
     double *out;
@@ -203,6 +237,11 @@ __global__ void k_assemble(const double *__restrict__ lagww, const double *__res
         if (row < nker && col < nker) {
             int i = row / ns, l = row - i * ns, j = col / ns, l2 = col - j * ns;
             int dy = l / L - h, dx = l % L - h, dy2 = l2 / L - h, dx2 = l2 % L - h;
+            // an autocorrelation has C(D) = C(-D): read one canonical lag so N is exactly symmetric
+            if (i == j && (dy - dy2 < 0 || (dy == dy2 && dx - dx2 < 0))) {
+                int t1 = dy; dy = dy2; dy2 = t1;
+                int t2 = dx; dx = dx2; dx2 = t2;
+            }
             if (i <= j) {
                 int pr = i * nk - i * (i - 1) / 2 + (j - i);
                 v = lagww[((size_t)pr * Lw + (dy - dy2 + L - 1)) * Lw + (dx - dx2 + L - 1)];
@@ -253,16 +292,33 @@ cudaError_t launch_moments(const Geometry &g, int dtype, int precision, const vo
 
 cudaError_t launch_lag_tables(const Geometry &g, const double *ypart, double *ysum, const double *tw_x,
                               double *lagww, double *lagwg, double *lagws, const double *mom_part, double *mom,
-                              cudaStream_t st) {
+                              bool ws_only, bool pairs, cudaStream_t st) {
     size_t total = (size_t)g.nkf * g.nent;
     note_launch();
-    k_ysum<<<(unsigned)((total + 255) / 256), 256, 0, st>>>((const double2 *)ypart, g, (double2 *)ysum);
-    int nout = g.npair * (2 * g.L - 1) * (2 * g.L - 1) + g.nk * (g.nb + 1) * g.L * g.L;
+    if (ws_only && pairs) {
+        size_t per = (size_t)g.nkf * g.nk * g.L;
+        k_ysum_ws<<<(unsigned)((per + 255) / 256), 256, 0, st>>>((const float4 *)ypart, g, (double2 *)ysum);
+    } else {
+        k_ysum<<<(unsigned)((total + 255) / 256), 256, 0, st>>>((const double2 *)ypart, g, pairs, (double2 *)ysum);
+    }
+    int nout = ws_only ? g.nk * g.L * g.L : g.npair * (2 * g.L - 1) * (2 * g.L - 1) + g.nk * (g.nb + 1) * g.L * g.L;
     note_launch();
-    k_lagx<<<(nout + 127) / 128, 128, 0, st>>>((const double2 *)ysum, (const double2 *)tw_x, g, lagww, lagwg,
-                                               lagws);
+    k_lagx<<<(nout + 127) / 128, 128, 0, st>>>((const double2 *)ysum, (const double2 *)tw_x, g, ws_only, lagww,
+                                               lagwg, lagws);
     note_launch();
-    k_mom_reduce<<<(g.nmom + 63) / 64, 64, 0, st>>>(mom_part, g.mom_ctas, g.nmom, mom);
+    k_mom_reduce<<<g.nmom, 256, 0, st>>>(mom_part, g.mom_ctas, g.nmom, mom);
+    return cudaGetLastError();
+}
+
+__global__ void k_refine_rhs(const double *__restrict__ lagws, const double *__restrict__ mom, Geometry g,
+                             double *__restrict__ c) {
+    int row = blockIdx.x * blockDim.x + threadIdx.x;
+    if (row < g.n) c[row] = row < g.nker ? lagws[row] : mom[npoly(2 * g.db) + (row - g.nker)];
+}
+
+cudaError_t launch_refine_rhs(const Geometry &g, const double *lagws, const double *mom, double *c, cudaStream_t st) {
+    note_launch();
+    k_refine_rhs<<<(g.n + 255) / 256, 256, 0, st>>>(lagws, mom, g, c);
     return cudaGetLastError();
 }
 

@@ -16,7 +16,6 @@ namespace sfft {
 namespace {
 
 constexpr int kP = 256;
-constexpr int kRows = 8;  // rows per CTA
 
 template <class R>
 __device__ __forceinline__ R coord(int i, int n) {
@@ -76,39 +75,67 @@ __device__ __forceinline__ void dft16(cpx<R> (&v)[16], const cpx<R> *tw, const c
     for (int k = 0; k < 16; k++) v[k] = t[k];
 }
 
-template <class R, class In>
-__global__ void __launch_bounds__(256) k_segment_fft(const In *__restrict__ sci, const In *__restrict__ tmpl,
+// one 256-point complex FFT by the 16 lanes (t = lane & 15) of a half-warp: v[jj] holds
+// z[t + 16 jj] on entry and X[t + 16 k2] in v[k2] on exit; e is this FFT's 16 x 17 exchange
+// buffer, msk the lanes of the warp that take part.
+template <class R>
+__device__ __forceinline__ void fft256(cpx<R> (&v)[16], int t, cpx<R> *e, const cpx<R> *tw, const cpx<R> *twl,
+                                       unsigned msk) {
+    // X[k1 + 16 k2] = sum_t W16^{t k2} W256^{t k1} sum_jj x[t + 16 jj] W16^{jj k1}
+    dft16(v, tw, twl);
+#pragma unroll
+    for (int k1 = 1; k1 < 16; k1++) v[k1] = twmul(v[k1], tw[(t * k1) & (kP - 1)], twl[(t * k1) & (kP - 1)]);
+#pragma unroll
+    for (int k1 = 0; k1 < 16; k1++) e[k1 * 17 + t] = v[k1];
+    __syncwarp(msk);
+#pragma unroll
+    for (int tt = 0; tt < 16; tt++) v[tt] = e[t * 17 + tt];
+    dft16(v, tw, twl);  // now over tt: X[t + 16 k2] = v[k2]
+    __syncwarp(msk);
+}
+
+constexpr int kRowsPerCta = 16;
+// exchange buffer per FFT: 16 x 17 (padded transpose) + 1, so that buffers of consecutive
+// FFTs start two banks apart instead of on the same bank
+constexpr int kEx = 16 * 17 + 1;
+
+// Spectra of every image of a row segment, two rows per pass.  Layout of the output:
+// spec[s][y][k][img] (a contiguous block of nkf * nimg_pad values per row segment).
+template <class R, class In, int MAXT, int MINB>
+__global__ void __launch_bounds__(MAXT, MINB) k_segment_fft(const In *__restrict__ sci, const In *__restrict__ tmpl,
                                                     const uint8_t *__restrict__ mask, Geometry g,
                                                     const cpx<R> *__restrict__ tw_g, const R *__restrict__ xpow_g,
                                                     const R *__restrict__ ypow_g, cpx<R> *__restrict__ spec) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int nk = g.nk, nb = g.nb, G = g.G, U = g.U, nx = g.nx, ny = g.ny;
+    const int nk = g.nk, nb = g.nb, G = g.G, U = g.U, nx = g.nx, ny = g.ny, NI = g.nimg_pad, nkf = g.nkf;
     const int maxdeg = g.dk > g.db ? g.dk : g.db;
     const int s = blockIdx.x;
     const int x0 = s * U;
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    const int per_row = g.nfft * 16;
 
-    // shared layout
-    cpx<R> *tw = reinterpret_cast<cpx<R> *>(smem_raw);            // [P] twiddle, high part
-    cpx<R> *twl = tw + kP;                                          // [P] remainder
-    cpx<R> *ex = twl + kP;                                          // [nfft][16*17]
-    R *xpow = reinterpret_cast<R *>(ex + g.nfft * 16 * 17);         // [maxdeg+1][P]
-    R *tv = xpow + (maxdeg + 1) * kP;                               // [P] T_m on the window
-    R *sv = tv + kP;                                                // [P] S_m
-    R *mv = sv + kP;                                                // [P] m
-    int *ik = reinterpret_cast<int *>(mv + kP);                     // [nimg_pad] kind
-    int *ip = ik + g.nimg_pad;                                      // [nimg_pad] p
-    int *iq = ip + g.nimg_pad;                                      // [nimg_pad] q
+    cpx<R> *tw = reinterpret_cast<cpx<R> *>(smem_raw);  // [P] twiddle, high part
+    cpx<R> *twl = tw + kP;                              // [P] remainder
+    cpx<R> *ex = twl + kP;                              // [2][nfft][kEx]
+    R *xpow = reinterpret_cast<R *>(ex + 2 * g.nfft * kEx);  // [maxdeg+1][P + 1] (row P is all ones)
+    R *ones = xpow + (maxdeg + 1) * kP;                 // [P] ones (S_m has no coordinate weight)
+    R *tv = ones + kP;                                  // [2][P] T_m on the window
+    R *sv = tv + 2 * kP;                                // [2][P] S_m
+    R *mv = sv + 2 * kP;                                // [2][P] m
+    int *ik = reinterpret_cast<int *>(mv + 2 * kP);     // [nimg_pad] kind
+    int *ip = ik + NI;                                  // [nimg_pad] p
+    int *iq = ip + NI;                                  // [nimg_pad] q
 
-    for (int i = tid; i < kP; i += blockDim.x) {
+    for (int i = tid; i < kP; i += nthr) {
         tw[i] = tw_g[i];
         twl[i] = tw_g[kP + i];
         // coordinate powers come from FP64 tables rounded once: repeated FP32 products
         // are biased (~-3e-8 at power 4)
         int xw = wrapi(x0 - G + i, nx);
         for (int p = 0; p <= maxdeg; p++) xpow[p * kP + i] = xpow_g[(size_t)p * nx + xw];
+        ones[i] = (R)1;
     }
-    for (int i = tid; i < g.nimg_pad; i += blockDim.x) {
+    for (int i = tid; i < NI; i += nthr) {
         // kinds: 0 = A (W_i on own columns), 1 = B W_i, 2 = Psi_r, 3 = S_m, 4 = zero pad
         int kind, mi = 0;
         if (i < nk) { kind = 0; mi = i; }
@@ -123,82 +150,150 @@ __global__ void __launch_bounds__(256) k_segment_fft(const In *__restrict__ sci,
         iq[i] = q;
     }
 
-    const int f = tid >> 4, t = tid & 15;
-    const bool fft_thread = f < g.nfft;
-    // FFT lanes of this warp: all 32, or the lower 16 when the FFT count is odd
-    const unsigned fmask = ((tid & ~31) + 32 <= g.nfft * 16) ? 0xffffffffu : 0x0000ffffu;
-    const int y_end = min(ny, (int)(blockIdx.y + 1) * kRows);
-    for (int y = blockIdx.y * kRows; y < y_end; y++) {
-        __syncthreads();  // previous row's readers of ex / window are done
-        const size_t rowoff = (size_t)y * g.pitch;
-        for (int j = tid; j < kP; j += blockDim.x) {
+    const int ybeg = blockIdx.y * kRowsPerCta, yend = min(ny, ybeg + kRowsPerCta);
+    // window positions loaded per thread per pass (2 rows x P positions)
+    constexpr int kMaxPf = 4;
+    const int npos = 2 * kP;
+    auto load_pos = [&](int q, int ybase, R &t_out, R &s_out, R &m_out) {
+        int r = q / kP, j = q - r * kP, y = ybase + r;
+        if (y < yend) {
             int xw = wrapi(x0 - G + j, nx);
-            R good = (mask && mask[rowoff + xw]) ? (R)0 : (R)1;
-            tv[j] = good * (R)tmpl[rowoff + xw];
-            sv[j] = good * (R)sci[rowoff + xw];
-            mv[j] = good;
+            size_t u = (size_t)y * g.pitch + xw;
+            R good = (mask && mask[u]) ? (R)0 : (R)1;
+            t_out = good * (R)tmpl[u];
+            s_out = good * (R)sci[u];
+            m_out = good;
+        } else {
+            t_out = s_out = m_out = (R)0;
         }
-        __syncthreads();
-        if (fft_thread) {
-            cpx<R> v[16];
-            int kinds[2], ps[2];
+    };
+    // prologue: window of the first pass straight to shared memory
+    for (int q = tid; q < npos; q += nthr) load_pos(q, ybeg, tv[q], sv[q], mv[q]);
+    __syncthreads();
+
+    const int r_fft = tid / per_row, rem = tid - r_fft * per_row;
+    const int f = rem >> 4, t = rem & 15;
+    for (int y0 = ybeg; y0 < yend; y0 += 2) {
+        // prefetch the next pass's window into registers
+        R pft[kMaxPf], pfs[kMaxPf], pfm[kMaxPf];
+        const bool more = y0 + 2 < yend;
+#pragma unroll
+        for (int c = 0; c < kMaxPf; c++) {
+            int q = tid + c * nthr;
+            if (more && q < npos) load_pos(q, y0 + 2, pft[c], pfs[c], pfm[c]);
+        }
+        // FFT lanes of this warp: each half-warp is one FFT of a row that exists
+        auto half_active = [&](int base) {
+            int rr = base / per_row;
+            return base < 2 * per_row && y0 + rr < yend;
+        };
+        const int wbase = tid & ~31;
+        const unsigned msk = (half_active(wbase) ? 0x0000ffffu : 0u) | (half_active(wbase + 16) ? 0xffff0000u : 0u);
+        if (r_fft < 2 && y0 + r_fft < yend) {
+            const int y = y0 + r_fft;
+            const R *tvr = tv + r_fft * kP, *svr = sv + r_fft * kP, *mvr = mv + r_fft * kP;
+            // per image of this lane's pair: source row, coordinate-power row, y weight, offset
+            // of the pixel inside the window and the number of valid positions (branch-free
+            // construction of z = x_{2f} + i x_{2f+1} below)
+            const R *src[2], *xpr[2];
             R yq[2];
+            int off[2], lim[2];
 #pragma unroll
             for (int c = 0; c < 2; c++) {
-                int im = 2 * f + c;
-                kinds[c] = ik[im];
-                ps[c] = ip[im];
-                yq[c] = ypow_g[(size_t)iq[im] * ny + y];
+                const int im = 2 * f + c, kind = ik[im];
+                src[c] = kind == 2 ? mvr : (kind == 3 ? svr : tvr);
+                xpr[c] = kind == 3 ? ones : xpow + ip[im] * kP;
+                yq[c] = kind == 3 ? (R)1 : (kind == 4 ? (R)0 : ypow_g[(size_t)iq[im] * ny + y]);
+                off[c] = kind == 0 ? G : 0;
+                lim[c] = kind == 0 ? min(U, nx - x0) : kP;
             }
+            cpx<R> v[16];
 #pragma unroll
             for (int jj = 0; jj < 16; jj++) {
                 const int n = t + 16 * jj;
                 R val[2];
 #pragma unroll
                 for (int c = 0; c < 2; c++) {
-                    R r = (R)0;
-                    switch (kinds[c]) {
-                        case 0:
-                            if (n < U && x0 + n < nx) r = xpow[ps[c] * kP + n + G] * yq[c] * tv[n + G];
-                            break;
-                        case 1: r = xpow[ps[c] * kP + n] * yq[c] * tv[n]; break;
-                        case 2: r = xpow[ps[c] * kP + n] * yq[c] * mv[n]; break;
-                        case 3: r = sv[n]; break;
-                        default: break;
-                    }
-                    val[c] = r;
+                    const int q = n < lim[c] ? n + off[c] : 0;
+                    R r = xpr[c][q] * yq[c] * src[c][q];
+                    val[c] = n < lim[c] ? r : (R)0;
                 }
                 v[jj] = {val[0], val[1]};
             }
-            // X[k1 + 16 k2] = sum_t W16^{t k2} W256^{t k1} sum_jj x[t + 16 jj] W16^{jj k1}
-            dft16(v, tw, twl);
-#pragma unroll
-            for (int k1 = 1; k1 < 16; k1++) v[k1] = twmul(v[k1], tw[(t * k1) & (kP - 1)], twl[(t * k1) & (kP - 1)]);
-            cpx<R> *e = ex + f * 16 * 17;
-#pragma unroll
-            for (int k1 = 0; k1 < 16; k1++) e[k1 * 17 + t] = v[k1];
-            __syncwarp(fmask);
-            // the 16 lanes of this FFT share one half-warp, so a warp barrier suffices
-#pragma unroll
-            for (int tt = 0; tt < 16; tt++) v[tt] = e[t * 17 + tt];
-            dft16(v, tw, twl);  // now over tt: X[t + 16 k2] = v[k2]
-            __syncwarp(fmask);
+            cpx<R> *e = ex + (r_fft * g.nfft + f) * kEx;
+            fft256(v, t, e, tw, twl, msk);
 #pragma unroll
             for (int k2 = 0; k2 < 16; k2++) e[t + 16 * k2] = v[k2];  // natural order Z[k]
         }
         __syncthreads();
-        // unpack the packed real pairs and write spec[s][k][y][img], k in [0, P/2]
-        const int total = g.nkf * g.nimg_pad;
-        for (int idx = tid; idx < total; idx += blockDim.x) {
-            const int k = idx / g.nimg_pad, img = idx - k * g.nimg_pad;
-            const cpx<R> *e = ex + (img >> 1) * 16 * 17;
+        // unpack the packed real pairs; each row segment is one contiguous block
+        const int per_out = nkf * NI;
+        const int nrow = min(2, yend - y0);
+        for (int idx = tid; idx < nrow * per_out; idx += nthr) {
+            const int rr = idx / per_out, r2 = idx - rr * per_out;
+            const int k = r2 / NI, img = r2 - k * NI;
+            const cpx<R> *e = ex + (rr * g.nfft + (img >> 1)) * kEx;
             cpx<R> zk = e[k], zc = e[(kP - k) & (kP - 1)];
             cpx<R> out;
             if ((img & 1) == 0)
                 out = {(R)0.5 * (zk.re + zc.re), (R)0.5 * (zk.im - zc.im)};
             else
                 out = {(R)0.5 * (zk.im + zc.im), (R)0.5 * (zc.re - zk.re)};
-            spec[(((size_t)s * g.nkf + k) * ny + y) * g.nimg_pad + img] = out;
+            spec[((size_t)s * ny + (y0 + rr)) * per_out + r2] = out;
+        }
+        // the next pass's window (its FFT readers are past the barrier above)
+#pragma unroll
+        for (int c = 0; c < kMaxPf; c++) {
+            int q = tid + c * nthr;
+            if (more && q < npos) {
+                tv[q] = pft[c];
+                sv[q] = pfs[c];
+                mv[q] = pfm[c];
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// Spectrum of one image (the refinement residual) over every row segment, written into the
+// S_m slot of spec.  Two rows share one complex FFT (z = X_y + i X_{y+1}).
+template <class R, class In>
+__global__ void __launch_bounds__(128) k_segment_fft_single(const In *__restrict__ img, Geometry g,
+                                                           const cpx<R> *__restrict__ tw_g, int slot,
+                                                           cpx<R> *__restrict__ spec) {
+    __shared__ cpx<R> tw[kP], twl[kP];
+    __shared__ cpx<R> ex[8][kEx];
+    const int G = g.G, nx = g.nx, ny = g.ny, NI = g.nimg_pad, nkf = g.nkf;
+    const int s = blockIdx.x, x0 = s * g.U;
+    for (int i = threadIdx.x; i < kP; i += blockDim.x) {
+        tw[i] = tw_g[i];
+        twl[i] = tw_g[kP + i];
+    }
+    __syncthreads();
+    const int f = threadIdx.x >> 4, t = threadIdx.x & 15;  // 8 FFTs of row pairs
+    const int y = (blockIdx.y * 8 + f) * 2;
+    const bool act = y < ny;
+    const unsigned msk = 0xffffffffu;  // both half-warps always run the FFT (zeros past the end)
+    cpx<R> v[16];
+#pragma unroll
+    for (int jj = 0; jj < 16; jj++) {
+        int xw = wrapi(x0 - G + t + 16 * jj, nx);
+        R a = act ? (R)img[(size_t)y * g.pitch + xw] : (R)0;
+        R b = (act && y + 1 < ny) ? (R)img[(size_t)(y + 1) * g.pitch + xw] : (R)0;
+        v[jj] = {a, b};
+    }
+    cpx<R> *e = ex[f];
+    fft256(v, t, e, tw, twl, msk);
+#pragma unroll
+    for (int k2 = 0; k2 < 16; k2++) e[t + 16 * k2] = v[k2];
+    __syncwarp(msk);
+    if (act) {
+        for (int k = t; k < nkf; k += 16) {
+            cpx<R> zk = e[k], zc = e[(kP - k) & (kP - 1)];
+            spec[(((size_t)s * ny + y) * nkf + k) * NI + slot] = {(R)0.5 * (zk.re + zc.re), (R)0.5 * (zk.im - zc.im)};
+            if (y + 1 < ny)
+                spec[(((size_t)s * ny + y + 1) * nkf + k) * NI + slot] = {(R)0.5 * (zk.im + zc.im),
+                                                                         (R)0.5 * (zc.re - zk.re)};
         }
     }
 }
@@ -206,20 +301,23 @@ __global__ void __launch_bounds__(256) k_segment_fft(const In *__restrict__ sci,
 template <class R>
 size_t segfft_smem(const Geometry &g) {
     const int maxdeg = g.dk > g.db ? g.dk : g.db;
-    return sizeof(cpx<R>) * (2 * kP + (size_t)g.nfft * 16 * 17) + sizeof(R) * ((size_t)(maxdeg + 1) * kP + 3 * kP) +
-           sizeof(int) * 3 * g.nimg_pad;
+    return sizeof(cpx<R>) * (2 * kP + (size_t)2 * g.nfft * kEx) +
+           sizeof(R) * ((size_t)(maxdeg + 2) * kP + 6 * kP) + sizeof(int) * 3 * g.nimg_pad;
 }
 
 template <class R, class In>
 cudaError_t run(const Geometry &g, const void *sci, const void *tmpl, const uint8_t *mask, const void *tw,
                 const void *xpow, const void *ypow, void *spec, cudaStream_t st) {
     size_t sm = segfft_smem<R>(g);
-    auto kern = k_segment_fft<R, In>;
+    int threads = ((2 * g.nfft * 16 + 31) / 32) * 32;
+    if (threads < 128) threads = 128;
+    // up to 384 threads: register budget for two CTAs per SM; larger bases: one
+    auto kern = threads <= 384 ? k_segment_fft<R, In, 384, 2> : k_segment_fft<R, In, 512, 1>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return e;
-    int threads = ((g.nfft * 16 + 31) / 32) * 32;
-    if (threads < 64) threads = 64;
-    dim3 grid(g.nseg, (g.ny + kRows - 1) / kRows);
+    dim3 grid(g.nseg, (g.ny + kRowsPerCta - 1) / kRowsPerCta);
     note_launch();
     kern<<<grid, threads, sm, st>>>((const In *)sci, (const In *)tmpl, mask, g, (const cpx<R> *)tw,
                                     (const R *)xpow, (const R *)ypow, (cpx<R> *)spec);
@@ -227,6 +325,25 @@ cudaError_t run(const Geometry &g, const void *sci, const void *tmpl, const uint
 }
 
 }  // namespace
+
+cudaError_t launch_segment_fft_single(const Geometry &g, int dtype, int precision, const void *img, const void *tw_fft,
+                                      int slot, void *spec, cudaStream_t st) {
+    if (g.P != kP) return cudaErrorInvalidValue;
+    dim3 grid(g.nseg, (g.ny + 15) / 16);
+    note_launch();
+    if (precision == SFFT_PREC_FP64) {
+        if (dtype == SFFT_F64)
+            k_segment_fft_single<double, double><<<grid, 128, 0, st>>>((const double *)img, g, (const cpx<double> *)tw_fft, slot, (cpx<double> *)spec);
+        else
+            k_segment_fft_single<double, float><<<grid, 128, 0, st>>>((const float *)img, g, (const cpx<double> *)tw_fft, slot, (cpx<double> *)spec);
+    } else {
+        if (dtype == SFFT_F64)
+            k_segment_fft_single<float, double><<<grid, 128, 0, st>>>((const double *)img, g, (const cpx<float> *)tw_fft, slot, (cpx<float> *)spec);
+        else
+            k_segment_fft_single<float, float><<<grid, 128, 0, st>>>((const float *)img, g, (const cpx<float> *)tw_fft, slot, (cpx<float> *)spec);
+    }
+    return cudaGetLastError();
+}
 
 cudaError_t launch_segment_fft(const Geometry &g, int dtype, int precision, const void *sci, const void *tmpl,
                                const uint8_t *mask, const void *tw_fft, const void *xpow, const void *ypow,

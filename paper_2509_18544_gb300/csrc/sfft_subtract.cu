@@ -6,6 +6,8 @@
 // c_p(d, y_s) = sum_{i: p_i = p} a_{i,d} yh_s^q_i, so each output pixel costs
 // (DK+1) L^2 multiply-adds instead of nP(DK) L^2.
 //
+// The folded coefficients depend only on the source row, so k_fold tabulates them once per
+// call (FP64 sums rounded once) for every row: cf[ys][dy][p][dx] and bg[y][p].
 // CTA: 8 output rows x 256 columns; a warp per row, 8 consecutive pixels per thread.
 // Shared memory holds the cyclic template window (rows y0-h.., columns x0-h..), the x
 // powers of its columns and the folded coefficients for the CTA's rows.
@@ -15,25 +17,66 @@ namespace sfft {
 namespace {
 
 constexpr int kRowsO = 8, kRX = 8, kColsO = 32 * kRX;
+// Each lane reads a window starting at column 8 * lane; a skew of one word every 8 columns
+// (index c + c / 8) makes the 32 lanes' addresses 9 words apart, i.e. on 32 distinct banks.
+__device__ __forceinline__ int skew(int c) { return c + (c >> 3); }
 
 template <class R>
 __device__ __forceinline__ R coordv(int i, int n) {
     return n > 1 ? (R)(2 * i - (n - 1)) / (R)(n - 1) : (R)0;
 }
 
+// cf[ys][l][p] over l = (dy+h) L + (dx+h): sum_{i: p_i = p} a_{i,l} yh(ys)^q_i, and after
+// the table bg[y][p] = sum_{r: p_r = p} b_r yh(y)^q_r
+template <class R>
+__global__ void k_fold(const double *__restrict__ coeffs, Geometry g, R *__restrict__ cf) {
+    const int L2 = g.L * g.L, np = g.dk + 1, nbp = g.db + 1;
+    const size_t ncf = (size_t)g.ny * L2;
+    size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < ncf) {
+        const int ys = (int)(t / L2), l = (int)(t - (size_t)ys * L2);
+        const double yh = g.ny > 1 ? (2.0 * ys - (g.ny - 1)) / (double)(g.ny - 1) : 0.0;
+        double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        for (int i = 0; i < g.nk; i++) {
+            int pi, qi;
+            mono_pq(i, pi, qi);
+            double w = 1.0;
+            for (int q = 0; q < qi; q++) w *= yh;
+            acc[pi] = fma(coeffs[(size_t)i * L2 + l], w, acc[pi]);
+        }
+        const int dyi = l / g.L, dxi = l - dyi * g.L;
+        R *o = cf + (((size_t)ys * g.L + dyi) * np) * g.L + dxi;
+        for (int p = 0; p < np; p++) o[(size_t)p * g.L] = (R)acc[p];
+    } else if (t < ncf + (size_t)g.ny) {
+        const int y = (int)(t - ncf);
+        const double yh = g.ny > 1 ? (2.0 * y - (g.ny - 1)) / (double)(g.ny - 1) : 0.0;
+        double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        for (int r = 0; r < g.nb; r++) {
+            int pr, qr;
+            mono_pq(r, pr, qr);
+            double w = 1.0;
+            for (int q = 0; q < qr; q++) w *= yh;
+            acc[pr] = fma(coeffs[g.nker + r], w, acc[pr]);
+        }
+        R *o = cf + ncf * np + (size_t)y * nbp;
+        for (int p = 0; p < nbp; p++) o[p] = (R)acc[p];
+    }
+}
+
 template <class R, class In, int LL>
 __global__ void __launch_bounds__(256) k_subtract(const In *__restrict__ sci, const In *__restrict__ tmpl,
-                                                 Geometry g, const double *__restrict__ coeffs,
-                                                 const R *__restrict__ xpow_g, In *__restrict__ diff) {
+                                                 const uint8_t *__restrict__ mask, bool residual, Geometry g,
+                                                 const R *__restrict__ cfold, const R *__restrict__ xpow_g,
+                                                 In *__restrict__ diff) {
     constexpr int h = LL / 2;
     constexpr int WC = kColsO + 2 * h;  // window columns
+    constexpr int WCS = WC + WC / 8 + 1; // skewed row length
     constexpr int WR = kRowsO + 2 * h;  // window rows
     constexpr int NW = kRX + LL - 1;    // register window per thread
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int dk = g.dk, np = dk + 1;
-    R *Tw = reinterpret_cast<R *>(smem_raw);  // [WR][WC]
-    R *xp = Tw + WR * WC;                      // [np][WC]
-    R *cf = xp + np * WC;                      // [kRowsO][LL][np][LL]
+    R *Tp = reinterpret_cast<R *>(smem_raw);  // [np][WR][WCS] skewed: template times xh^p
+    R *cf = Tp + np * WR * WCS;                // [kRowsO][LL][np][LL]
     R *byp = cf + kRowsO * LL * np * LL;       // [kRowsO][db+1]  background per x power
 
     const int x0 = blockIdx.x * kColsO, y0 = blockIdx.y * kRowsO;
@@ -44,11 +87,10 @@ __global__ void __launch_bounds__(256) k_subtract(const In *__restrict__ sci, co
         int r = e / WC, c = e - r * WC;
         int yy = ((y0 - h + r) % ny + ny) % ny;
         int xx = ((x0 - h + c) % nx + nx) % nx;
-        Tw[e] = (R)tmpl[(size_t)yy * g.pitch + xx];
-    }
-    for (int c = tid; c < WC; c += blockDim.x) {
-        int xx = ((x0 - h + c) % nx + nx) % nx;
-        for (int p = 0; p < np; p++) xp[p * WC + c] = xpow_g[(size_t)p * nx + xx];
+        size_t u = (size_t)yy * g.pitch + xx;
+        // the residual of the fit convolves the masked template W_i = w_i T_m
+        R tv = (residual && mask && mask[u]) ? (R)0 : (R)tmpl[u];
+        for (int p = 0; p < np; p++) Tp[(p * WR + r) * WCS + skew(c)] = tv * xpow_g[(size_t)p * nx + xx];
     }
     // folded kernel coefficients c_p(d, y - dy) for each of the CTA's output rows
     const int ncf = kRowsO * LL * np * LL;
@@ -58,31 +100,12 @@ __global__ void __launch_bounds__(256) k_subtract(const In *__restrict__ sci, co
         rest /= np;
         int dyi = rest % LL, ry = rest / LL;
         int ys = (((y0 + ry) - (dyi - h)) % ny + ny) % ny;  // source row y - dy
-        double yh = coordv<double>(ys, ny);
-        double acc = 0.0;
-        for (int i = 0; i < g.nk; i++) {
-            int pi, qi;
-            mono_pq(i, pi, qi);
-            if (pi != p) continue;
-            double w = 1.0;
-            for (int q = 0; q < qi; q++) w *= yh;
-            acc += coeffs[(size_t)i * LL * LL + dyi * LL + dxi] * w;
-        }
-        cf[e] = (R)acc;
+        cf[e] = cfold[(((size_t)ys * LL + dyi) * np + p) * LL + dxi];
     }
+    const R *bgf = cfold + (size_t)ny * LL * LL * np;
     for (int e = tid; e < kRowsO * (g.db + 1); e += blockDim.x) {
         int ry = e / (g.db + 1), p = e % (g.db + 1);
-        double yh = coordv<double>(min(y0 + ry, ny - 1), ny);
-        double acc = 0.0;
-        for (int r = 0; r < g.nb; r++) {
-            int pr, qr;
-            mono_pq(r, pr, qr);
-            if (pr != p) continue;
-            double w = 1.0;
-            for (int q = 0; q < qr; q++) w *= yh;
-            acc += coeffs[g.nker + r] * w;
-        }
-        byp[e] = (R)acc;
+        byp[e] = bgf[(size_t)min(y0 + ry, ny - 1) * (g.db + 1) + p];
     }
     __syncthreads();
 
@@ -94,15 +117,12 @@ __global__ void __launch_bounds__(256) k_subtract(const In *__restrict__ sci, co
     for (int r = 0; r < kRX; r++) out[r] = (R)0;
     for (int dyi = 0; dyi < LL; dyi++) {
         // source row y - dy sits at window row ty + h - dy = ty + (LL - 1) - dyi
-        const R *trow = Tw + (ty + (LL - 1) - dyi) * WC + cx;
-        R wv[NW];
-#pragma unroll
-        for (int m = 0; m < NW; m++) wv[m] = trow[m];
+        const int wr = ty + (LL - 1) - dyi;
         for (int p = 0; p < np; p++) {
+            const R *trow = Tp + (p * WR + wr) * WCS;
             R wp[NW];
-            const R *xr = xp + p * WC + cx;
 #pragma unroll
-            for (int m = 0; m < NW; m++) wp[m] = wv[m] * xr[m];
+            for (int m = 0; m < NW; m++) wp[m] = trow[skew(cx + m)];
             const R *c = cf + ((ty * LL + dyi) * np + p) * LL;
 #pragma unroll
             for (int dxi = 0; dxi < LL; dxi++) {
@@ -122,40 +142,54 @@ __global__ void __launch_bounds__(256) k_subtract(const In *__restrict__ sci, co
                 R bg = (R)0;
                 for (int p = 0; p <= g.db; p++) bg += bp[p] * xpow_g[(size_t)p * nx + x];
                 size_t u = (size_t)y * g.pitch + x;
-                diff[u] = (In)((R)sci[u] - out[r] - bg);
+                if (residual) {
+                    R m = (mask && mask[u]) ? (R)0 : (R)1;
+                    diff[u] = (In)(m * ((R)sci[u] - bg) - out[r]);
+                } else {
+                    diff[u] = (In)((R)sci[u] - out[r] - bg);
+                }
             }
         }
     }
 }
 
 template <class R, class In, int LL>
-cudaError_t run(const Geometry &g, const void *sci, const void *tmpl, const double *coeffs, const void *xpow,
-                void *diff, cudaStream_t st) {
+cudaError_t run(const Geometry &g, const void *sci, const void *tmpl, const uint8_t *mask, bool residual,
+                const double *coeffs, const void *xpow, void *cfold, void *diff, cudaStream_t st) {
+    {
+        size_t nt = (size_t)g.ny * LL * LL + g.ny;
+        note_launch();
+        k_fold<R><<<(unsigned)((nt + 255) / 256), 256, 0, st>>>(coeffs, g, (R *)cfold);
+    }
     constexpr int h = LL / 2;
     const int np = g.dk + 1;
-    size_t sm = sizeof(R) * ((size_t)(kRowsO + 2 * h) * (kColsO + 2 * h) + (size_t)np * (kColsO + 2 * h) +
+    constexpr int WCS = (kColsO + 2 * h) + (kColsO + 2 * h) / 8 + 1;
+    size_t sm = sizeof(R) * ((size_t)np * (kRowsO + 2 * h) * WCS +
                              (size_t)kRowsO * LL * np * LL + (size_t)kRowsO * (g.db + 1));
     auto kern = k_subtract<R, In, LL>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return e;
     dim3 grid((g.nx + kColsO - 1) / kColsO, (g.ny + kRowsO - 1) / kRowsO);
     note_launch();
-    kern<<<grid, 256, sm, st>>>((const In *)sci, (const In *)tmpl, g, coeffs, (const R *)xpow, (In *)diff);
+    kern<<<grid, 256, sm, st>>>((const In *)sci, (const In *)tmpl, mask, residual, g, (const R *)cfold,
+                                (const R *)xpow, (In *)diff);
     return cudaGetLastError();
 }
 
 template <class R, class In>
-cudaError_t dispatch_L(const Geometry &g, const void *sci, const void *tmpl, const double *coeffs, const void *xpow,
-                       void *diff, cudaStream_t st) {
+cudaError_t dispatch_L(const Geometry &g, const void *sci, const void *tmpl, const uint8_t *mask, bool residual,
+                       const double *coeffs, const void *xpow, void *cfold, void *diff, cudaStream_t st) {
     switch (g.L) {
-        case 1: return run<R, In, 1>(g, sci, tmpl, coeffs, xpow, diff, st);
-        case 3: return run<R, In, 3>(g, sci, tmpl, coeffs, xpow, diff, st);
-        case 5: return run<R, In, 5>(g, sci, tmpl, coeffs, xpow, diff, st);
-        case 7: return run<R, In, 7>(g, sci, tmpl, coeffs, xpow, diff, st);
-        case 9: return run<R, In, 9>(g, sci, tmpl, coeffs, xpow, diff, st);
-        case 11: return run<R, In, 11>(g, sci, tmpl, coeffs, xpow, diff, st);
-        case 13: return run<R, In, 13>(g, sci, tmpl, coeffs, xpow, diff, st);
-        case 15: return run<R, In, 15>(g, sci, tmpl, coeffs, xpow, diff, st);
+        case 1: return run<R, In, 1>(g, sci, tmpl, mask, residual, coeffs, xpow, cfold, diff, st);
+        case 3: return run<R, In, 3>(g, sci, tmpl, mask, residual, coeffs, xpow, cfold, diff, st);
+        case 5: return run<R, In, 5>(g, sci, tmpl, mask, residual, coeffs, xpow, cfold, diff, st);
+        case 7: return run<R, In, 7>(g, sci, tmpl, mask, residual, coeffs, xpow, cfold, diff, st);
+        case 9: return run<R, In, 9>(g, sci, tmpl, mask, residual, coeffs, xpow, cfold, diff, st);
+        case 11: return run<R, In, 11>(g, sci, tmpl, mask, residual, coeffs, xpow, cfold, diff, st);
+        case 13: return run<R, In, 13>(g, sci, tmpl, mask, residual, coeffs, xpow, cfold, diff, st);
+        case 15: return run<R, In, 15>(g, sci, tmpl, mask, residual, coeffs, xpow, cfold, diff, st);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -163,12 +197,15 @@ cudaError_t dispatch_L(const Geometry &g, const void *sci, const void *tmpl, con
 }  // namespace
 
 cudaError_t launch_subtract(const Geometry &g, int dtype, int precision, const void *sci, const void *tmpl,
-                            const double *coeffs, const void *xpow, void *diff, cudaStream_t st) {
+                            const uint8_t *mask, bool residual, const double *coeffs, const void *xpow,
+                            const void *ypow, void *cfold, void *diff, cudaStream_t st) {
+    (void)ypow;
+    if (g.dk > 7 || g.db > 7) return cudaErrorInvalidValue;
     if (precision == SFFT_PREC_FP64)
-        return dtype == SFFT_F64 ? dispatch_L<double, double>(g, sci, tmpl, coeffs, xpow, diff, st)
-                                 : dispatch_L<double, float>(g, sci, tmpl, coeffs, xpow, diff, st);
-    return dtype == SFFT_F64 ? dispatch_L<float, double>(g, sci, tmpl, coeffs, xpow, diff, st)
-                             : dispatch_L<float, float>(g, sci, tmpl, coeffs, xpow, diff, st);
+        return dtype == SFFT_F64 ? dispatch_L<double, double>(g, sci, tmpl, mask, residual, coeffs, xpow, cfold, diff, st)
+                                 : dispatch_L<double, float>(g, sci, tmpl, mask, residual, coeffs, xpow, cfold, diff, st);
+    return dtype == SFFT_F64 ? dispatch_L<float, double>(g, sci, tmpl, mask, residual, coeffs, xpow, cfold, diff, st)
+                             : dispatch_L<float, float>(g, sci, tmpl, mask, residual, coeffs, xpow, cfold, diff, st);
 }
 
 }  // namespace sfft

@@ -8,19 +8,23 @@
 // every (A, B) pair the normal matrix uses -- W_i x W_j (i <= j, |dy| <= L-1), W_i x Psi_r
 // and W_i x S_m (|dy| <= h) -- and K3 finishes the x direction.
 //
-// One CTA owns one segment and `kg` consecutive frequencies; each thread owns one
-// (frequency, A, B, dy-chunk of C = L lags) work item and streams over y.  Rows are staged
-// in shared memory in tiles of `ytile` rows plus a halo of G = L-1 rows on each side
-// (cyclic in y).  Inner step: TY rows at once, C+TY-1 B values in registers, C*TY
-// complex multiply-adds.  FP32 spectra accumulate in FP32 for one tile and are then
-// folded into a double-float (hi, lo) pair with an error-free two-sum, so the long sums
-// over y keep ~FP64 accuracy at FP32 speed; FP64 spectra accumulate in FP64.
+// Work unit (one CTA): one segment, `kg` consecutive frequencies, one of `ysplit` chunks of
+// rows.  Each thread owns one (frequency, A, B, dy-chunk of C = L lags) item and streams
+// over the chunk's rows.  Rows are staged in shared memory by cp.async in tiles of
+// `ytile` rows plus a halo of G = L-1 rows on each side (cyclic in y), double-buffered so
+// the next tile loads while this one is consumed.  Inner step: TY rows, C+TY-1 B values in
+// registers, C*TY complex multiply-adds.  FP32 spectra accumulate in FP32 for one tile and
+// are then folded into a double-float (hi, lo) pair with an error-free two-sum; FP64
+// spectra accumulate in FP64.  Items can be restricted to the W x S_m pairs (the
+// refinement pass correlates the basis with a residual image stored in the S_m slot).
+#include <stdlib.h>
+
 #include "sfft_internal.cuh"
 
 namespace sfft {
 namespace {
 
-constexpr int kTY = 4;
+constexpr int kTY = 8;
 
 // error-free transformation: s + e == a + b exactly
 __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
@@ -29,14 +33,31 @@ __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
     e = (a - (s - bb)) + (b - bb);
 }
 
+// compact staging for the W x S_m pass: W_0..W_{nk-1} padded to an even count, then the
+// 16-byte pair of images that holds the S_m slot
+__host__ __device__ __forceinline__ int ws_nka(const Geometry &g) { return (g.nk + 1) & ~1; }
+__host__ __device__ __forceinline__ int ws_slot(const Geometry &g) { return 2 * g.nk + g.nb; }
+
 struct Item {
     int A, B, dylo, ent0, c0, cn;  // images, first lag, first entry, valid chunk range [c0, cn)
 };
 
-__device__ __forceinline__ Item decode_item(const Geometry &g, int it) {
+// item numbering: 2*npair W-W half items, then nk*(nb+1) W-(Psi|S) items.  With
+// ws_only, item it is the W_it x S_m item.
+__device__ __forceinline__ Item decode_item(const Geometry &g, int it, bool ws_only) {
     Item m;
     const int L = g.L, nk = g.nk;
     const int two_pairs = 2 * g.npair;
+    if (ws_only) {
+        // W_it x S_m with the compact staging: B sits after the padded W block
+        m.A = it;
+        m.B = ws_nka(g) + (ws_slot(g) & 1);
+        m.dylo = -g.h;
+        m.ent0 = g.npair * (2 * L - 1) + (it * (g.nb + 1) + g.nb) * L;
+        m.c0 = 0;
+        m.cn = L;
+        return m;
+    }
     if (it < two_pairs) {
         int pr = it >> 1, half = it & 1;
         int i = 0, rem = pr;
@@ -64,20 +85,63 @@ __device__ __forceinline__ Item decode_item(const Geometry &g, int it) {
     return m;
 }
 
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+    unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+struct Launch {
+    int items;     // items per frequency in this launch
+    int kg;        // frequencies per CTA
+    int ngroups;   // frequency groups
+    int ysplit;    // row chunks
+    bool ws_only;  // W x S_m items only
+    int cw;        // staged images per frequency (all nimg_pad, or the compact W_i + S_m set)
+};
+
+// stage rows [y0 - G, y0 - G + rows) (cyclic) of the CTA's frequencies into buf via 16-byte
+// cp.async; layout buf[r][kl][img]
+template <class CT>
+__device__ __forceinline__ void stage_tile(const CT *__restrict__ spec, const Geometry &g, int s, int k0, int kcnt,
+                                           int kg, int y0, int rows, bool ws, int cw, CT *buf) {
+    const int NI = g.nimg_pad, ny = g.ny;
+    constexpr int per16 = 16 / (int)sizeof(CT);  // complex values per 16-byte chunk
+    const int chunks_k = cw / per16;              // chunks per frequency in the staged layout
+    const int per_row = kcnt * chunks_k;
+    const int total = rows * per_row;
+    const int nka = ws_nka(g), slot_pair = ws_slot(g) & ~1;
+    for (int v = threadIdx.x; v < total; v += blockDim.x) {
+        int r = v / per_row, c = v - r * per_row;
+        int kk = c / chunks_k, cc = c - kk * chunks_k;
+        int yy = ((y0 - g.G + r) % ny + ny) % ny;
+        // source image index of this chunk's first value
+        int img = ws ? (cc * per16 < nka ? cc * per16 : slot_pair + (cc * per16 - nka)) : cc * per16;
+        const CT *src = spec + (((size_t)s * ny + yy) * g.nkf + k0 + kk) * NI + img;
+        CT *dst = buf + ((size_t)r * kg + kk) * cw + cc * per16;
+        cp_async16(dst, src);
+    }
+    cp_async_commit();
+}
+
 template <int C>
-__global__ void __launch_bounds__(256) k_ycorr_f32(const cpx<float> *__restrict__ spec, Geometry g,
-                                                  double *__restrict__ ypart) {
+__global__ void __launch_bounds__(256, 2) k_ycorr_f32(const cpx<float> *__restrict__ spec, Geometry g, Launch ln,
+                                                     double *__restrict__ ypart) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    cpx<float> *tile = reinterpret_cast<cpx<float> *>(smem_raw);  // [ytile + 2G][kg][nimg_pad]
-    const int s = blockIdx.x;
-    const int k0 = blockIdx.y * g.kg;
-    const int kcnt = min(g.kg, g.nkf - k0);
-    const int G = g.G, ny = g.ny, YT = g.ytile, NI = g.nimg_pad;
+    const int YT = g.ytile, G = g.G, ny = g.ny;
     const int rows = YT + 2 * G;
+    cpx<float> *buf0 = reinterpret_cast<cpx<float> *>(smem_raw);
+    cpx<float> *buf1 = buf0 + (size_t)rows * ln.kg * ln.cw;
+    const int s = blockIdx.x / ln.ysplit, ych = blockIdx.x % ln.ysplit;
+    const int k0 = blockIdx.y * ln.kg;
+    const int kcnt = min(ln.kg, g.nkf - k0);
+    const int chunk = (ny + ln.ysplit - 1) / ln.ysplit;
+    const int ya = ych * chunk, yb = min(ny, ya + chunk);
     const int tid = threadIdx.x;
-    const int kl = tid / g.items_per_k, it = tid - kl * g.items_per_k;
+    const int kl = tid / ln.items, it = tid - kl * ln.items;
     const bool active = kl < kcnt;
-    Item m = decode_item(g, active ? it : 0);
+    Item m = decode_item(g, active ? it : 0, ln.ws_only);
 
     float2 acc[C], hi[C], lo[C];
 #pragma unroll
@@ -86,29 +150,18 @@ __global__ void __launch_bounds__(256) k_ycorr_f32(const cpx<float> *__restrict_
         hi[c] = make_float2(0.f, 0.f);
         lo[c] = make_float2(0.f, 0.f);
     }
-
-    const size_t kstride = (size_t)ny * NI;  // elements between consecutive k for fixed s
-    const cpx<float> *base = spec + ((size_t)s * g.nkf + k0) * kstride;
-    const int vec_per_row = NI / 2;  // float4 = two complex values; NI is even
-
-    for (int y0 = 0; y0 < ny; y0 += YT) {
+    const int rs = ln.kg * ln.cw;  // row stride inside a staged tile
+    if (ya < yb) stage_tile(spec, g, s, k0, kcnt, ln.kg, ya, rows, ln.ws_only, ln.cw, buf0);
+    int cur = 0;
+    for (int y0 = ya; y0 < yb; y0 += YT) {
+        cp_async_wait_all();
         __syncthreads();
-        // stage rows (y0 - G + r) mod ny, r in [0, rows), for the CTA's kcnt frequencies
-        const int nvec = rows * kcnt * vec_per_row;
-        for (int v = tid; v < nvec; v += blockDim.x) {
-            int r = v / (kcnt * vec_per_row);
-            int rem = v - r * (kcnt * vec_per_row);
-            int kk = rem / vec_per_row, c2 = rem - kk * vec_per_row;
-            int yy = ((y0 - G + r) % ny + ny) % ny;  // cyclic in y, any number of wraps
-            const float4 *src = reinterpret_cast<const float4 *>(base + (size_t)kk * kstride + (size_t)yy * NI) + c2;
-            reinterpret_cast<float4 *>(tile + ((size_t)r * g.kg + kk) * NI)[c2] = __ldg(src);
-        }
-        __syncthreads();
+        cpx<float> *tile = cur ? buf1 : buf0;
+        if (y0 + YT < yb) stage_tile(spec, g, s, k0, kcnt, ln.kg, y0 + YT, rows, ln.ws_only, ln.cw, cur ? buf0 : buf1);
         if (active) {
-            const int yvalid = min(YT, ny - y0);
-            const cpx<float> *ta = tile + (size_t)kl * NI + m.A;
-            const cpx<float> *tb = tile + (size_t)kl * NI + m.B;
-            const int rs = g.kg * NI;  // row stride in the tile
+            const int yvalid = min(YT, yb - y0);
+            const cpx<float> *ta = tile + (size_t)kl * ln.cw + m.A;
+            const cpx<float> *tb = tile + (size_t)kl * ln.cw + m.B;
             for (int yy = 0; yy < yvalid; yy += kTY) {
                 float2 a[kTY];
 #pragma unroll
@@ -147,54 +200,130 @@ __global__ void __launch_bounds__(256) k_ycorr_f32(const cpx<float> *__restrict_
                 acc[c] = make_float2(0.f, 0.f);
             }
         }
+        cur ^= 1;
     }
+    cp_async_wait_all();
     if (active) {
-        double *out = ypart + (((size_t)s * g.nkf + (k0 + kl)) * g.nent) * 2;
+        // (hi, lo) float pairs; K3 adds them in FP64 (keeps FP64 work off this kernel's tail)
+        float4 *out = reinterpret_cast<float4 *>(ypart) + (((size_t)s * ln.ysplit + ych) * g.nkf + (k0 + kl)) * g.nent;
 #pragma unroll
         for (int c = 0; c < C; c++) {
-            if (c >= m.c0 && c < m.cn) {
-                out[2 * (m.ent0 + c)] = (double)hi[c].x + (double)lo[c].x;
-                out[2 * (m.ent0 + c) + 1] = (double)hi[c].y + (double)lo[c].y;
-            }
+            if (c >= m.c0 && c < m.cn) out[m.ent0 + c] = make_float4(hi[c].x, hi[c].y, lo[c].x, lo[c].y);
         }
     }
 }
 
+// Same work as k_ycorr_f32 with Blackwell's packed FP32x2 FMA: the complex multiply-add
+// conj(a) w is split into two packed accumulators P += {a.re, a.re} * w and
+// Q += {a.im, a.im} * w (re = P.x + Q.y, im = P.y - Q.x at the fold), which halves the FMA
+// instruction count without any operand shuffles.
+template <int C, int TYP>
+__global__ void __launch_bounds__(256, 1) k_ycorr_f32x2(const cpx<float> *__restrict__ spec, Geometry g, Launch ln,
+                                                       double *__restrict__ ypart) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int YT = g.ytile, G = g.G, ny = g.ny;
+    const int rows = YT + 2 * G;
+    cpx<float> *buf0 = reinterpret_cast<cpx<float> *>(smem_raw);
+    cpx<float> *buf1 = buf0 + (size_t)rows * ln.kg * ln.cw;
+    const int s = blockIdx.x / ln.ysplit, ych = blockIdx.x % ln.ysplit;
+    const int k0 = blockIdx.y * ln.kg;
+    const int kcnt = min(ln.kg, g.nkf - k0);
+    const int chunk = (ny + ln.ysplit - 1) / ln.ysplit;
+    const int ya = ych * chunk, yb = min(ny, ya + chunk);
+    const int tid = threadIdx.x;
+    const int kl = tid / ln.items, it = tid - kl * ln.items;
+    const bool active = kl < kcnt;
+    Item m = decode_item(g, active ? it : 0, ln.ws_only);
+    float2 P[C], Q[C], hi[C], lo[C];
+#pragma unroll
+    for (int c = 0; c < C; c++) P[c] = Q[c] = hi[c] = lo[c] = make_float2(0.f, 0.f);
+    const int rs = ln.kg * ln.cw;
+    if (ya < yb) stage_tile(spec, g, s, k0, kcnt, ln.kg, ya, rows, ln.ws_only, ln.cw, buf0);
+    int cur = 0;
+    for (int y0 = ya; y0 < yb; y0 += YT) {
+        cp_async_wait_all();
+        __syncthreads();
+        cpx<float> *tile = cur ? buf1 : buf0;
+        if (y0 + YT < yb) stage_tile(spec, g, s, k0, kcnt, ln.kg, y0 + YT, rows, ln.ws_only, ln.cw, cur ? buf0 : buf1);
+        if (active) {
+            const int yvalid = min(YT, yb - y0);
+            const float2 *ta = reinterpret_cast<const float2 *>(tile + (size_t)kl * ln.cw + m.A);
+            const float2 *tb = reinterpret_cast<const float2 *>(tile + (size_t)kl * ln.cw + m.B);
+            for (int yy = 0; yy < yvalid; yy += TYP) {
+                float2 ar[TYP], ai[TYP];
+#pragma unroll
+                for (int t = 0; t < TYP; t++) {
+                    float2 v = ta[(size_t)(G + yy + t) * rs];
+                    bool ok = yy + t < yvalid;
+                    ar[t] = make_float2(ok ? v.x : 0.f, ok ? v.x : 0.f);
+                    ai[t] = make_float2(ok ? v.y : 0.f, ok ? v.y : 0.f);
+                }
+                float2 w[C + TYP - 1];
+#pragma unroll
+                for (int q = 0; q < C + TYP - 1; q++) w[q] = tb[(size_t)(G + yy + m.dylo + q) * rs];
+#pragma unroll
+                for (int t = 0; t < TYP; t++)
+#pragma unroll
+                    for (int c = 0; c < C; c++) {
+                        P[c] = __ffma2_rn(ar[t], w[t + c], P[c]);
+                        Q[c] = __ffma2_rn(ai[t], w[t + c], Q[c]);
+                    }
+            }
+#pragma unroll
+            for (int c = 0; c < C; c++) {
+                float s1, e1, s2, e2;
+                two_sum(hi[c].x, P[c].x + Q[c].y, s1, e1);
+                two_sum(hi[c].y, P[c].y - Q[c].x, s2, e2);
+                hi[c].x = s1;
+                lo[c].x += e1;
+                hi[c].y = s2;
+                lo[c].y += e2;
+                P[c] = Q[c] = make_float2(0.f, 0.f);
+            }
+        }
+        cur ^= 1;
+    }
+    cp_async_wait_all();
+    if (active) {
+        float4 *out = reinterpret_cast<float4 *>(ypart) + (((size_t)s * ln.ysplit + ych) * g.nkf + (k0 + kl)) * g.nent;
+#pragma unroll
+        for (int c = 0; c < C; c++)
+            if (c >= m.c0 && c < m.cn) out[m.ent0 + c] = make_float4(hi[c].x, hi[c].y, lo[c].x, lo[c].y);
+    }
+}
+
 template <int C>
-__global__ void __launch_bounds__(256) k_ycorr_f64(const cpx<double> *__restrict__ spec, Geometry g,
+__global__ void __launch_bounds__(256) k_ycorr_f64(const cpx<double> *__restrict__ spec, Geometry g, Launch ln,
                                                   double *__restrict__ ypart) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    cpx<double> *tile = reinterpret_cast<cpx<double> *>(smem_raw);
-    const int s = blockIdx.x;
-    const int k0 = blockIdx.y * g.kg;
-    const int kcnt = min(g.kg, g.nkf - k0);
-    const int G = g.G, ny = g.ny, YT = g.ytile, NI = g.nimg_pad;
+    const int YT = g.ytile, G = g.G, ny = g.ny;
     const int rows = YT + 2 * G;
+    cpx<double> *buf0 = reinterpret_cast<cpx<double> *>(smem_raw);
+    cpx<double> *buf1 = buf0 + (size_t)rows * ln.kg * ln.cw;
+    const int s = blockIdx.x / ln.ysplit, ych = blockIdx.x % ln.ysplit;
+    const int k0 = blockIdx.y * ln.kg;
+    const int kcnt = min(ln.kg, g.nkf - k0);
+    const int chunk = (ny + ln.ysplit - 1) / ln.ysplit;
+    const int ya = ych * chunk, yb = min(ny, ya + chunk);
     const int tid = threadIdx.x;
-    const int kl = tid / g.items_per_k, it = tid - kl * g.items_per_k;
+    const int kl = tid / ln.items, it = tid - kl * ln.items;
     const bool active = kl < kcnt;
-    Item m = decode_item(g, active ? it : 0);
+    Item m = decode_item(g, active ? it : 0, ln.ws_only);
     double2 acc[C];
 #pragma unroll
     for (int c = 0; c < C; c++) acc[c] = make_double2(0.0, 0.0);
-    const size_t kstride = (size_t)ny * NI;
-    const cpx<double> *base = spec + ((size_t)s * g.nkf + k0) * kstride;
-    for (int y0 = 0; y0 < ny; y0 += YT) {
+    const int rs = ln.kg * ln.cw;
+    if (ya < yb) stage_tile(spec, g, s, k0, kcnt, ln.kg, ya, rows, ln.ws_only, ln.cw, buf0);
+    int cur = 0;
+    for (int y0 = ya; y0 < yb; y0 += YT) {
+        cp_async_wait_all();
         __syncthreads();
-        const int nv = rows * kcnt * NI;
-        for (int v = tid; v < nv; v += blockDim.x) {
-            int r = v / (kcnt * NI);
-            int rem = v - r * (kcnt * NI);
-            int kk = rem / NI, c2 = rem - kk * NI;
-            int yy = ((y0 - G + r) % ny + ny) % ny;  // cyclic in y, any number of wraps
-            tile[((size_t)r * g.kg + kk) * NI + c2] = base[(size_t)kk * kstride + (size_t)yy * NI + c2];
-        }
-        __syncthreads();
+        cpx<double> *tile = cur ? buf1 : buf0;
+        if (y0 + YT < yb) stage_tile(spec, g, s, k0, kcnt, ln.kg, y0 + YT, rows, ln.ws_only, ln.cw, cur ? buf0 : buf1);
         if (active) {
-            const int yvalid = min(YT, ny - y0);
-            const cpx<double> *ta = tile + (size_t)kl * NI + m.A;
-            const cpx<double> *tb = tile + (size_t)kl * NI + m.B;
-            const int rs = g.kg * NI;
+            const int yvalid = min(YT, yb - y0);
+            const cpx<double> *ta = tile + (size_t)kl * ln.cw + m.A;
+            const cpx<double> *tb = tile + (size_t)kl * ln.cw + m.B;
             for (int yy = 0; yy < yvalid; yy++) {
                 cpx<double> a = ta[(size_t)(G + yy) * rs];
 #pragma unroll
@@ -207,9 +336,11 @@ __global__ void __launch_bounds__(256) k_ycorr_f64(const cpx<double> *__restrict
                 }
             }
         }
+        cur ^= 1;
     }
+    cp_async_wait_all();
     if (active) {
-        double *out = ypart + (((size_t)s * g.nkf + (k0 + kl)) * g.nent) * 2;
+        double *out = ypart + ((((size_t)s * ln.ysplit + ych) * g.nkf + (k0 + kl)) * g.nent) * 2;
 #pragma unroll
         for (int c = 0; c < C; c++)
             if (c >= m.c0 && c < m.cn) {
@@ -219,39 +350,135 @@ __global__ void __launch_bounds__(256) k_ycorr_f64(const cpx<double> *__restrict
     }
 }
 
+// W_i x S_m correlations of the refinement pass (the S_m slot holds the residual image):
+// one thread per (segment, row chunk, frequency, W_i), streaming the chunk's rows straight
+// from global memory with the L residual values of the lag window in a rotating register
+// window (the loop is unrolled by C so the rotation is free).  Output: (hi, lo) float pairs
+// per (segment, chunk, frequency, i, dy) -> wspart.
 template <int C>
-cudaError_t run(const Geometry &g, int precision, const void *spec, double *ypart, cudaStream_t st) {
-    dim3 grid(g.nseg, (g.nkf + g.kg - 1) / g.kg);
-    int threads = ((g.kg * g.items_per_k + 31) / 32) * 32;
+__global__ void __launch_bounds__(256) k_ycorr_ws(const cpx<float> *__restrict__ spec, Geometry g, int ychunks,
+                                                 float4 *__restrict__ wspart) {
+    const int nk = g.nk, nkf = g.nkf, ny = g.ny, NI = g.nimg_pad, h = g.h;
+    const int slot = 2 * nk + g.nb;
+    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long total = (long)g.nseg * ychunks * nkf * nk;
+    if (t >= total) return;
+    const int i = (int)(t % nk);
+    const int k = (int)((t / nk) % nkf);
+    const int sy = (int)(t / ((long)nk * nkf));
+    const int s = sy / ychunks, ych = sy % ychunks;
+    const int chunk = (ny + ychunks - 1) / ychunks;
+    const int ya = ych * chunk, yb = min(ny, ya + chunk);
+    const size_t rowstride = (size_t)nkf * NI;  // complex values between consecutive rows
+    const cpx<float> *base = spec + ((size_t)s * ny * nkf + k) * NI;
+    float2 acc[C], hi[C], lo[C], w[C];
+#pragma unroll
+    for (int c = 0; c < C; c++) {
+        acc[c] = hi[c] = lo[c] = make_float2(0.f, 0.f);
+    }
+    // window: w[c] = R(y - h + c) for the current row y (cyclic in y)
+#pragma unroll
+    for (int c = 0; c < C - 1; c++) {
+        int yy = ((ya - h + c) % ny + ny) % ny;
+        cpx<float> v = base[(size_t)yy * rowstride + slot];
+        w[c] = make_float2(v.re, v.im);
+    }
+    int y = ya;
+    while (y < yb) {
+#pragma unroll
+        for (int u = 0; u < C; u++) {
+            // entering value R(y + h) goes to slot (C - 1 + u) % C; lag dy = c - h sits in slot (c + u) % C
+            if (y + u < yb) {
+                int yy = y + u + h;
+                yy = yy >= ny ? yy - ny : yy;
+                cpx<float> v = base[(size_t)yy * rowstride + slot];
+                w[(C - 1 + u) % C] = make_float2(v.re, v.im);
+                cpx<float> av = base[(size_t)(y + u) * rowstride + i];
+#pragma unroll
+                for (int c = 0; c < C; c++) {
+                    const float2 b = w[(c + u) % C];
+                    acc[c].x = fmaf(av.re, b.x, acc[c].x);
+                    acc[c].x = fmaf(av.im, b.y, acc[c].x);
+                    acc[c].y = fmaf(av.re, b.y, acc[c].y);
+                    acc[c].y = fmaf(-av.im, b.x, acc[c].y);
+                }
+            }
+        }
+        // rotate so that slot 0 again holds R(y_next - h): the unrolled block advanced C rows,
+        // which maps every slot back onto itself
+        y += C;
+#pragma unroll
+        for (int c = 0; c < C; c++) {
+            float s1, e1, s2, e2;
+            two_sum(hi[c].x, acc[c].x, s1, e1);
+            two_sum(hi[c].y, acc[c].y, s2, e2);
+            hi[c].x = s1;
+            lo[c].x += e1;
+            hi[c].y = s2;
+            lo[c].y += e2;
+            acc[c] = make_float2(0.f, 0.f);
+        }
+    }
+    float4 *out = wspart + (((size_t)sy * nkf + k) * nk + i) * C;
+#pragma unroll
+    for (int c = 0; c < C; c++) out[c] = make_float4(hi[c].x, hi[c].y, lo[c].x, lo[c].y);
+}
+
+template <int C>
+cudaError_t run_ws(const Geometry &g, const void *spec, float4 *wspart, cudaStream_t st) {
+    const long total = (long)g.nseg * g.ychunks_ws * g.nkf * g.nk;
+    note_launch();
+    k_ycorr_ws<C><<<(unsigned)((total + 255) / 256), 256, 0, st>>>((const cpx<float> *)spec, g, g.ychunks_ws, wspart);
+    return cudaGetLastError();
+}
+
+template <int C>
+cudaError_t run(const Geometry &g, int precision, const void *spec, double *ypart, bool ws_only, cudaStream_t st) {
+    if (ws_only && precision != SFFT_PREC_FP64) return run_ws<C>(g, spec, reinterpret_cast<float4 *>(ypart), st);
+    Launch ln;
+    ln.ws_only = ws_only;
+    ln.items = ws_only ? g.nk : g.items_per_k;
+    ln.kg = ws_only ? g.kg_ws : g.kg;
+    ln.ngroups = (g.nkf + ln.kg - 1) / ln.kg;
+    ln.ysplit = g.ysplit;
+    ln.cw = ws_only ? ws_nka(g) + 2 : g.nimg_pad;
+    dim3 grid(g.nseg * ln.ysplit, ln.ngroups);
+    int threads = ((ln.kg * ln.items + 31) / 32) * 32;
     size_t rows = (size_t)g.ytile + 2 * g.G;
     if (precision == SFFT_PREC_FP64) {
-        size_t sm = rows * g.kg * g.nimg_pad * sizeof(cpx<double>);
+        size_t sm = 2 * rows * ln.kg * ln.cw * sizeof(cpx<double>);
         cudaError_t e = cudaFuncSetAttribute(k_ycorr_f64<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return e;
         note_launch();
-        k_ycorr_f64<C><<<grid, threads, sm, st>>>((const cpx<double> *)spec, g, ypart);
+        k_ycorr_f64<C><<<grid, threads, sm, st>>>((const cpx<double> *)spec, g, ln, ypart);
     } else {
-        size_t sm = rows * g.kg * g.nimg_pad * sizeof(cpx<float>);
-        cudaError_t e = cudaFuncSetAttribute(k_ycorr_f32<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        size_t sm = 2 * rows * ln.kg * ln.cw * sizeof(cpx<float>);
+        // packed FP32x2 variant unless SFFT_YCORR_SCALAR is set (kept for A/B comparison)
+        static const bool scalar = getenv("SFFT_YCORR_SCALAR") != nullptr;
+        auto kern = scalar ? k_ycorr_f32<C> : k_ycorr_f32x2<C, 4>;
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
         if (e != cudaSuccess) return e;
         note_launch();
-        k_ycorr_f32<C><<<grid, threads, sm, st>>>((const cpx<float> *)spec, g, ypart);
+        kern<<<grid, threads, sm, st>>>((const cpx<float> *)spec, g, ln, ypart);
     }
     return cudaGetLastError();
 }
 
 }  // namespace
 
-cudaError_t launch_ycorr(const Geometry &g, int precision, const void *spec, double *ypart, cudaStream_t st) {
+cudaError_t launch_ycorr(const Geometry &g, int precision, const void *spec, double *ypart, bool ws_only,
+                         cudaStream_t st) {
     switch (g.C) {
-        case 1: return run<1>(g, precision, spec, ypart, st);
-        case 3: return run<3>(g, precision, spec, ypart, st);
-        case 5: return run<5>(g, precision, spec, ypart, st);
-        case 7: return run<7>(g, precision, spec, ypart, st);
-        case 9: return run<9>(g, precision, spec, ypart, st);
-        case 11: return run<11>(g, precision, spec, ypart, st);
-        case 13: return run<13>(g, precision, spec, ypart, st);
-        case 15: return run<15>(g, precision, spec, ypart, st);
+        case 1: return run<1>(g, precision, spec, ypart, ws_only, st);
+        case 3: return run<3>(g, precision, spec, ypart, ws_only, st);
+        case 5: return run<5>(g, precision, spec, ypart, ws_only, st);
+        case 7: return run<7>(g, precision, spec, ypart, ws_only, st);
+        case 9: return run<9>(g, precision, spec, ypart, ws_only, st);
+        case 11: return run<11>(g, precision, spec, ypart, ws_only, st);
+        case 13: return run<13>(g, precision, spec, ypart, ws_only, st);
+        case 15: return run<15>(g, precision, spec, ypart, ws_only, st);
         default: return cudaErrorInvalidValue;
     }
 }
