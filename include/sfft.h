@@ -145,6 +145,29 @@ sfft_status sfft_batch(const sfft_desc *base, int32_t n_sci, int32_t n_tmpl, con
                        const int32_t *nx, double *const *coeffs, void *const *diff,
                        sfft_fit_info *infos, sfft_stream_t stream);
 
+/* Difference image exactly like sfft_subtract, but without a plan and without allocating:
+ * no cudaMalloc, no cudaFree, no library routine that allocates.  The paper has no
+ * counterpart; this entry point exists for callers that cannot allocate device memory at
+ * the point where they need the difference image -- for example code whose device memory
+ * is owned by another allocator (a framework's caching allocator or a fixed-size arena that
+ * must not be bypassed) or a latency-critical path that cannot afford the implicit device
+ * synchronisation cudaMalloc and cudaFree may perform.
+ *
+ * desc gives the frame geometry, basis, dtype and precision (solver fields are ignored);
+ * sci, tmpl, coeffs (n doubles) and diff are device pointers as for sfft_subtract, with
+ * pitch = desc->pitch (0 = nx), queued on `stream`.  The scratch -- the coordinate-power
+ * table and the folded kernel coefficients, (max(dk,db)+1) nx + ny (L^2 (dk+1) + db + 1)
+ * values of 4 bytes (8 for SFFT_PREC_FP64) -- lives in one fixed 16 MiB device array that
+ * every GPU which loads the library holds until the process exits; a frame that needs more
+ * is rejected with SFFT_ERR_INVALID_ARG (message in sfft_last_error(NULL)).  The first call
+ * on each device looks up that array's device address (cudaGetSymbolAddress, once per
+ * device, with the device current); make that first call before any stream capture.  All
+ * calls share the array and each call overwrites everything it reads, so nothing carries
+ * over from the previous call, but calls that overlap on the GPU (different streams,
+ * or different host threads on one device) race on it and must be serialised. */
+sfft_status sfft_subtract_noalloc(const sfft_desc *desc, const void *sci, const void *tmpl,
+                                  const double *coeffs, void *diff, sfft_stream_t stream);
+
 /* Stage timing (instrumentation; the paper profiles its pipeline stage by stage, Sec. "GPU
  * acceleration and performance").  With enable != 0 every later call records CUDA events
  * around its stages on the plan's stream.  sfft_stage_times synchronises the stream, adds

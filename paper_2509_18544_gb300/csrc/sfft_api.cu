@@ -38,6 +38,8 @@ size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 namespace sfft {
 
+void set_global_error(const char *msg) { set_err(nullptr, "%s", msg); }
+
 bool make_geometry(const sfft_desc &d, Geometry &g, char *err, size_t errlen) {
     memset(&g, 0, sizeof g);
     if (d.ny < 1 || d.nx < 1) return snprintf(err, errlen, "ny, nx must be >= 1"), false;

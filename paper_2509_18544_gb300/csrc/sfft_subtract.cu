@@ -209,3 +209,123 @@ cudaError_t launch_subtract(const Geometry &g, int dtype, int precision, const v
 }
 
 }  // namespace sfft
+
+// ---------------------------------------------------------------------------------------
+// Difference image without any allocation: the same fold and subtract kernels, with their
+// scratch (coordinate powers and folded coefficients) in a fixed device array that the
+// library holds for the life of the process.
+#include <stdio.h>
+
+#include <mutex>
+
+namespace sfft {
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = (size_t)16 << 20;  // 16 MiB, on every device that loads the library
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void *g_noalloc_ptr[kMaxDevices] = {};
+
+// xh^p for p < np, FP64 powers rounded once (the table the planned path uploads)
+template <class R>
+__global__ void k_xpow_table(int nx, int np, R *__restrict__ out) {
+    int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= nx) return;
+    double c = nx > 1 ? (2.0 * x - (nx - 1)) / (double)(nx - 1) : 0.0, v = 1.0;
+    for (int p = 0; p < np; p++) {
+        out[(size_t)p * nx + x] = (R)v;
+        v *= c;
+    }
+}
+
+size_t align256(size_t v) { return (v + 255) / 256 * 256; }
+
+}  // namespace
+
+void set_global_error(const char *msg);
+
+}  // namespace sfft
+
+using namespace sfft;
+
+extern "C" sfft_status sfft_subtract_noalloc(const sfft_desc *desc, const void *sci, const void *tmpl,
+                                             const double *coeffs, void *diff, sfft_stream_t stream) {
+    char err[256];
+    if (!desc || !sci || !tmpl || !coeffs || !diff) {
+        set_global_error("sfft_subtract_noalloc: null argument");
+        return SFFT_ERR_INVALID_ARG;
+    }
+    Geometry g;
+    if (!make_geometry(*desc, g, err, sizeof err)) {
+        set_global_error(err);
+        return SFFT_ERR_INVALID_ARG;
+    }
+    if (diff == sci || diff == tmpl || (reinterpret_cast<uintptr_t>(sci) & 15) || (reinterpret_cast<uintptr_t>(tmpl) & 15)) {
+        set_global_error("sfft_subtract_noalloc: diff aliases an input, or an input is not 16-byte aligned");
+        return SFFT_ERR_INVALID_ARG;
+    }
+    if (g.dk > 7 || g.db > 7) {
+        set_global_error("sfft_subtract_noalloc: dk and db must be <= 7");
+        return SFFT_ERR_INVALID_ARG;
+    }
+    const size_t rsz = desc->precision == SFFT_PREC_FP64 ? 8 : 4;
+    const int npx = (g.dk > g.db ? g.dk : g.db) + 1;
+    const size_t xpow_bytes = align256((size_t)npx * g.nx * rsz);
+    const size_t fold_bytes = align256(((size_t)g.ny * g.L * g.L * (g.dk + 1) + (size_t)g.ny * (g.db + 1)) * rsz);
+    if (xpow_bytes + fold_bytes > kNoAllocScratchBytes) {
+        snprintf(err, sizeof err,
+                 "sfft_subtract_noalloc: this frame needs %zu bytes of scratch, the fixed device array holds %zu",
+                 xpow_bytes + fold_bytes, kNoAllocScratchBytes);
+        set_global_error(err);
+        return SFFT_ERR_INVALID_ARG;
+    }
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+        set_global_error("sfft_subtract_noalloc: no current CUDA device");
+        return SFFT_ERR_CUDA;
+    }
+    void *scratch = nullptr;
+    {
+        // once per device, with that device current: the device address of the array
+        std::lock_guard<std::mutex> lk(g_noalloc_mu);
+        if (!g_noalloc_ptr[dev]) {
+            void *ptr = nullptr;
+            e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+            if (e != cudaSuccess) {
+                snprintf(err, sizeof err, "sfft_subtract_noalloc: cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+                set_global_error(err);
+                return SFFT_ERR_CUDA;
+            }
+            g_noalloc_ptr[dev] = ptr;
+        }
+        scratch = g_noalloc_ptr[dev];
+    }
+    // every value of both tables is written below before any kernel reads it, so the
+    // previous call's contents never leak into this one
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    void *xpow = scratch;
+    void *cfold = static_cast<unsigned char *>(scratch) + xpow_bytes;
+    note_launch();
+    if (rsz == 8)
+        k_xpow_table<double><<<(g.nx + 255) / 256, 256, 0, st>>>(g.nx, npx, (double *)xpow);
+    else
+        k_xpow_table<float><<<(g.nx + 255) / 256, 256, 0, st>>>(g.nx, npx, (float *)xpow);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) {
+        if (desc->precision == SFFT_PREC_FP64)
+            e = desc->dtype == SFFT_F64 ? dispatch_L<double, double>(g, sci, tmpl, nullptr, false, coeffs, xpow, cfold, diff, st)
+                                        : dispatch_L<double, float>(g, sci, tmpl, nullptr, false, coeffs, xpow, cfold, diff, st);
+        else
+            e = desc->dtype == SFFT_F64 ? dispatch_L<float, double>(g, sci, tmpl, nullptr, false, coeffs, xpow, cfold, diff, st)
+                                        : dispatch_L<float, float>(g, sci, tmpl, nullptr, false, coeffs, xpow, cfold, diff, st);
+    }
+    if (e != cudaSuccess) {
+        snprintf(err, sizeof err, "sfft_subtract_noalloc: %s", cudaGetErrorString(e));
+        set_global_error(err);
+        return SFFT_ERR_CUDA;
+    }
+    return SFFT_OK;
+}

@@ -21,7 +21,7 @@ SOLVE_CHOLESKY, SOLVE_PCG = 0, 1
 
 EXPORTED = ("sfft_plan", "sfft_destroy", "sfft_n_unknowns", "sfft_workspace_size", "sfft_set_stream",
             "sfft_normal", "sfft_fit", "sfft_subtract", "sfft_sync_status", "sfft_batch",
-            "sfft_profile", "sfft_stage_times", "sfft_launch_count",
+            "sfft_profile", "sfft_stage_times", "sfft_launch_count", "sfft_subtract_noalloc",
             "sfft_status_string", "sfft_last_error")
 NSTAGES = 8
 STAGES = ("segment_fft", "moments", "ycorr", "lag_tables", "assemble", "solve", "subtract", "refine")
@@ -73,6 +73,7 @@ def load_library(path: str = LIB_PATH):
         lib.sfft_sync_status.argtypes = [P]
         lib.sfft_batch.argtypes = [ctypes.POINTER(sfft_desc), I32, I32, P, P, P, P, P, P, P,
                                    ctypes.POINTER(sfft_fit_info), P]
+        lib.sfft_subtract_noalloc.argtypes = [ctypes.POINTER(sfft_desc), P, P, P, P, P]
         lib.sfft_profile.argtypes = [P, I32]
         lib.sfft_stage_times.argtypes = [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(I32)]
         lib.sfft_launch_count.argtypes = [ctypes.POINTER(ctypes.c_uint64)]
@@ -230,3 +231,9 @@ def sfft_launch_count() -> int:
     v = ctypes.c_uint64()
     _check(load_library().sfft_launch_count(ctypes.byref(v)))
     return v.value
+
+
+def sfft_subtract_noalloc(desc: sfft_desc, sci, tmpl, coeffs, diff, stream=None):
+    """Plan-free difference image whose scratch is a fixed device array (no allocation)."""
+    _check(load_library().sfft_subtract_noalloc(ctypes.byref(desc), _ptr(sci), _ptr(tmpl), _ptr(coeffs),
+                                                _ptr(diff), _stream(stream)))
