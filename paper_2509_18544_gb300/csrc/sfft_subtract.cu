@@ -11,6 +11,8 @@
 // CTA: 8 output rows x 256 columns; a warp per row, 8 consecutive pixels per thread.
 // Shared memory holds the cyclic template window (rows y0-h.., columns x0-h..), the x
 // powers of its columns and the folded coefficients for the CTA's rows.
+#include <type_traits>
+
 #include "sfft_internal.cuh"
 
 namespace sfft {
@@ -63,6 +65,43 @@ __global__ void k_fold(const double *__restrict__ coeffs, Geometry g, R *__restr
     }
 }
 
+// Stages a CTA's cyclic template window (times xh^p, masked when `masked`), the folded
+// coefficients of its kRows output rows and their background x-power sums in shared memory.
+template <class R, class In, int LL, int kRows>
+__device__ __forceinline__ void stage_window(const In *__restrict__ tmpl, const uint8_t *__restrict__ mask,
+                                             bool masked, const Geometry &g, const R *__restrict__ cfold,
+                                             const R *__restrict__ xpow_g, int x0, int y0, R *Tp, R *cf, R *byp) {
+    constexpr int h = LL / 2;
+    constexpr int WC = kColsO + 2 * h;
+    constexpr int WCS = WC + WC / 8 + 1;
+    constexpr int WR = kRows + 2 * h;
+    const int np = g.dk + 1, nx = g.nx, ny = g.ny, tid = threadIdx.x;
+    for (int e = tid; e < WR * WC; e += blockDim.x) {
+        int r = e / WC, c = e - r * WC;
+        int yy = ((y0 - h + r) % ny + ny) % ny;
+        int xx = ((x0 - h + c) % nx + nx) % nx;
+        size_t u = (size_t)yy * g.pitch + xx;
+        // the residual of the fit convolves the masked template W_i = w_i T_m
+        R tv = (masked && mask && mask[u]) ? (R)0 : (R)tmpl[u];
+        for (int p = 0; p < np; p++) Tp[(p * WR + r) * WCS + skew(c)] = tv * xpow_g[(size_t)p * nx + xx];
+    }
+    // folded kernel coefficients c_p(d, y - dy) for each of the CTA's output rows
+    const int ncf = kRows * LL * np * LL;
+    for (int e = tid; e < ncf; e += blockDim.x) {
+        int dxi = e % LL, rest = e / LL;
+        int p = rest % np;
+        rest /= np;
+        int dyi = rest % LL, ry = rest / LL;
+        int ys = (((y0 + ry) - (dyi - h)) % ny + ny) % ny;  // source row y - dy
+        cf[e] = cfold[(((size_t)ys * LL + dyi) * np + p) * LL + dxi];
+    }
+    const R *bgf = cfold + (size_t)ny * LL * LL * np;
+    for (int e = tid; e < kRows * (g.db + 1); e += blockDim.x) {
+        int ry = e / (g.db + 1), p = e % (g.db + 1);
+        byp[e] = bgf[(size_t)min(y0 + ry, ny - 1) * (g.db + 1) + p];
+    }
+}
+
 template <class R, class In, int LL>
 __global__ void __launch_bounds__(256) k_subtract(const In *__restrict__ sci, const In *__restrict__ tmpl,
                                                  const uint8_t *__restrict__ mask, bool residual, Geometry g,
@@ -83,30 +122,7 @@ __global__ void __launch_bounds__(256) k_subtract(const In *__restrict__ sci, co
     const int tid = threadIdx.x;
     const int nx = g.nx, ny = g.ny;
 
-    for (int e = tid; e < WR * WC; e += blockDim.x) {
-        int r = e / WC, c = e - r * WC;
-        int yy = ((y0 - h + r) % ny + ny) % ny;
-        int xx = ((x0 - h + c) % nx + nx) % nx;
-        size_t u = (size_t)yy * g.pitch + xx;
-        // the residual of the fit convolves the masked template W_i = w_i T_m
-        R tv = (residual && mask && mask[u]) ? (R)0 : (R)tmpl[u];
-        for (int p = 0; p < np; p++) Tp[(p * WR + r) * WCS + skew(c)] = tv * xpow_g[(size_t)p * nx + xx];
-    }
-    // folded kernel coefficients c_p(d, y - dy) for each of the CTA's output rows
-    const int ncf = kRowsO * LL * np * LL;
-    for (int e = tid; e < ncf; e += blockDim.x) {
-        int dxi = e % LL, rest = e / LL;
-        int p = rest % np;
-        rest /= np;
-        int dyi = rest % LL, ry = rest / LL;
-        int ys = (((y0 + ry) - (dyi - h)) % ny + ny) % ny;  // source row y - dy
-        cf[e] = cfold[(((size_t)ys * LL + dyi) * np + p) * LL + dxi];
-    }
-    const R *bgf = cfold + (size_t)ny * LL * LL * np;
-    for (int e = tid; e < kRowsO * (g.db + 1); e += blockDim.x) {
-        int ry = e / (g.db + 1), p = e % (g.db + 1);
-        byp[e] = bgf[(size_t)min(y0 + ry, ny - 1) * (g.db + 1) + p];
-    }
+    stage_window<R, In, LL, kRowsO>(tmpl, mask, residual, g, cfold, xpow_g, x0, y0, Tp, cf, byp);
     __syncthreads();
 
     const int ty = tid >> 5, lane = tid & 31;
@@ -153,6 +169,143 @@ __global__ void __launch_bounds__(256) k_subtract(const In *__restrict__ sci, co
     }
 }
 
+// ---------------------------------------------------------------------------------------
+// Residual of the fit for the FP32 path, R = S_m - sum a (w T_m)(u - d) - m sum b w, in
+// compensated arithmetic.  At a star core |S| is ~100x the residual, so plain FP32 sums
+// leave rounding errors of order u |S| in R; fitted back onto the basis by the refinement
+// step they bound the coefficients near 1e-6.  The terms that carry |S| are those near the
+// kernel centre, where both the kernel and the star's profile peak: for |dx|, |dy| <= kCore
+// every product is split exactly (p + e = c w, e from an FMA) and the running sum is a
+// hi + lo pair updated by an error-free two-sum (Knuth).  The outer lags, whose terms are
+// the product of two wings, accumulate in plain FP32 in a separate sum.  R then carries
+// about the rounding of its operands (the folded coefficients and xh^p T_m, each rounded
+// once to FP32).  Each thread holds two output rows (ty, ty + kRowsC / 2) as the two lanes
+// of packed FP32x2 operations.
+constexpr int kRowsC = 8;
+constexpr int kCore = 2;
+
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+
+// s + e = a + b exactly (round-to-nearest adds, no reassociation: the _rn intrinsics are
+// never contracted or reordered by the compiler)
+__device__ __forceinline__ void two_sum2(float2 a, float2 b, float2 &s, float2 &e) {
+    s = __fadd2_rn(a, b);
+    float2 bb = __fadd2_rn(s, neg2(a));
+    e = __fadd2_rn(__fadd2_rn(a, neg2(__fadd2_rn(s, neg2(bb)))), __fadd2_rn(b, neg2(bb)));
+}
+
+template <class In>
+__device__ __forceinline__ void split_input(In v, float &hi, float &lo) {
+    hi = (float)v;
+    lo = (float)((double)v - (double)hi);
+}
+template <>
+__device__ __forceinline__ void split_input<float>(float v, float &hi, float &lo) {
+    hi = v;
+    lo = 0.f;
+}
+
+template <class In, int LL>
+__global__ void __launch_bounds__(128, 2) k_residual_comp(const In *__restrict__ sci, const In *__restrict__ tmpl,
+                                                      const uint8_t *__restrict__ mask, Geometry g,
+                                                      const float *__restrict__ cfold,
+                                                      const float *__restrict__ xpow_g, In *__restrict__ resid) {
+    constexpr int h = LL / 2;
+    constexpr int WC = kColsO + 2 * h;
+    constexpr int WCS = WC + WC / 8 + 1;
+    constexpr int WR = kRowsC + 2 * h;
+    constexpr int NW = kRX + LL - 1;
+    constexpr int kHalf = kRowsC / 2;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int np = g.dk + 1, nx = g.nx, ny = g.ny;
+    float *Tp = reinterpret_cast<float *>(smem_raw);  // [np][WR][WCS]
+    float *cf = Tp + np * WR * WCS;                    // [kRowsC][LL][np][LL]
+    float *byp = cf + kRowsC * LL * np * LL;           // [kRowsC][db+1]
+
+    const int x0 = blockIdx.x * kColsO, y0 = blockIdx.y * kRowsC;
+    stage_window<float, In, LL, kRowsC>(tmpl, mask, true, g, cfold, xpow_g, x0, y0, Tp, cf, byp);
+    __syncthreads();
+
+    const int ty = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int cx = lane * kRX;
+    const int ya = y0 + ty, yb = ya + kHalf;
+    float2 hi[kRX], lo[kRX];
+    // start from m (S - bg): S split exactly into hi + lo, the background subtracted by two-sum
+#pragma unroll
+    for (int r = 0; r < kRX; r++) {
+        const int x = x0 + cx + r;
+        float sh[2] = {0.f, 0.f}, sl[2] = {0.f, 0.f}, bg[2] = {0.f, 0.f};
+#pragma unroll
+        for (int k = 0; k < 2; k++) {
+            const int y = k ? yb : ya;
+            if (y < ny && x < nx) {
+                const size_t u = (size_t)y * g.pitch + x;
+                if (!(mask && mask[u])) {
+                    split_input<In>(sci[u], sh[k], sl[k]);
+                    const float *bp = byp + (k ? ty + kHalf : ty) * (g.db + 1);
+                    float b = 0.f;
+                    for (int p = 0; p <= g.db; p++) b = fmaf(bp[p], xpow_g[(size_t)p * nx + x], b);
+                    bg[k] = b;
+                }
+            }
+        }
+        float2 s, e;
+        two_sum2(make_float2(sh[0], sh[1]), make_float2(-bg[0], -bg[1]), s, e);
+        hi[r] = s;
+        lo[r] = __fadd2_rn(e, make_float2(sl[0], sl[1]));
+    }
+    float2 wing[kRX];
+#pragma unroll
+    for (int r = 0; r < kRX; r++) wing[r] = make_float2(0.f, 0.f);
+    for (int dyi = 0; dyi < LL; dyi++) {
+        const int wra = ty + (LL - 1) - dyi, wrb = wra + kHalf;
+        const bool core_row = dyi >= h - kCore && dyi <= h + kCore;
+        for (int p = 0; p < np; p++) {
+            const float *ta = Tp + (p * WR + wra) * WCS, *tb = Tp + (p * WR + wrb) * WCS;
+            float2 wp[NW];
+#pragma unroll
+            for (int m = 0; m < NW; m++) wp[m] = make_float2(ta[skew(cx + m)], tb[skew(cx + m)]);
+            const float *ca = cf + ((ty * LL + dyi) * np + p) * LL;
+            const float *cb = cf + (((ty + kHalf) * LL + dyi) * np + p) * LL;
+            if (core_row) {
+#pragma unroll
+                for (int dxi = 0; dxi < LL; dxi++) {
+                    const float2 cc = make_float2(ca[dxi], cb[dxi]);
+                    if (dxi >= h - kCore && dxi <= h + kCore) {
+#pragma unroll
+                        for (int r = 0; r < kRX; r++) {
+                            const float2 w = wp[r + (LL - 1) - dxi];
+                            const float2 pr = __fmul2_rn(cc, w);
+                            const float2 pe = __ffma2_rn(cc, w, neg2(pr));  // cc w - pr, exact
+                            float2 s, e;
+                            two_sum2(hi[r], neg2(pr), s, e);
+                            hi[r] = s;
+                            lo[r] = __fadd2_rn(lo[r], __fadd2_rn(e, neg2(pe)));
+                        }
+                    } else {
+#pragma unroll
+                        for (int r = 0; r < kRX; r++) wing[r] = __ffma2_rn(cc, wp[r + (LL - 1) - dxi], wing[r]);
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int dxi = 0; dxi < LL; dxi++) {
+                    const float2 cc = make_float2(ca[dxi], cb[dxi]);
+#pragma unroll
+                    for (int r = 0; r < kRX; r++) wing[r] = __ffma2_rn(cc, wp[r + (LL - 1) - dxi], wing[r]);
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < kRX; r++) {
+        const int x = x0 + cx + r;
+        if (x >= nx) continue;
+        if (ya < ny) resid[(size_t)ya * g.pitch + x] = (In)((double)hi[r].x + ((double)lo[r].x - (double)wing[r].x));
+        if (yb < ny) resid[(size_t)yb * g.pitch + x] = (In)((double)hi[r].y + ((double)lo[r].y - (double)wing[r].y));
+    }
+}
+
 template <class R, class In, int LL>
 cudaError_t run(const Geometry &g, const void *sci, const void *tmpl, const uint8_t *mask, bool residual,
                 const double *coeffs, const void *xpow, void *cfold, void *diff, cudaStream_t st) {
@@ -166,6 +319,23 @@ cudaError_t run(const Geometry &g, const void *sci, const void *tmpl, const uint
     constexpr int WCS = (kColsO + 2 * h) + (kColsO + 2 * h) / 8 + 1;
     size_t sm = sizeof(R) * ((size_t)np * (kRowsO + 2 * h) * WCS +
                              (size_t)kRowsO * LL * np * LL + (size_t)kRowsO * (g.db + 1));
+    if constexpr (std::is_same<R, float>::value) {
+        if (residual) {
+            const size_t smc = sizeof(float) * ((size_t)np * (kRowsC + 2 * h) * WCS +
+                                                (size_t)kRowsC * LL * np * LL + (size_t)kRowsC * (g.db + 1));
+            auto kc = k_residual_comp<In, LL>;
+            cudaError_t e = cudaFuncSetAttribute(kc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smc);
+            if (e == cudaSuccess)
+                e = cudaFuncSetAttribute(kc, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                         cudaSharedmemCarveoutMaxShared);
+            if (e != cudaSuccess) return e;
+            dim3 gridc((g.nx + kColsO - 1) / kColsO, (g.ny + kRowsC - 1) / kRowsC);
+            note_launch();
+            kc<<<gridc, 128, smc, st>>>((const In *)sci, (const In *)tmpl, mask, g, (const float *)cfold,
+                                        (const float *)xpow, (In *)diff);
+            return cudaGetLastError();
+        }
+    }
     auto kern = k_subtract<R, In, LL>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e == cudaSuccess)
