@@ -8,20 +8,13 @@
 //
 // The folded coefficients depend only on the source row, so k_fold tabulates them once per
 // call (FP64 sums rounded once) for every row: cf[ys][dy][p][dx] and bg[y][p].
-// CTA: 8 output rows x 256 columns; a warp per row, 8 consecutive pixels per thread.
-// Shared memory holds the cyclic template window (rows y0-h.., columns x0-h..), the x
-// powers of its columns and the folded coefficients for the CTA's rows.
+#include <algorithm>
 #include <type_traits>
 
 #include "sfft_internal.cuh"
 
 namespace sfft {
 namespace {
-
-constexpr int kRowsO = 8, kRX = 8, kColsO = 32 * kRX;
-// Each lane reads a window starting at column 8 * lane; a skew of one word every 8 columns
-// (index c + c / 8) makes the 32 lanes' addresses 9 words apart, i.e. on 32 distinct banks.
-__device__ __forceinline__ int skew(int c) { return c + (c >> 3); }
 
 template <class R>
 __device__ __forceinline__ R coordv(int i, int n) {
@@ -65,107 +58,154 @@ __global__ void k_fold(const double *__restrict__ coeffs, Geometry g, R *__restr
     }
 }
 
-// Stages a CTA's cyclic template window (times xh^p, masked when `masked`), the folded
-// coefficients of its kRows output rows and their background x-power sums in shared memory.
-template <class R, class In, int LL, int kRows>
-__device__ __forceinline__ void stage_window(const In *__restrict__ tmpl, const uint8_t *__restrict__ mask,
-                                             bool masked, const Geometry &g, const R *__restrict__ cfold,
-                                             const R *__restrict__ xpow_g, int x0, int y0, R *Tp, R *cf, R *byp) {
-    constexpr int h = LL / 2;
-    constexpr int WC = kColsO + 2 * h;
-    constexpr int WCS = WC + WC / 8 + 1;
-    constexpr int WR = kRows + 2 * h;
-    const int np = g.dk + 1, nx = g.nx, ny = g.ny, tid = threadIdx.x;
-    for (int e = tid; e < WR * WC; e += blockDim.x) {
-        int r = e / WC, c = e - r * WC;
-        int yy = ((y0 - h + r) % ny + ny) % ny;
-        int xx = ((x0 - h + c) % nx + nx) % nx;
-        size_t u = (size_t)yy * g.pitch + xx;
-        // the residual of the fit convolves the masked template W_i = w_i T_m
-        R tv = (masked && mask && mask[u]) ? (R)0 : (R)tmpl[u];
-        for (int p = 0; p < np; p++) Tp[(p * WR + r) * WCS + skew(c)] = tv * xpow_g[(size_t)p * nx + xx];
+// Streaming layout: a CTA owns a strip of kCols<R> output columns and a chunk of rows, which
+// it walks in bands of kBand rows.  Shared memory keeps a ring of kBand + 2h template rows
+// (each as np planes xh^p T, for the strip's columns plus the h-column halo on each side),
+// so every source row is staged once per chunk; after a band the kBand rows no longer
+// needed are overwritten by the next band's new rows.  The folded coefficients of a band's
+// rows are staged beside it.
+constexpr int kBand = 8;
+template <class R> struct Tile {
+    static constexpr int kRX = 32 / (int)sizeof(R);   // consecutive pixels per lane
+    static constexpr int kCols = 32 * kRX;            // strip width
+};
+// Lanes read register windows starting kRX columns apart; one pad word every 8 floats
+// (every 4 doubles) puts the 32 lanes' (16 half-warp lanes') reads on distinct banks.
+template <class R>
+__device__ __forceinline__ int skew(int c) { return sizeof(R) == 4 ? c + (c >> 3) : c + (c >> 2); }
+template <class R, int LL> struct Win {
+    static constexpr int h = LL / 2;
+    static constexpr int WC = Tile<R>::kCols + 2 * h;                               // window columns
+    static constexpr int WCS = sizeof(R) == 4 ? WC + WC / 8 + 1 : WC + WC / 4 + 1;  // skewed row length
+    static constexpr int RING = kBand + 2 * h;                                       // ring rows
+    static constexpr int NW = Tile<R>::kRX + LL - 1;                                 // register window
+};
+
+__device__ __forceinline__ int wrapi(int v, int n) {
+    if (v >= 0 && v < n) return v;
+    v %= n;
+    return v < 0 ? v + n : v;
+}
+
+template <class R, int LL>
+size_t stream_smem(int np, int db) {
+    using W = Win<R, LL>;
+    return sizeof(R) * ((size_t)np * W::RING * W::WCS + (size_t)kBand * LL * np * LL + (size_t)kBand * (db + 1));
+}
+
+// Stages `count` consecutive source rows starting at (unwrapped) row ys0 into their ring
+// slots, as np planes xh^p T (T_m when `masked`).
+template <class R, class In, int LL>
+__device__ __forceinline__ void stage_rows(const In *__restrict__ tmpl, const uint8_t *__restrict__ mask, bool masked,
+                                           const Geometry &g, const R *__restrict__ xpow_g, int x0, int ys0, int count,
+                                           int ring_origin, R *Tp) {
+    using W = Win<R, LL>;
+    const int np = g.dk + 1, nx = g.nx;
+    for (int e = threadIdx.x; e < count * W::WC; e += blockDim.x) {
+        const int r = e / W::WC, c = e - r * W::WC;
+        const int ys = ys0 + r;
+        const int yy = wrapi(ys, g.ny), xx = wrapi(x0 - W::h + c, nx);
+        const size_t u = (size_t)yy * g.pitch + xx;
+        const R tv = (masked && mask && mask[u]) ? (R)0 : (R)tmpl[u];
+        R *dst = Tp + (size_t)((ys - ring_origin) % W::RING) * W::WCS + skew<R>(c);
+        dst[0] = tv;
+        for (int p = 1; p < np; p++) dst[(size_t)p * W::RING * W::WCS] = tv * xpow_g[(size_t)p * nx + xx];
     }
-    // folded kernel coefficients c_p(d, y - dy) for each of the CTA's output rows
-    const int ncf = kRows * LL * np * LL;
-    for (int e = tid; e < ncf; e += blockDim.x) {
+}
+
+// Folded coefficients c_p(d, y - dy) of output rows yb .. yb + kBand - 1, and their
+// background x-power sums.
+template <class R, int LL>
+__device__ __forceinline__ void stage_coeffs(const Geometry &g, const R *__restrict__ cfold, int yb, R *cf, R *byp) {
+    constexpr int h = LL / 2;
+    const int np = g.dk + 1, ny = g.ny;
+    const int ncf = kBand * LL * np * LL;
+    for (int e = threadIdx.x; e < ncf; e += blockDim.x) {
         int dxi = e % LL, rest = e / LL;
         int p = rest % np;
         rest /= np;
         int dyi = rest % LL, ry = rest / LL;
-        int ys = (((y0 + ry) - (dyi - h)) % ny + ny) % ny;  // source row y - dy
+        int ys = wrapi(yb + ry - (dyi - h), ny);  // source row y - dy
         cf[e] = cfold[(((size_t)ys * LL + dyi) * np + p) * LL + dxi];
     }
     const R *bgf = cfold + (size_t)ny * LL * LL * np;
-    for (int e = tid; e < kRows * (g.db + 1); e += blockDim.x) {
+    for (int e = threadIdx.x; e < kBand * (g.db + 1); e += blockDim.x) {
         int ry = e / (g.db + 1), p = e % (g.db + 1);
-        byp[e] = bgf[(size_t)min(y0 + ry, ny - 1) * (g.db + 1) + p];
+        byp[e] = bgf[(size_t)min(yb + ry, ny - 1) * (g.db + 1) + p];
     }
 }
 
+// Difference image (residual = false) or the fit residual m (S - bg) - conv(T_m)
+// (residual = true), one warp per output row of a band.
 template <class R, class In, int LL>
-__global__ void __launch_bounds__(256) k_subtract(const In *__restrict__ sci, const In *__restrict__ tmpl,
-                                                 const uint8_t *__restrict__ mask, bool residual, Geometry g,
-                                                 const R *__restrict__ cfold, const R *__restrict__ xpow_g,
-                                                 In *__restrict__ diff) {
-    constexpr int h = LL / 2;
-    constexpr int WC = kColsO + 2 * h;  // window columns
-    constexpr int WCS = WC + WC / 8 + 1; // skewed row length
-    constexpr int WR = kRowsO + 2 * h;  // window rows
-    constexpr int NW = kRX + LL - 1;    // register window per thread
+__global__ void __launch_bounds__(32 * kBand) k_subtract(const In *__restrict__ sci, const In *__restrict__ tmpl,
+                                                        const uint8_t *__restrict__ mask, bool residual, Geometry g,
+                                                        int rows_per_chunk, const R *__restrict__ cfold,
+                                                        const R *__restrict__ xpow_g, In *__restrict__ diff) {
+    using W = Win<R, LL>;
+    constexpr int h = W::h, kRX = Tile<R>::kRX, NW = W::NW;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int dk = g.dk, np = dk + 1;
-    R *Tp = reinterpret_cast<R *>(smem_raw);  // [np][WR][WCS] skewed: template times xh^p
-    R *cf = Tp + np * WR * WCS;                // [kRowsO][LL][np][LL]
-    R *byp = cf + kRowsO * LL * np * LL;       // [kRowsO][db+1]  background per x power
+    const int np = g.dk + 1, nx = g.nx, ny = g.ny;
+    R *Tp = reinterpret_cast<R *>(smem_raw);   // [np][RING][WCS]
+    R *cf = Tp + np * W::RING * W::WCS;         // [kBand][LL][np][LL]
+    R *byp = cf + kBand * LL * np * LL;         // [kBand][db+1]
 
-    const int x0 = blockIdx.x * kColsO, y0 = blockIdx.y * kRowsO;
-    const int tid = threadIdx.x;
-    const int nx = g.nx, ny = g.ny;
+    const int x0 = blockIdx.x * Tile<R>::kCols;
+    const int yc0 = blockIdx.y * rows_per_chunk, yc1 = min(ny, yc0 + rows_per_chunk);
+    if (yc0 >= ny) return;
+    const int ring_origin = yc0 - h;
+    const int ty = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int cx = lane * kRX;
 
-    stage_window<R, In, LL, kRowsO>(tmpl, mask, residual, g, cfold, xpow_g, x0, y0, Tp, cf, byp);
-    __syncthreads();
-
-    const int ty = tid >> 5, lane = tid & 31;
-    const int y = y0 + ty;
-    const int cx = lane * kRX;  // first output column of this thread within the tile
-    R out[kRX];
+    stage_rows<R, In, LL>(tmpl, mask, residual, g, xpow_g, x0, yc0 - h, W::RING, ring_origin, Tp);
+    for (int yb = yc0; yb < yc1; yb += kBand) {
+        stage_coeffs<R, LL>(g, cfold, yb, cf, byp);
+        __syncthreads();
+        const int y = yb + ty;
+        R out[kRX];
 #pragma unroll
-    for (int r = 0; r < kRX; r++) out[r] = (R)0;
-    for (int dyi = 0; dyi < LL; dyi++) {
-        // source row y - dy sits at window row ty + h - dy = ty + (LL - 1) - dyi
-        const int wr = ty + (LL - 1) - dyi;
-        for (int p = 0; p < np; p++) {
-            const R *trow = Tp + (p * WR + wr) * WCS;
-            R wp[NW];
+        for (int r = 0; r < kRX; r++) out[r] = (R)0;
+        for (int dyi = 0; dyi < LL; dyi++) {
+            // source row y - dy = y + h - dyi
+            const int slot = (y + h - dyi - ring_origin) % W::RING;
+            for (int p = 0; p < np; p++) {
+                const R *trow = Tp + (p * W::RING + slot) * W::WCS;
+                R wp[NW];
 #pragma unroll
-            for (int m = 0; m < NW; m++) wp[m] = trow[skew(cx + m)];
-            const R *c = cf + ((ty * LL + dyi) * np + p) * LL;
+                for (int m = 0; m < NW; m++) wp[m] = trow[skew<R>(cx + m)];
+                const R *c = cf + ((ty * LL + dyi) * np + p) * LL;
 #pragma unroll
-            for (int dxi = 0; dxi < LL; dxi++) {
-                R cc = c[dxi];
-                // source column x - dx -> window index (r - dx + h) = r + (LL - 1) - dxi
+                for (int dxi = 0; dxi < LL; dxi++) {
+                    const R cc = c[dxi];
+                    // source column x - dx -> window index r - dx + h = r + (LL - 1) - dxi
 #pragma unroll
-                for (int r = 0; r < kRX; r++) out[r] += cc * wp[r + (LL - 1) - dxi];
-            }
-        }
-    }
-    if (y < ny) {
-        const R *bp = byp + ty * (g.db + 1);
-#pragma unroll
-        for (int r = 0; r < kRX; r++) {
-            int x = x0 + cx + r;
-            if (x < nx) {
-                R bg = (R)0;
-                for (int p = 0; p <= g.db; p++) bg += bp[p] * xpow_g[(size_t)p * nx + x];
-                size_t u = (size_t)y * g.pitch + x;
-                if (residual) {
-                    R m = (mask && mask[u]) ? (R)0 : (R)1;
-                    diff[u] = (In)(m * ((R)sci[u] - bg) - out[r]);
-                } else {
-                    diff[u] = (In)((R)sci[u] - out[r] - bg);
+                    for (int r = 0; r < kRX; r++) out[r] += cc * wp[r + (LL - 1) - dxi];
                 }
             }
         }
+        if (y < yc1) {
+            const R *bp = byp + ty * (g.db + 1);
+#pragma unroll
+            for (int r = 0; r < kRX; r++) {
+                const int x = x0 + cx + r;
+                if (x < nx) {
+                    R bg = (R)0;
+                    for (int p = 0; p <= g.db; p++) bg += bp[p] * xpow_g[(size_t)p * nx + x];
+                    const size_t u = (size_t)y * g.pitch + x;
+                    if (residual) {
+                        const R m = (mask && mask[u]) ? (R)0 : (R)1;
+                        diff[u] = (In)(m * ((R)sci[u] - bg) - out[r]);
+                    } else {
+                        diff[u] = (In)((R)sci[u] - out[r] - bg);
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        // the next band reads source rows up to yb + 2 kBand + h - 1; the kBand new ones
+        // replace rows yb - h .. yb - h + kBand - 1, which no later band reads
+        if (yb + kBand < yc1) stage_rows<R, In, LL>(tmpl, mask, residual, g, xpow_g, x0, yb + kBand + h, kBand,
+                                                    ring_origin, Tp);
     }
 }
 
@@ -179,9 +219,8 @@ __global__ void __launch_bounds__(256) k_subtract(const In *__restrict__ sci, co
 // hi + lo pair updated by an error-free two-sum (Knuth).  The outer lags, whose terms are
 // the product of two wings, accumulate in plain FP32 in a separate sum.  R then carries
 // about the rounding of its operands (the folded coefficients and xh^p T_m, each rounded
-// once to FP32).  Each thread holds two output rows (ty, ty + kRowsC / 2) as the two lanes
-// of packed FP32x2 operations.
-constexpr int kRowsC = 8;
+// once to FP32).  Each thread holds two output rows (ty, ty + kBand / 2) of a band as the
+// two lanes of packed FP32x2 operations.
 constexpr int kCore = 2;
 
 __device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
@@ -206,104 +245,130 @@ __device__ __forceinline__ void split_input<float>(float v, float &hi, float &lo
 }
 
 template <class In, int LL>
-__global__ void __launch_bounds__(128, 2) k_residual_comp(const In *__restrict__ sci, const In *__restrict__ tmpl,
-                                                      const uint8_t *__restrict__ mask, Geometry g,
-                                                      const float *__restrict__ cfold,
-                                                      const float *__restrict__ xpow_g, In *__restrict__ resid) {
-    constexpr int h = LL / 2;
-    constexpr int WC = kColsO + 2 * h;
-    constexpr int WCS = WC + WC / 8 + 1;
-    constexpr int WR = kRowsC + 2 * h;
-    constexpr int NW = kRX + LL - 1;
-    constexpr int kHalf = kRowsC / 2;
+__global__ void __launch_bounds__(16 * kBand, 2) k_residual_comp(const In *__restrict__ sci,
+                                                                 const In *__restrict__ tmpl,
+                                                                 const uint8_t *__restrict__ mask, Geometry g,
+                                                                 int rows_per_chunk, const float *__restrict__ cfold,
+                                                                 const float *__restrict__ xpow_g,
+                                                                 In *__restrict__ resid) {
+    using W = Win<float, LL>;
+    constexpr int h = W::h, kRX = Tile<float>::kRX, NW = W::NW;
+    constexpr int kHalf = kBand / 2;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int np = g.dk + 1, nx = g.nx, ny = g.ny;
-    float *Tp = reinterpret_cast<float *>(smem_raw);  // [np][WR][WCS]
-    float *cf = Tp + np * WR * WCS;                    // [kRowsC][LL][np][LL]
-    float *byp = cf + kRowsC * LL * np * LL;           // [kRowsC][db+1]
+    float *Tp = reinterpret_cast<float *>(smem_raw);
+    float *cf = Tp + np * W::RING * W::WCS;
+    float *byp = cf + kBand * LL * np * LL;
 
-    const int x0 = blockIdx.x * kColsO, y0 = blockIdx.y * kRowsC;
-    stage_window<float, In, LL, kRowsC>(tmpl, mask, true, g, cfold, xpow_g, x0, y0, Tp, cf, byp);
-    __syncthreads();
-
+    const int x0 = blockIdx.x * Tile<float>::kCols;
+    const int yc0 = blockIdx.y * rows_per_chunk, yc1 = min(ny, yc0 + rows_per_chunk);
+    if (yc0 >= ny) return;
+    const int ring_origin = yc0 - h;
     const int ty = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int cx = lane * kRX;
-    const int ya = y0 + ty, yb = ya + kHalf;
-    float2 hi[kRX], lo[kRX];
-    // start from m (S - bg): S split exactly into hi + lo, the background subtracted by two-sum
+
+    stage_rows<float, In, LL>(tmpl, mask, true, g, xpow_g, x0, yc0 - h, W::RING, ring_origin, Tp);
+    for (int yb = yc0; yb < yc1; yb += kBand) {
+        stage_coeffs<float, LL>(g, cfold, yb, cf, byp);
+        __syncthreads();
+        const int ya = yb + ty, yb2 = ya + kHalf;
+        float2 hi[kRX], lo[kRX], wing[kRX];
+        // start from m (S - bg): S split exactly into hi + lo, the background subtracted by two-sum
 #pragma unroll
-    for (int r = 0; r < kRX; r++) {
-        const int x = x0 + cx + r;
-        float sh[2] = {0.f, 0.f}, sl[2] = {0.f, 0.f}, bg[2] = {0.f, 0.f};
+        for (int r = 0; r < kRX; r++) {
+            const int x = x0 + cx + r;
+            float sh[2] = {0.f, 0.f}, sl[2] = {0.f, 0.f}, bg[2] = {0.f, 0.f};
 #pragma unroll
-        for (int k = 0; k < 2; k++) {
-            const int y = k ? yb : ya;
-            if (y < ny && x < nx) {
-                const size_t u = (size_t)y * g.pitch + x;
-                if (!(mask && mask[u])) {
-                    split_input<In>(sci[u], sh[k], sl[k]);
-                    const float *bp = byp + (k ? ty + kHalf : ty) * (g.db + 1);
-                    float b = 0.f;
-                    for (int p = 0; p <= g.db; p++) b = fmaf(bp[p], xpow_g[(size_t)p * nx + x], b);
-                    bg[k] = b;
+            for (int k = 0; k < 2; k++) {
+                const int y = k ? yb2 : ya;
+                if (y < yc1 && x < nx) {
+                    const size_t u = (size_t)y * g.pitch + x;
+                    if (!(mask && mask[u])) {
+                        split_input<In>(sci[u], sh[k], sl[k]);
+                        const float *bp = byp + (k ? ty + kHalf : ty) * (g.db + 1);
+                        float b = 0.f;
+                        for (int p = 0; p <= g.db; p++) b = fmaf(bp[p], xpow_g[(size_t)p * nx + x], b);
+                        bg[k] = b;
+                    }
                 }
             }
+            float2 s, e;
+            two_sum2(make_float2(sh[0], sh[1]), make_float2(-bg[0], -bg[1]), s, e);
+            hi[r] = s;
+            lo[r] = __fadd2_rn(e, make_float2(sl[0], sl[1]));
+            wing[r] = make_float2(0.f, 0.f);
         }
-        float2 s, e;
-        two_sum2(make_float2(sh[0], sh[1]), make_float2(-bg[0], -bg[1]), s, e);
-        hi[r] = s;
-        lo[r] = __fadd2_rn(e, make_float2(sl[0], sl[1]));
-    }
-    float2 wing[kRX];
+        for (int dyi = 0; dyi < LL; dyi++) {
+            const int sa = (ya + h - dyi - ring_origin) % W::RING, sb = (sa + kHalf) % W::RING;
+            const bool core_row = dyi >= h - kCore && dyi <= h + kCore;
+            for (int p = 0; p < np; p++) {
+                const float *ta = Tp + (p * W::RING + sa) * W::WCS, *tb = Tp + (p * W::RING + sb) * W::WCS;
+                float2 wp[NW];
 #pragma unroll
-    for (int r = 0; r < kRX; r++) wing[r] = make_float2(0.f, 0.f);
-    for (int dyi = 0; dyi < LL; dyi++) {
-        const int wra = ty + (LL - 1) - dyi, wrb = wra + kHalf;
-        const bool core_row = dyi >= h - kCore && dyi <= h + kCore;
-        for (int p = 0; p < np; p++) {
-            const float *ta = Tp + (p * WR + wra) * WCS, *tb = Tp + (p * WR + wrb) * WCS;
-            float2 wp[NW];
+                for (int m = 0; m < NW; m++) wp[m] = make_float2(ta[skew<float>(cx + m)], tb[skew<float>(cx + m)]);
+                const float *ca = cf + ((ty * LL + dyi) * np + p) * LL;
+                const float *cb = cf + (((ty + kHalf) * LL + dyi) * np + p) * LL;
+                if (core_row) {
 #pragma unroll
-            for (int m = 0; m < NW; m++) wp[m] = make_float2(ta[skew(cx + m)], tb[skew(cx + m)]);
-            const float *ca = cf + ((ty * LL + dyi) * np + p) * LL;
-            const float *cb = cf + (((ty + kHalf) * LL + dyi) * np + p) * LL;
-            if (core_row) {
+                    for (int dxi = 0; dxi < LL; dxi++) {
+                        const float2 cc = make_float2(ca[dxi], cb[dxi]);
+                        if (dxi >= h - kCore && dxi <= h + kCore) {
 #pragma unroll
-                for (int dxi = 0; dxi < LL; dxi++) {
-                    const float2 cc = make_float2(ca[dxi], cb[dxi]);
-                    if (dxi >= h - kCore && dxi <= h + kCore) {
+                            for (int r = 0; r < kRX; r++) {
+                                const float2 w = wp[r + (LL - 1) - dxi];
+                                const float2 pr = __fmul2_rn(cc, w);
+                                const float2 pe = __ffma2_rn(cc, w, neg2(pr));  // cc w - pr, exact
+                                float2 s, e;
+                                two_sum2(hi[r], neg2(pr), s, e);
+                                hi[r] = s;
+                                lo[r] = __fadd2_rn(lo[r], __fadd2_rn(e, neg2(pe)));
+                            }
+                        } else {
 #pragma unroll
-                        for (int r = 0; r < kRX; r++) {
-                            const float2 w = wp[r + (LL - 1) - dxi];
-                            const float2 pr = __fmul2_rn(cc, w);
-                            const float2 pe = __ffma2_rn(cc, w, neg2(pr));  // cc w - pr, exact
-                            float2 s, e;
-                            two_sum2(hi[r], neg2(pr), s, e);
-                            hi[r] = s;
-                            lo[r] = __fadd2_rn(lo[r], __fadd2_rn(e, neg2(pe)));
+                            for (int r = 0; r < kRX; r++) wing[r] = __ffma2_rn(cc, wp[r + (LL - 1) - dxi], wing[r]);
                         }
-                    } else {
+                    }
+                } else {
+#pragma unroll
+                    for (int dxi = 0; dxi < LL; dxi++) {
+                        const float2 cc = make_float2(ca[dxi], cb[dxi]);
 #pragma unroll
                         for (int r = 0; r < kRX; r++) wing[r] = __ffma2_rn(cc, wp[r + (LL - 1) - dxi], wing[r]);
                     }
                 }
-            } else {
-#pragma unroll
-                for (int dxi = 0; dxi < LL; dxi++) {
-                    const float2 cc = make_float2(ca[dxi], cb[dxi]);
-#pragma unroll
-                    for (int r = 0; r < kRX; r++) wing[r] = __ffma2_rn(cc, wp[r + (LL - 1) - dxi], wing[r]);
-                }
             }
         }
-    }
 #pragma unroll
-    for (int r = 0; r < kRX; r++) {
-        const int x = x0 + cx + r;
-        if (x >= nx) continue;
-        if (ya < ny) resid[(size_t)ya * g.pitch + x] = (In)((double)hi[r].x + ((double)lo[r].x - (double)wing[r].x));
-        if (yb < ny) resid[(size_t)yb * g.pitch + x] = (In)((double)hi[r].y + ((double)lo[r].y - (double)wing[r].y));
+        for (int r = 0; r < kRX; r++) {
+            const int x = x0 + cx + r;
+            if (x >= nx) continue;
+            if (ya < yc1) resid[(size_t)ya * g.pitch + x] = (In)((double)hi[r].x + ((double)lo[r].x - (double)wing[r].x));
+            if (yb2 < yc1)
+                resid[(size_t)yb2 * g.pitch + x] = (In)((double)hi[r].y + ((double)lo[r].y - (double)wing[r].y));
+        }
+        __syncthreads();
+        if (yb + kBand < yc1)
+            stage_rows<float, In, LL>(tmpl, mask, true, g, xpow_g, x0, yb + kBand + h, kBand, ring_origin, Tp);
     }
+}
+
+int sm_count() {
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0, v = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess)
+            sms = v;
+        if (sms <= 0) sms = 1;
+    }
+    return sms;
+}
+
+// rows per chunk: a multiple of kBand that gives about `per_sm` CTAs per SM
+int rows_per_chunk(const Geometry &g, int strips, int per_sm) {
+    const int want = std::max(1, (per_sm * sm_count() + strips - 1) / strips);
+    int rpc = (g.ny + want - 1) / want;
+    rpc = (rpc + kBand - 1) / kBand * kBand;
+    return std::max(rpc, kBand);
 }
 
 template <class R, class In, int LL>
@@ -314,25 +379,22 @@ cudaError_t run(const Geometry &g, const void *sci, const void *tmpl, const uint
         note_launch();
         k_fold<R><<<(unsigned)((nt + 255) / 256), 256, 0, st>>>(coeffs, g, (R *)cfold);
     }
-    constexpr int h = LL / 2;
     const int np = g.dk + 1;
-    constexpr int WCS = (kColsO + 2 * h) + (kColsO + 2 * h) / 8 + 1;
-    size_t sm = sizeof(R) * ((size_t)np * (kRowsO + 2 * h) * WCS +
-                             (size_t)kRowsO * LL * np * LL + (size_t)kRowsO * (g.db + 1));
+    const size_t sm = stream_smem<R, LL>(np, g.db);
+    const int strips = (g.nx + Tile<R>::kCols - 1) / Tile<R>::kCols;
     if constexpr (std::is_same<R, float>::value) {
         if (residual) {
-            const size_t smc = sizeof(float) * ((size_t)np * (kRowsC + 2 * h) * WCS +
-                                                (size_t)kRowsC * LL * np * LL + (size_t)kRowsC * (g.db + 1));
             auto kc = k_residual_comp<In, LL>;
-            cudaError_t e = cudaFuncSetAttribute(kc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smc);
+            cudaError_t e = cudaFuncSetAttribute(kc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
             if (e == cudaSuccess)
                 e = cudaFuncSetAttribute(kc, cudaFuncAttributePreferredSharedMemoryCarveout,
                                          cudaSharedmemCarveoutMaxShared);
             if (e != cudaSuccess) return e;
-            dim3 gridc((g.nx + kColsO - 1) / kColsO, (g.ny + kRowsC - 1) / kRowsC);
+            const int rpc = rows_per_chunk(g, strips, 2);
+            dim3 grid(strips, (g.ny + rpc - 1) / rpc);
             note_launch();
-            kc<<<gridc, 128, smc, st>>>((const In *)sci, (const In *)tmpl, mask, g, (const float *)cfold,
-                                        (const float *)xpow, (In *)diff);
+            kc<<<grid, 16 * kBand, sm, st>>>((const In *)sci, (const In *)tmpl, mask, g, rpc, (const float *)cfold,
+                                              (const float *)xpow, (In *)diff);
             return cudaGetLastError();
         }
     }
@@ -341,10 +403,11 @@ cudaError_t run(const Geometry &g, const void *sci, const void *tmpl, const uint
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return e;
-    dim3 grid((g.nx + kColsO - 1) / kColsO, (g.ny + kRowsO - 1) / kRowsO);
+    const int rpc = rows_per_chunk(g, strips, sizeof(R) == 4 ? 2 : 1);
+    dim3 grid(strips, (g.ny + rpc - 1) / rpc);
     note_launch();
-    kern<<<grid, 256, sm, st>>>((const In *)sci, (const In *)tmpl, mask, residual, g, (const R *)cfold,
-                                (const R *)xpow, (In *)diff);
+    kern<<<grid, 32 * kBand, sm, st>>>((const In *)sci, (const In *)tmpl, mask, residual, g, rpc, (const R *)cfold,
+                                        (const R *)xpow, (In *)diff);
     return cudaGetLastError();
 }
 
