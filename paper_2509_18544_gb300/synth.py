@@ -18,6 +18,12 @@ Recipes (seed fixes everything, numpy PCG64):
     linearly 1.8 -> 2.4 px along x in the template and along y in the science image,
     Poisson(sky 80 e- + stars) with the known sky subtracted afterwards, and a union of two
     Bernoulli(0.005) masks (byte 1 = masked).
+  * ``psf_field`` / ``psf_stamps`` / ``psf_grid_pair`` -- training data of the warm-start
+    network: a random pair of spatially varying elliptical Moffat PSF fields (FWHM linear
+    in the normalised coordinates, within 1.6 .. 2.8 px; ellipticity <= 0.15 at a random
+    position angle), their 32 x 32 stamps at the 3 x 3 cell centres, and a noise-free
+    frame pair with stars on a regular grid drawn with those fields.
+  * ``cnn_init`` -- seeded He-normal initial weights of that network.
 """
 from __future__ import annotations
 
@@ -134,3 +140,121 @@ def cutout_sizes(n: int, seed: int, choices=(512, 1024, 1536, 2048)):
     """Square cutout sizes drawn uniformly from ``choices``."""
     rng = np.random.Generator(np.random.PCG64(seed))
     return [int(c) for c in rng.choice(np.asarray(choices), size=n)]
+
+
+# ---------------------------------------------------------------------------------------
+# PSF fields and stamps for the warm-start network
+
+STAMP = 32
+GRID3 = (-2.0 / 3.0, 0.0, 2.0 / 3.0)  # normalised coordinates of the 3 x 3 cell centres
+
+
+def _moffat_ell(dx, dy, alpha, e, phi, beta=MOFFAT_BETA):
+    """Elliptical Moffat with axis ratio 1 - e and the area of the round profile of width
+    alpha (semi-axes alpha / sqrt(1 - e), alpha sqrt(1 - e))."""
+    q = 1.0 - e
+    a, b = alpha / np.sqrt(q), alpha * np.sqrt(q)
+    c, s = np.cos(phi), np.sin(phi)
+    u = c * dx + s * dy
+    v = -s * dx + c * dy
+    return (1.0 + (u / a) ** 2 + (v / b) ** 2) ** (-beta)
+
+
+def _draw_field(rng, fwhm_range, e_max):
+    lo, hi = fwhm_range
+    f0 = rng.uniform(lo + 0.05, hi - 0.05)
+    r = min(f0 - lo, hi - f0)
+    fx, fy = rng.uniform(-r, r, 2)
+    if abs(fx) + abs(fy) > r:
+        sc = r / (abs(fx) + abs(fy))
+        fx, fy = fx * sc, fy * sc
+    return dict(f0=f0, fx=fx, fy=fy, e=rng.uniform(0.0, e_max), phi=rng.uniform(0.0, np.pi))
+
+
+def psf_field(seed: int, fwhm_range=(1.6, 2.8), e_max: float = 0.15):
+    """A random (science, template) pair of PSF fields: FWHM(xh, yh) = f0 + fx xh + fy yh
+    stays inside ``fwhm_range`` over [-1, 1]^2; ellipticity and angle are constant."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return dict(sci=_draw_field(rng, fwhm_range, e_max), tmpl=_draw_field(rng, fwhm_range, e_max))
+
+
+def roman_field(fwhm=(1.8, 2.4)):
+    """The PSF fields ``roman_pair`` draws with: round Moffats, FWHM linear along x in the
+    template and along y in the science image."""
+    f0, f1 = fwhm
+    c, g = 0.5 * (f0 + f1), 0.5 * (f1 - f0)
+    return dict(sci=dict(f0=c, fx=0.0, fy=g, e=0.0, phi=0.0), tmpl=dict(f0=c, fx=g, fy=0.0, e=0.0, phi=0.0))
+
+
+def _fwhm_at(fd, xh, yh):
+    return fd["f0"] + fd["fx"] * xh + fd["fy"] * yh
+
+
+def psf_stamps(field, size: int = STAMP) -> np.ndarray:
+    """float32 [18][size][size]: unit-sum stamps centred on pixel (size/2, size/2) at the
+    3 x 3 cell centres (row-major, yh outer), science then template for each cell."""
+    off = np.arange(size) - size // 2
+    dy, dx = np.meshgrid(off, off, indexing="ij")
+    out = np.zeros((18, size, size), dtype=np.float64)
+    k = 0
+    for yh in GRID3:
+        for xh in GRID3:
+            for key in ("sci", "tmpl"):
+                fd = field[key]
+                st = _moffat_ell(dx, dy, moffat_alpha(_fwhm_at(fd, xh, yh)), fd["e"], fd["phi"])
+                out[k] = st / st.sum()
+                k += 1
+    return out.astype(np.float32)
+
+
+def psf_grid_pair(field, seed: int, size: int = 256, spacing: int = 32, flux: float = 1e4,
+                  radius: int = 12, dtype=np.float32):
+    """Noise-free (sci, tmpl) frames with one star per ``spacing`` x ``spacing`` cell (random
+    sub-pixel offset), each drawn with the field's PSF at its position."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    c = np.arange(spacing // 2, size, spacing, dtype=np.float64)
+    ys, xs = np.meshgrid(c, c, indexing="ij")
+    xs = xs.ravel() + rng.uniform(-0.5, 0.5, xs.size)
+    ys = ys.ravel() + rng.uniform(-0.5, 0.5, ys.size)
+    fl = np.full(xs.size, flux)
+    xh = 2.0 * xs / (size - 1) - 1.0
+    yh = 2.0 * ys / (size - 1) - 1.0
+
+    out = []
+    for key in ("sci", "tmpl"):
+        fd = field[key]
+        al = moffat_alpha(_fwhm_at(fd, xh, yh))
+        out.append(_render_signed(size, size, xs, ys, fl, al, fd["e"], fd["phi"], radius))
+    return out[0].astype(dtype), out[1].astype(dtype)
+
+
+def _render_signed(ny, nx, xs, ys, flux, alpha, e, phi, radius):
+    """Like ``_render`` for elliptical profiles (which need signed offsets)."""
+    img = np.zeros(ny * nx, dtype=np.float64)
+    off = np.arange(-radius, radius + 1)
+    oy, ox = np.meshgrid(off, off, indexing="ij")
+    x = xs[:, None, None]
+    y = ys[:, None, None]
+    cx = np.floor(x + 0.5).astype(np.int64)
+    cy = np.floor(y + 0.5).astype(np.int64)
+    px = cx + ox[None]
+    py = cy + oy[None]
+    prof = _moffat_ell(px - x, py - y, alpha[:, None, None], e, phi)
+    prof /= prof.sum(axis=(1, 2), keepdims=True)
+    prof *= flux[:, None, None]
+    np.add.at(img, (np.mod(py, ny) * nx + np.mod(px, nx)).ravel(), prof.ravel())
+    return img.reshape(ny, nx)
+
+
+def cnn_init(n_out: int, seed: int) -> np.ndarray:
+    """Seeded He-normal weights (zero biases) of the warm-start network, as one flat float32
+    vector in the network's parameter order: 4 x (conv W [32][cin][3][3], b [32]) with
+    cin = 18, 32, 32, 32, then linear W [n_out][128], b [n_out]."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    parts = []
+    for cin in (18, 32, 32, 32):
+        parts.append(rng.normal(0.0, np.sqrt(2.0 / (cin * 9)), (32, cin, 3, 3)).ravel())
+        parts.append(np.zeros(32))
+    parts.append(rng.normal(0.0, np.sqrt(2.0 / 128), (n_out, 128)).ravel())
+    parts.append(np.zeros(n_out))
+    return np.concatenate(parts).astype(np.float32)
