@@ -91,7 +91,9 @@ typedef struct {
     int32_t iterations;    /* solver iterations (refinement steps for Cholesky) */
     int32_t fallback;      /* 1 when PCG fell back to Cholesky */
     double rel_residual;   /* ||b - N theta||_2 / ||b||_2 after the last step */
-    double reserved[3];
+    double start_residual; /* ||b - N x||_2 / ||b||_2 at PCG's starting point (after the warm
+                              start's projection); 1 for Cholesky and for a fallback */
+    double reserved[2];
 } sfft_fit_info;
 
 /* Create a plan for one frame geometry and basis.  Validates the descriptor, chooses the
@@ -167,6 +169,51 @@ sfft_status sfft_batch(const sfft_desc *base, int32_t n_sci, int32_t n_tmpl, con
  * or different host threads on one device) race on it and must be serialised. */
 sfft_status sfft_subtract_noalloc(const sfft_desc *desc, const void *sci, const void *tmpl,
                                   const double *coeffs, void *diff, sfft_stream_t stream);
+
+/* ---------------------------------------------------------------------------------
+ * Warm-start network (the learned warm start of the PCG solve).  A small CNN maps the
+ * point-spread functions of a pair -- 32 x 32 stamps of unit mean at the centres of a
+ * 3 x 3 grid over the frame, 18 channels ordered (cell row-major, then science, template)
+ * -- to the n_out = L^2 nP(DK) kernel coefficients of the fit in the unknowns' order.  It
+ * is trained on coefficients that sfft_fit produces.  The paper has no network; it
+ * stands in for the prior knowledge of how a kernel follows the two PSFs.
+ *   layers: 4 x [3x3 conv, stride 2, zero pad 1, 32 ch, ReLU] (32 -> 2 px), flatten
+ *           (channel, row, column), linear 128 -> n_out;
+ *   parameters: one float vector, conv1 W[32][18][3][3], b[32], conv2 W[32][32][3][3], b,
+ *           conv3, conv4 likewise, linear W[n_out][128], b[n_out];
+ *   loss: mean squared error; optimiser: Adam (beta1 0.9, beta2 0.999, eps 1e-8).
+ * All pointers are device memory except where marked host; calls are queued on the
+ * network's stream.  Stamps are [batch][18][32][32] float, targets and outputs
+ * [batch][n_out] float.  A network is not thread-safe. */
+typedef struct sfft_cnn_s *sfft_cnn_t;
+/* Allocate a network (parameters, Adam moments, activations for up to max_batch samples),
+ * zero-initialised; SFFT_ERR_OOM if the allocation fails. */
+sfft_status sfft_cnn_create(sfft_cnn_t *cnn, int32_t n_out, int32_t max_batch, sfft_stream_t stream);
+void sfft_cnn_destroy(sfft_cnn_t cnn);
+sfft_status sfft_cnn_param_count(sfft_cnn_t cnn, int64_t *count /* host */);
+/* Copy params (host or device, param_count floats) in; resets the Adam moments and step.
+ * Synchronises the stream. */
+sfft_status sfft_cnn_set_params(sfft_cnn_t cnn, const float *params);
+/* Copy the parameters out (host or device); synchronises the stream. */
+sfft_status sfft_cnn_get_params(sfft_cnn_t cnn, float *params);
+sfft_status sfft_cnn_forward(sfft_cnn_t cnn, const float *stamps, int32_t batch, float *out);
+/* Loss and gradients without an update: grad (param_count floats), grad_in (the stamps'
+ * gradient, nullable), loss (1 float, nullable). */
+sfft_status sfft_cnn_gradients(sfft_cnn_t cnn, const float *stamps, const float *targets, int32_t batch,
+                               float *grad, float *grad_in, float *loss);
+/* One Adam step on one batch; loss (1 float, nullable) receives the batch's loss before the update. */
+sfft_status sfft_cnn_train_step(sfft_cnn_t cnn, const float *stamps, const float *targets, int32_t batch,
+                                float lr, float *loss);
+/* `epochs` passes over n samples in minibatches of `batch`, reshuffled every epoch by a
+ * host SplitMix64 stream seeded with `seed` (the ragged remainder is skipped).
+ * epoch_loss (host, epochs floats, nullable) receives each epoch's mean minibatch loss.
+ * Synchronises the stream once per epoch. */
+sfft_status sfft_cnn_train(sfft_cnn_t cnn, const float *stamps, const float *targets, int32_t n, int32_t batch,
+                           int32_t epochs, float lr, uint64_t seed, float *epoch_loss);
+/* Warm starts for sfft_fit: x0[b n_stride + j] = output j of sample b (j < n_out), 0 for
+ * the remaining n_stride - n_out unknowns (the background). */
+sfft_status sfft_cnn_warm_start(sfft_cnn_t cnn, const float *stamps, int32_t batch, int32_t n_stride, double *x0);
+const char *sfft_cnn_last_error(sfft_cnn_t cnn);
 
 /* Stage timing (instrumentation; the paper profiles its pipeline stage by stage, Sec. "GPU
  * acceleration and performance").  With enable != 0 every later call records CUDA events

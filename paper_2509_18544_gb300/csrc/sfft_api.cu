@@ -500,9 +500,9 @@ sfft_status sfft_normal(sfft_plan_t plan, const void *sci, const void *tmpl, con
 
 static sfft_status read_status(sfft_plan_t p, sfft_fit_info *info) {
     int st_h = 0, fl[2] = {0, 0};
-    double scal[2] = {0.0, 0.0};
+    double scal[3] = {0.0, 0.0, 0.0};
     cudaError_t e = cudaMemcpyAsync(&st_h, p->ws.status, sizeof(int), cudaMemcpyDeviceToHost, p->stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(scal, p->ws.scal, 2 * sizeof(double), cudaMemcpyDeviceToHost, p->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(scal, p->ws.scal, 3 * sizeof(double), cudaMemcpyDeviceToHost, p->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(fl, p->ws.flags, 2 * sizeof(int), cudaMemcpyDeviceToHost, p->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
     if (e != cudaSuccess) return cuda_fail(p, e, "status read-back");
@@ -514,6 +514,7 @@ static sfft_status read_status(sfft_plan_t p, sfft_fit_info *info) {
         info->iterations = fast && fl[0] ? fl[1] : 1;
         info->fallback = fast && !fl[0] ? 1 : 0;
         info->rel_residual = scal[1] > 0 ? sqrt(scal[0] / scal[1]) : 0.0;
+        info->start_residual = fast && fl[0] && scal[1] > 0 ? sqrt(scal[2] / scal[1]) : 1.0;
     }
     if (st_h != 0) {
         set_err(p, "device status: %s", sfft_status_string((sfft_status)st_h));

@@ -14,8 +14,11 @@
 //
 // Outcome flags (device): flag[0] = 1 when PCG met the tolerance; otherwise 0, and the
 // caller's stream-ordered fallback (the FP64 Cholesky) runs.  A non-positive FP32 pivot or a
-// non-finite value also leaves flag[0] = 0.  The warm start x0 (nullable) is scaled by
-// alpha = x0.b / x0.N x0 before use.  Mode 1 reuses the factor stored in global memory by a
+// non-finite value also leaves flag[0] = 0.  A warm start x0 (nullable) is replaced by the
+// Galerkin projection of the solution onto span{x0, background unit vectors}: the starting
+// point alpha x0 + sum_r beta_r e_r minimising the N-norm error, from a (1 + nB) system
+// (a warm start that predicts the kernel coefficients leaves the background to this
+// projection).  Mode 1 reuses the factor stored in global memory by a
 // mode-0 call and applies one preconditioned correction x += M^{-1} c (refinement passes).
 #include <cooperative_groups.h>
 #include <math.h>
@@ -39,9 +42,10 @@ struct FastArgs {
     double *x;         // solution (mode 1: updated in place)
     double *r, *p, *q, *z, *d;  // [n] FP64 work vectors, d = diag(N)^{-1/2}
     float *Lg;         // packed FP32 factor tiles in global memory [ntiles][TT]
-    double *scal;      // [0] final ||r||^2, [1] ||b||^2
+    double *scal;      // [0] final ||r||^2, [1] ||b||^2, [2] ||r||^2 at the starting point
     int *flags;        // [0] converged, [1] iterations
     int n, nblk, ntiles;
+    int nker, nb;      // kernel and background unknowns (n = nker + nb)
     int max_iter;
     double tol;
     int mode;
@@ -55,6 +59,50 @@ __device__ __forceinline__ void tile_ij(int t, int &i, int &j) {
     j = t - a * (a + 1) / 2;
 }
 __device__ __forceinline__ int tile_id(int i, int j) { return i * (i + 1) / 2 + j; }
+
+constexpr int kGalMax = 11;  // warm-start projection for up to 10 background terms (DB <= 3)
+
+// Solves the m x m system held as the augmented m x (m + 1) matrix a (overwritten) by
+// Gaussian elimination with partial pivoting; a column without a usable pivot (relative
+// size < 1e-13) gets the value 0.  One thread.
+__device__ void solve_small(double *a, int m, double *x) {
+    const int w = m + 1;
+    int prow[kGalMax];
+    double amax = 0.0;
+    for (int e = 0; e < m * w; e++) amax = fmax(amax, fabs(a[e]));
+    int r = 0;
+    for (int c = 0; c < m; c++) {
+        int best = -1;
+        double bv = 1e-13 * amax;
+        for (int i = r; i < m; i++)
+            if (fabs(a[i * w + c]) > bv) bv = fabs(a[i * w + c]), best = i;
+        if (best < 0 || !isfinite(bv)) {
+            prow[c] = -1;
+            continue;
+        }
+        if (best != r)
+            for (int j = 0; j < w; j++) {
+                double t = a[r * w + j];
+                a[r * w + j] = a[best * w + j];
+                a[best * w + j] = t;
+            }
+        for (int i = r + 1; i < m; i++) {
+            const double f = a[i * w + c] / a[r * w + c];
+            for (int j = c; j < w; j++) a[i * w + j] -= f * a[r * w + j];
+        }
+        prow[c] = r++;
+    }
+    for (int c = m - 1; c >= 0; c--) {
+        if (prow[c] < 0) {
+            x[c] = 0.0;
+            continue;
+        }
+        const int i = prow[c];
+        double s = a[i * w + m];
+        for (int j = c + 1; j < m; j++) s -= a[i * w + j] * x[j];
+        x[c] = s / a[i * w + c];
+    }
+}
 
 // copy a 32 x 32 tile (stride TS) from src (possibly another CTA's shared memory) to dst
 __device__ __forceinline__ void copy_tile(float *dst, const float *src) {
@@ -320,15 +368,40 @@ __global__ void __launch_bounds__(CTH) k_pcg_cluster(FastArgs A) {
         for (int i = rank * CTH + tid; i < n; i += CL * CTH) s += __ldcg(u + i) * __ldcg(w + i);
         return cluster_sum(cl, &slot, s);
     };
-    // x0: scaled warm start, or zero
-    double alpha0 = 0.0;
+    // x0: Galerkin projection onto span{x0, background unit vectors}, or zero
+    __shared__ double gal[kGalMax * (kGalMax + 1)], gco[kGalMax];
     if (A.x0) {
         matvec(A.x0, A.q);
         cl.sync();
-        double xb = dot(A.x0, A.b), xnx = dot(A.x0, A.q);
-        alpha0 = xnx > 0.0 ? xb / xnx : 0.0;
+        const double xq = dot(A.x0, A.q), xb = dot(A.x0, A.b);
+        const int m = A.nb + 1 <= kGalMax ? A.nb + 1 : 1;
+        if (threadIdx.x == 0) {
+            // order (x0, e_0, e_1, ...): G_00 = x0.N x0, G_0r = (N x0)_r, G_rs = N_rs
+            for (int i = 0; i < m; i++) {
+                for (int j = 0; j < m; j++) {
+                    double v;
+                    if (i == 0 && j == 0)
+                        v = xq;
+                    else if (i == 0)
+                        v = __ldcg(A.q + A.nker + j - 1);
+                    else if (j == 0)
+                        v = __ldcg(A.q + A.nker + i - 1);
+                    else
+                        v = A.N[(size_t)(A.nker + i - 1) * n + A.nker + j - 1];
+                    gal[i * (m + 1) + j] = v;
+                }
+                gal[i * (m + 1) + m] = i == 0 ? xb : A.b[A.nker + i - 1];
+            }
+            solve_small(gal, m, gco);
+        }
+        __syncthreads();
+        for (int i = rank * CTH + tid; i < n; i += CL * CTH) {
+            const int r = i - A.nker;
+            A.x[i] = gco[0] * A.x0[i] + (r >= 0 && r < m - 1 ? gco[1 + r] : 0.0);
+        }
+    } else {
+        for (int i = rank * CTH + tid; i < n; i += CL * CTH) A.x[i] = 0.0;
     }
-    for (int i = rank * CTH + tid; i < n; i += CL * CTH) A.x[i] = A.x0 ? alpha0 * A.x0[i] : 0.0;
     cl.sync();
     matvec(A.x, A.q);
     cl.sync();
@@ -339,6 +412,7 @@ __global__ void __launch_bounds__(CTH) k_pcg_cluster(FastArgs A) {
     for (int i = rank * CTH + tid; i < n; i += CL * CTH) A.p[i] = __ldcg(A.z + i);
     cl.sync();
     double rz = dot(A.r, A.z), rr = dot(A.r, A.r);
+    const double rr0 = rr;
     int it = 0;
     bool conv = rr <= A.tol * A.tol * bb;
     while (!conv && it < A.max_iter && isfinite(rz)) {
@@ -370,6 +444,7 @@ __global__ void __launch_bounds__(CTH) k_pcg_cluster(FastArgs A) {
         A.flags[1] = it;
         A.scal[0] = rr;
         A.scal[1] = bb;
+        A.scal[2] = rr0;
     }
 }
 
@@ -433,6 +508,8 @@ cudaError_t launch_pcg_cluster(const Geometry &g, const double *N, const double 
     A.N = N;
     A.b = b;
     A.x0 = x0;
+    A.nker = g.nker;
+    A.nb = g.nb;
     A.x = x;
     A.r = r;
     A.p = p;

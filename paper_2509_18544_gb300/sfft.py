@@ -22,7 +22,10 @@ SOLVE_CHOLESKY, SOLVE_PCG = 0, 1
 EXPORTED = ("sfft_plan", "sfft_destroy", "sfft_n_unknowns", "sfft_workspace_size", "sfft_set_stream",
             "sfft_normal", "sfft_fit", "sfft_subtract", "sfft_sync_status", "sfft_batch",
             "sfft_profile", "sfft_stage_times", "sfft_launch_count", "sfft_subtract_noalloc",
-            "sfft_status_string", "sfft_last_error")
+            "sfft_status_string", "sfft_last_error",
+            "sfft_cnn_create", "sfft_cnn_destroy", "sfft_cnn_param_count", "sfft_cnn_set_params",
+            "sfft_cnn_get_params", "sfft_cnn_forward", "sfft_cnn_gradients", "sfft_cnn_train_step",
+            "sfft_cnn_train", "sfft_cnn_warm_start", "sfft_cnn_last_error")
 NSTAGES = 8
 STAGES = ("segment_fft", "moments", "ycorr", "lag_tables", "assemble", "solve", "subtract", "refine")
 
@@ -44,7 +47,7 @@ class sfft_desc(ctypes.Structure):
 class sfft_fit_info(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("n", ctypes.c_int32), ("iterations", ctypes.c_int32),
                 ("fallback", ctypes.c_int32), ("rel_residual", ctypes.c_double),
-                ("reserved", ctypes.c_double * 3)]
+                ("start_residual", ctypes.c_double), ("reserved", ctypes.c_double * 2)]
 
 
 _lib = None
@@ -81,8 +84,23 @@ def load_library(path: str = LIB_PATH):
         lib.sfft_status_string.restype = ctypes.c_char_p
         lib.sfft_last_error.argtypes = [P]
         lib.sfft_last_error.restype = ctypes.c_char_p
+        lib.sfft_cnn_create.argtypes = [ctypes.POINTER(P), I32, I32, P]
+        lib.sfft_cnn_destroy.argtypes = [P]
+        lib.sfft_cnn_destroy.restype = None
+        lib.sfft_cnn_param_count.argtypes = [P, ctypes.POINTER(ctypes.c_int64)]
+        lib.sfft_cnn_set_params.argtypes = [P, P]
+        lib.sfft_cnn_get_params.argtypes = [P, P]
+        lib.sfft_cnn_forward.argtypes = [P, P, I32, P]
+        lib.sfft_cnn_gradients.argtypes = [P, P, P, I32, P, P, P]
+        lib.sfft_cnn_train_step.argtypes = [P, P, P, I32, ctypes.c_float, P]
+        lib.sfft_cnn_train.argtypes = [P, P, P, I32, I32, I32, ctypes.c_float, ctypes.c_uint64,
+                                       ctypes.POINTER(ctypes.c_float)]
+        lib.sfft_cnn_warm_start.argtypes = [P, P, I32, I32, P]
+        lib.sfft_cnn_last_error.argtypes = [P]
+        lib.sfft_cnn_last_error.restype = ctypes.c_char_p
         for name in EXPORTED:
-            if name not in ("sfft_destroy", "sfft_status_string", "sfft_last_error"):
+            if name not in ("sfft_destroy", "sfft_status_string", "sfft_last_error", "sfft_cnn_destroy",
+                            "sfft_cnn_last_error"):
                 getattr(lib, name).restype = ctypes.c_int
         _lib = lib
         return lib
@@ -237,3 +255,89 @@ def sfft_subtract_noalloc(desc: sfft_desc, sci, tmpl, coeffs, diff, stream=None)
     """Plan-free difference image whose scratch is a fixed device array (no allocation)."""
     _check(load_library().sfft_subtract_noalloc(ctypes.byref(desc), _ptr(sci), _ptr(tmpl), _ptr(coeffs),
                                                 _ptr(diff), _stream(stream)))
+
+
+# ---------------------------------------------------------------------------------------
+# warm-start network
+
+def _check_cnn(rc, handle):
+    if rc != OK:
+        lib = load_library()
+        msg = lib.sfft_cnn_last_error(handle).decode(errors="replace") or lib.sfft_status_string(rc).decode()
+        raise SfftError(rc, msg)
+
+
+class Cnn:
+    """Owns one ``sfft_cnn_t``; created by :func:`sfft_cnn_create`."""
+
+    def __init__(self, handle, n_out, max_batch):
+        self.handle, self.n_out, self.max_batch = handle, n_out, max_batch
+
+    def close(self):
+        if self.handle:
+            load_library().sfft_cnn_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def sfft_cnn_create(n_out: int, max_batch: int, stream=None) -> Cnn:
+    h = ctypes.c_void_p()
+    _check_cnn(load_library().sfft_cnn_create(ctypes.byref(h), n_out, max_batch, _stream(stream)), None)
+    return Cnn(h.value, n_out, max_batch)
+
+
+def sfft_cnn_destroy(cnn: Cnn):
+    cnn.close()
+
+
+def sfft_cnn_param_count(cnn: Cnn) -> int:
+    v = ctypes.c_int64()
+    _check_cnn(load_library().sfft_cnn_param_count(cnn.handle, ctypes.byref(v)), cnn.handle)
+    return v.value
+
+
+def sfft_cnn_set_params(cnn: Cnn, params):
+    """params: a float32 device tensor, or a host buffer address (int)."""
+    _check_cnn(load_library().sfft_cnn_set_params(cnn.handle, _ptr(params)), cnn.handle)
+
+
+def sfft_cnn_get_params(cnn: Cnn, params):
+    _check_cnn(load_library().sfft_cnn_get_params(cnn.handle, _ptr(params)), cnn.handle)
+
+
+def sfft_cnn_forward(cnn: Cnn, stamps, batch: int, out):
+    _check_cnn(load_library().sfft_cnn_forward(cnn.handle, _ptr(stamps), batch, _ptr(out)), cnn.handle)
+
+
+def sfft_cnn_gradients(cnn: Cnn, stamps, targets, batch: int, grad, grad_in=None, loss=None):
+    _check_cnn(load_library().sfft_cnn_gradients(cnn.handle, _ptr(stamps), _ptr(targets), batch, _ptr(grad),
+                                                 _ptr(grad_in), _ptr(loss)), cnn.handle)
+
+
+def sfft_cnn_train_step(cnn: Cnn, stamps, targets, batch: int, lr: float, loss=None):
+    _check_cnn(load_library().sfft_cnn_train_step(cnn.handle, _ptr(stamps), _ptr(targets), batch, lr, _ptr(loss)),
+               cnn.handle)
+
+
+def sfft_cnn_train(cnn: Cnn, stamps, targets, n: int, batch: int, epochs: int, lr: float, seed: int):
+    """Returns the list of per-epoch mean losses."""
+    losses = (ctypes.c_float * epochs)()
+    _check_cnn(load_library().sfft_cnn_train(cnn.handle, _ptr(stamps), _ptr(targets), n, batch, epochs, lr,
+                                             seed, losses), cnn.handle)
+    return list(losses)
+
+
+def sfft_cnn_warm_start(cnn: Cnn, stamps, batch: int, n_stride: int, x0):
+    _check_cnn(load_library().sfft_cnn_warm_start(cnn.handle, _ptr(stamps), batch, n_stride, _ptr(x0)),
+               cnn.handle)

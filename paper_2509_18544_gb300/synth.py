@@ -22,7 +22,8 @@ Recipes (seed fixes everything, numpy PCG64):
     network: a random pair of spatially varying elliptical Moffat PSF fields (FWHM linear
     in the normalised coordinates, within 1.6 .. 2.8 px; ellipticity <= 0.15 at a random
     position angle), their 32 x 32 stamps at the 3 x 3 cell centres, and a noise-free
-    frame pair with stars on a regular grid drawn with those fields.
+    frame pair with stars on a regular grid drawn with those fields (stamps scaled to unit
+    mean).
   * ``cnn_init`` -- seeded He-normal initial weights of that network.
 """
 from __future__ import annotations
@@ -191,8 +192,9 @@ def _fwhm_at(fd, xh, yh):
 
 
 def psf_stamps(field, size: int = STAMP) -> np.ndarray:
-    """float32 [18][size][size]: unit-sum stamps centred on pixel (size/2, size/2) at the
-    3 x 3 cell centres (row-major, yh outer), science then template for each cell."""
+    """float32 [18][size][size]: stamps of unit mean (sum size^2, so that the network sees
+    values of order one) centred on pixel (size/2, size/2) at the 3 x 3 cell centres
+    (row-major, yh outer), science then template for each cell."""
     off = np.arange(size) - size // 2
     dy, dx = np.meshgrid(off, off, indexing="ij")
     out = np.zeros((18, size, size), dtype=np.float64)
@@ -202,7 +204,7 @@ def psf_stamps(field, size: int = STAMP) -> np.ndarray:
             for key in ("sci", "tmpl"):
                 fd = field[key]
                 st = _moffat_ell(dx, dy, moffat_alpha(_fwhm_at(fd, xh, yh)), fd["e"], fd["phi"])
-                out[k] = st / st.sum()
+                out[k] = st * (size * size / st.sum())
                 k += 1
     return out.astype(np.float32)
 
