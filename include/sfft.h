@@ -136,16 +136,69 @@ sfft_status sfft_subtract(sfft_plan_t plan, const void *sci, const void *tmpl, c
 /* Synchronise the plan's stream and return (and clear) the device status word. */
 sfft_status sfft_sync_status(sfft_plan_t plan);
 
-/* All S x T science/template pairs (the pairing of Sec. "Pipeline steps", step 1): pair
- * (i, j) has index i*n_tmpl + j (science-major).  sci[i], tmpl[j], masks (nullable array,
- * or per-pair NULL entries) are device pointers; every frame of pair (i, j) has size
- * ny[i*n_tmpl+j] x nx[...] with pitch = nx.  base supplies L, dk, db, dtype, precision,
- * solver.  coeffs[p] (n doubles) and diff[p] are device outputs; infos (host, nullable,
- * S*T entries) forces a final synchronisation.  Pairs run on the given stream. */
-sfft_status sfft_batch(const sfft_desc *base, int32_t n_sci, int32_t n_tmpl, const void *const *sci,
-                       const void *const *tmpl, const uint8_t *const *masks, const int32_t *ny,
-                       const int32_t *nx, double *const *coeffs, void *const *diff,
+/* ---------------------------------------------------------------------------------
+ * Batches: the S x T science/template pairs of one object (the pairing of Sec. "Pipeline
+ * steps", step 1), each a cutout of its own size.  Pairs are spread over `lanes` streams
+ * (longest first onto the least-loaded lane); each lane owns one plan per distinct
+ * geometry, so pairs overlap on the GPU.  Pair pointers stay fixed for the batch's life:
+ * a run reads the current contents of sci, tmpl, mask and x0 and writes coeffs and diff. */
+typedef struct {
+    const void *sci, *tmpl;   /* device: first pixel of each cutout (16-byte aligned) */
+    const uint8_t *mask;      /* device, nullable */
+    const double *x0;         /* device warm start for SFFT_SOLVE_PCG, nullable */
+    double *coeffs;           /* device output, n doubles */
+    void *diff;               /* device output, ny rows of `pitch` elements */
+    int32_t ny, nx;           /* cutout size */
+    int32_t pitch;            /* row pitch of the frames the cutouts lie in (elements; 0 = nx) */
+    int32_t reserved;
+} sfft_pair;
+typedef struct sfft_batch_s *sfft_batch_t;
+enum {
+    SFFT_BATCH_GRAPH = 1,     /* capture the whole batch into one CUDA graph; runs replay it */
+    SFFT_BATCH_AUTOTUNE = 2   /* autotune every geometry without a cached tuning first */
+};
+/* Build a batch (plans, lanes, and with SFFT_BATCH_GRAPH the graph) and run it once,
+ * ordered after the work already queued on `stream`, synchronising before it returns.
+ * base supplies L, dk, db, dtype, precision, solver, refine; lanes <= 0 means 4. */
+sfft_status sfft_batch_create(sfft_batch_t *batch, const sfft_desc *base, const sfft_pair *pairs,
+                              int32_t npairs, int32_t lanes, int32_t flags, sfft_stream_t stream);
+/* Queue one run of every pair on the creation stream (one graph launch with
+ * SFFT_BATCH_GRAPH). */
+sfft_status sfft_batch_run(sfft_batch_t batch);
+/* Synchronise and fill infos (host, npairs entries) from the last run; returns the first
+ * non-OK pair status (each pair's own is in its info). */
+sfft_status sfft_batch_info(sfft_batch_t batch, sfft_fit_info *infos);
+void sfft_batch_destroy(sfft_batch_t batch);
+/* One-shot: all n_sci x n_tmpl pairs (science-major, pair (i, j) at i*n_tmpl + j), run once
+ * and synchronised; infos (host, nullable) receives each pair's outcome, a non-positive-
+ * definite pair is reported there rather than failing the call. */
+sfft_status sfft_batch(const sfft_desc *base, int32_t n_sci, int32_t n_tmpl, const sfft_pair *pairs,
                        sfft_fit_info *infos, sfft_stream_t stream);
+
+/* ---------------------------------------------------------------------------------
+ * Launch tuning.  Plans take their y-correlation shape and subtract grid density from a
+ * process-wide cache keyed by (ny, nx, pitch, L, dk, db, dtype, precision, solver,
+ * refine); without an entry built-in heuristics apply.  Zero fields mean "heuristic". */
+typedef struct {
+    int32_t ycorr_bins;       /* frequencies per y-correlation CTA (1 .. the thread/smem limit) */
+    int32_t ycorr_split;      /* y-correlation row chunks */
+    int32_t ycorr_scalar;     /* 1: scalar FP32 y-correlation kernel, 0: packed FP32x2 */
+    int32_t subtract_ctas;    /* subtract / residual CTAs per SM the grid is sized for (1 .. 4) */
+    int32_t reserved[4];
+} sfft_tuning;
+/* The cached entry for desc (zeros and *cached = 0 when there is none). */
+sfft_status sfft_tuning_get(const sfft_desc *desc, sfft_tuning *t, int32_t *cached);
+/* Validate t against desc's limits and store it (SFFT_ERR_INVALID_ARG when out of range). */
+sfft_status sfft_tuning_set(const sfft_desc *desc, const sfft_tuning *t);
+/* Time candidate shapes on the given pair (device images; coordinate descent over the
+ * y-correlation kernel variant and bins, then its row split, then the subtract density;
+ * best of `trials` fit+subtract runs each, CUDA events), store the fastest and return it
+ * with its time in ms (best, best_ms: host, nullable).  Synchronises. */
+sfft_status sfft_autotune(const sfft_desc *desc, const void *sci, const void *tmpl, const uint8_t *mask,
+                          int32_t trials, sfft_tuning *best, double *best_ms);
+/* Write / read the whole cache as text, one entry per line. */
+sfft_status sfft_tuning_save(const char *path);
+sfft_status sfft_tuning_load(const char *path);
 
 /* Difference image exactly like sfft_subtract, but without a plan and without allocating:
  * no cudaMalloc, no cudaFree, no library routine that allocates.  The paper has no

@@ -40,8 +40,18 @@ namespace sfft {
 
 void set_global_error(const char *msg) { set_err(nullptr, "%s", msg); }
 
+int default_ysplit(const Geometry &g) {
+    // row chunks so the grid covers several waves of 2 CTAs on each of 152 SMs
+    const int units = g.nseg * ((g.nkf + g.kg - 1) / g.kg);
+    int ys = (4 * 304 + units - 1) / units;
+    const int max_ys = g.ny / (2 * g.ytile);
+    if (ys > max_ys) ys = max_ys;
+    return ys < 1 ? 1 : ys;
+}
+
 bool make_geometry(const sfft_desc &d, Geometry &g, char *err, size_t errlen) {
     memset(&g, 0, sizeof g);
+    g.sub_per_sm = 2;
     if (d.ny < 1 || d.nx < 1) return snprintf(err, errlen, "ny, nx must be >= 1"), false;
     if (d.L < 1 || d.L % 2 == 0) return snprintf(err, errlen, "L must be odd and >= 1 (got %d)", d.L), false;
     if (d.ny < d.L || d.nx < d.L) return snprintf(err, errlen, "frame %dx%d smaller than L=%d", d.ny, d.nx, d.L), false;
@@ -96,14 +106,10 @@ bool make_geometry(const sfft_desc &d, Geometry &g, char *err, size_t errlen) {
             return kg < 1 ? 1 : kg;
         };
         g.kg = pick(g.items_per_k, per_k);
+        g.kg_max = g.kg;
         g.kg_ws = pick(g.nk, per_k_ws);
         if (per_k > budget) return snprintf(err, errlen, "y-correlation tile does not fit shared memory"), false;
-        // row chunks so the grid covers several waves of 2 CTAs on each of 152 SMs
-        const int units = g.nseg * ((g.nkf + g.kg - 1) / g.kg);
-        int ys = (4 * 304 + units - 1) / units;
-        int max_ys = d.ny / (2 * g.ytile);
-        if (ys > max_ys) ys = max_ys;
-        g.ysplit = ys < 1 ? 1 : ys;
+        g.ysplit = default_ysplit(g);
         // refinement pass: one thread per (segment, chunk, frequency, W_i); ~200k threads
         long per_chunk = (long)g.nseg * g.nkf * g.nk;
         int yc = (int)((200000 + per_chunk - 1) / per_chunk);
@@ -184,6 +190,7 @@ size_t workspace_bytes(const Geometry &g, int precision, int dtype) {
 
 static std::atomic<uint64_t> g_launches{0};
 void note_launch(int count) { g_launches.fetch_add((uint64_t)count, std::memory_order_relaxed); }
+uint64_t launch_count() { return g_launches.load(std::memory_order_relaxed); }
 
 // Records a CUDA event pair around one stage on the plan's stream while profiling is on.
 struct StageTimer {
@@ -241,7 +248,7 @@ sfft_status sfft_workspace_size(const sfft_desc *desc, size_t *bytes) {
     if (!desc || !bytes) return set_err(nullptr, "null argument"), SFFT_ERR_INVALID_ARG;
     Geometry g;
     char err[256];
-    if (!make_geometry(*desc, g, err, sizeof err)) return set_err(nullptr, "%s", err), SFFT_ERR_INVALID_ARG;
+    if (!plan_geometry(*desc, g, err, sizeof err)) return set_err(nullptr, "%s", err), SFFT_ERR_INVALID_ARG;
     *bytes = workspace_bytes(g, desc->precision, desc->dtype);
     return SFFT_OK;
 }
@@ -252,7 +259,7 @@ sfft_status sfft_plan(sfft_plan_t *plan, const sfft_desc *desc, sfft_stream_t st
     if (!desc) return set_err(nullptr, "null descriptor"), SFFT_ERR_INVALID_ARG;
     Geometry g;
     char err[256];
-    if (!make_geometry(*desc, g, err, sizeof err)) {
+    if (!plan_geometry(*desc, g, err, sizeof err)) {
         bool unsup = strstr(err, "not supported") || strstr(err, "not built");
         set_err(nullptr, "%s", err);
         return unsup ? SFFT_ERR_UNSUPPORTED : SFFT_ERR_INVALID_ARG;
@@ -582,38 +589,5 @@ sfft_status sfft_sync_status(sfft_plan_t plan) {
     return read_status(plan, nullptr);
 }
 
-sfft_status sfft_batch(const sfft_desc *base, int32_t n_sci, int32_t n_tmpl, const void *const *sci,
-                       const void *const *tmpl, const uint8_t *const *masks, const int32_t *ny, const int32_t *nx,
-                       double *const *coeffs, void *const *diff, sfft_fit_info *infos, sfft_stream_t stream) {
-    if (!base || n_sci < 0 || n_tmpl < 0 || !sci || !tmpl || !ny || !nx || !coeffs || !diff)
-        return set_err(nullptr, "null or negative batch argument"), SFFT_ERR_INVALID_ARG;
-    const int npairs = n_sci * n_tmpl;
-    // one plan per distinct frame size, reused across pairs
-    std::map<std::pair<int, int>, sfft_plan_t> plans;
-    sfft_status result = SFFT_OK;
-    for (int pi = 0; pi < npairs && result == SFFT_OK; pi++) {
-        auto key = std::make_pair(ny[pi], nx[pi]);
-        if (!plans.count(key)) {
-            sfft_desc d = *base;
-            d.ny = ny[pi];
-            d.nx = nx[pi];
-            d.pitch = 0;
-            sfft_plan_t p = nullptr;
-            result = sfft_plan(&p, &d, stream);
-            if (result != SFFT_OK) break;
-            plans[key] = p;
-        }
-    }
-    for (int pi = 0; pi < npairs && result == SFFT_OK; pi++) {
-        sfft_plan_t p = plans[std::make_pair(ny[pi], nx[pi])];
-        int i = pi / (n_tmpl ? n_tmpl : 1), j = pi % (n_tmpl ? n_tmpl : 1);
-        const uint8_t *m = masks ? masks[pi] : nullptr;
-        result = sfft_fit(p, sci[i], tmpl[j], m, nullptr, coeffs[pi], infos ? &infos[pi] : nullptr);
-        if (result == SFFT_ERR_NOT_SPD && infos) result = SFFT_OK;  // reported per pair
-        if (result == SFFT_OK) result = sfft_subtract(p, sci[i], tmpl[j], coeffs[pi], diff[pi]);
-    }
-    for (auto &kv : plans) sfft_destroy(kv.second);
-    return result;
-}
 
 }  // extern "C"

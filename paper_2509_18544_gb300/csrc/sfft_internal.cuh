@@ -57,9 +57,17 @@ struct Geometry {
     int mom_rows, mom_ctas;    // background-moment reduction geometry
     int nmom;                  // moments: npoly(2 db) mask moments + npoly(db) science moments
     int pmax;                  // highest coordinate power tabulated: max(dk, 2 db)
+    // launch shape choices (heuristic defaults, or a tuned entry of the process-wide cache)
+    int kg_max;                // most y-correlation frequencies per CTA the thread and smem limits allow
+    int ycorr_scalar;          // 1: scalar FP32 y-correlation kernel instead of packed FP32x2
+    int sub_per_sm;            // subtract / residual CTAs per SM the grid is sized for
 };
 
 bool make_geometry(const sfft_desc &d, Geometry &g, char *err, size_t errlen);
+// make_geometry, then the cached tuning for this descriptor when there is one
+bool plan_geometry(const sfft_desc &d, Geometry &g, char *err, size_t errlen);
+// y-correlation row chunks for the current kg: several waves of 2 CTAs on each SM
+int default_ysplit(const Geometry &g);
 
 // ------------------------------------------------------------------ plan
 struct Workspace {
@@ -98,6 +106,7 @@ size_t workspace_bytes(const Geometry &g, int precision, int dtype);
 
 // process-wide count of kernel launches (every launcher calls this before each launch)
 void note_launch(int count = 1);
+uint64_t launch_count();
 
 enum Stage { ST_SEGFFT = 0, ST_MOMENTS, ST_YCORR, ST_LAGS, ST_ASSEMBLE, ST_SOLVE, ST_SUBTRACT, ST_REFINE, ST_COUNT };
 

@@ -390,7 +390,7 @@ cudaError_t run(const Geometry &g, const void *sci, const void *tmpl, const uint
                 e = cudaFuncSetAttribute(kc, cudaFuncAttributePreferredSharedMemoryCarveout,
                                          cudaSharedmemCarveoutMaxShared);
             if (e != cudaSuccess) return e;
-            const int rpc = rows_per_chunk(g, strips, 2);
+            const int rpc = rows_per_chunk(g, strips, g.sub_per_sm > 0 ? g.sub_per_sm : 2);
             dim3 grid(strips, (g.ny + rpc - 1) / rpc);
             note_launch();
             kc<<<grid, 16 * kBand, sm, st>>>((const In *)sci, (const In *)tmpl, mask, g, rpc, (const float *)cfold,
@@ -403,7 +403,7 @@ cudaError_t run(const Geometry &g, const void *sci, const void *tmpl, const uint
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return e;
-    const int rpc = rows_per_chunk(g, strips, sizeof(R) == 4 ? 2 : 1);
+    const int rpc = rows_per_chunk(g, strips, sizeof(R) == 4 ? (g.sub_per_sm > 0 ? g.sub_per_sm : 2) : 1);
     dim3 grid(strips, (g.ny + rpc - 1) / rpc);
     note_launch();
     kern<<<grid, 32 * kBand, sm, st>>>((const In *)sci, (const In *)tmpl, mask, residual, g, rpc, (const R *)cfold,

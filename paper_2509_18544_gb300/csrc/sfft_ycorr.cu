@@ -453,9 +453,8 @@ cudaError_t run(const Geometry &g, int precision, const void *spec, double *ypar
         k_ycorr_f64<C><<<grid, threads, sm, st>>>((const cpx<double> *)spec, g, ln, ypart);
     } else {
         size_t sm = 2 * rows * ln.kg * ln.cw * sizeof(cpx<float>);
-        // packed FP32x2 variant unless SFFT_YCORR_SCALAR is set (kept for A/B comparison)
-        static const bool scalar = getenv("SFFT_YCORR_SCALAR") != nullptr;
-        auto kern = scalar ? k_ycorr_f32<C> : k_ycorr_f32x2<C, 4>;
+        // packed FP32x2 variant unless the tuning picked the scalar one
+        auto kern = g.ycorr_scalar ? k_ycorr_f32<C> : k_ycorr_f32x2<C, 4>;
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);

@@ -21,6 +21,8 @@ SOLVE_CHOLESKY, SOLVE_PCG = 0, 1
 
 EXPORTED = ("sfft_plan", "sfft_destroy", "sfft_n_unknowns", "sfft_workspace_size", "sfft_set_stream",
             "sfft_normal", "sfft_fit", "sfft_subtract", "sfft_sync_status", "sfft_batch",
+            "sfft_batch_create", "sfft_batch_run", "sfft_batch_info", "sfft_batch_destroy",
+            "sfft_tuning_get", "sfft_tuning_set", "sfft_autotune", "sfft_tuning_save", "sfft_tuning_load",
             "sfft_profile", "sfft_stage_times", "sfft_launch_count", "sfft_subtract_noalloc",
             "sfft_status_string", "sfft_last_error",
             "sfft_cnn_create", "sfft_cnn_destroy", "sfft_cnn_param_count", "sfft_cnn_set_params",
@@ -50,6 +52,21 @@ class sfft_fit_info(ctypes.Structure):
                 ("start_residual", ctypes.c_double), ("reserved", ctypes.c_double * 2)]
 
 
+class sfft_pair(ctypes.Structure):
+    _fields_ = [("sci", ctypes.c_void_p), ("tmpl", ctypes.c_void_p), ("mask", ctypes.c_void_p),
+                ("x0", ctypes.c_void_p), ("coeffs", ctypes.c_void_p), ("diff", ctypes.c_void_p),
+                ("ny", ctypes.c_int32), ("nx", ctypes.c_int32), ("pitch", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class sfft_tuning(ctypes.Structure):
+    _fields_ = [("ycorr_bins", ctypes.c_int32), ("ycorr_split", ctypes.c_int32),
+                ("ycorr_scalar", ctypes.c_int32), ("subtract_ctas", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 4)]
+
+
+BATCH_GRAPH, BATCH_AUTOTUNE = 1, 2
+
 _lib = None
 _lock = threading.Lock()
 
@@ -74,8 +91,20 @@ def load_library(path: str = LIB_PATH):
         lib.sfft_fit.argtypes = [P, P, P, P, P, P, ctypes.POINTER(sfft_fit_info)]
         lib.sfft_subtract.argtypes = [P, P, P, P, P]
         lib.sfft_sync_status.argtypes = [P]
-        lib.sfft_batch.argtypes = [ctypes.POINTER(sfft_desc), I32, I32, P, P, P, P, P, P, P,
+        lib.sfft_batch.argtypes = [ctypes.POINTER(sfft_desc), I32, I32, ctypes.POINTER(sfft_pair),
                                    ctypes.POINTER(sfft_fit_info), P]
+        lib.sfft_batch_create.argtypes = [ctypes.POINTER(P), ctypes.POINTER(sfft_desc), ctypes.POINTER(sfft_pair),
+                                          I32, I32, I32, P]
+        lib.sfft_batch_run.argtypes = [P]
+        lib.sfft_batch_info.argtypes = [P, ctypes.POINTER(sfft_fit_info)]
+        lib.sfft_batch_destroy.argtypes = [P]
+        lib.sfft_batch_destroy.restype = None
+        lib.sfft_tuning_get.argtypes = [ctypes.POINTER(sfft_desc), ctypes.POINTER(sfft_tuning), ctypes.POINTER(I32)]
+        lib.sfft_tuning_set.argtypes = [ctypes.POINTER(sfft_desc), ctypes.POINTER(sfft_tuning)]
+        lib.sfft_autotune.argtypes = [ctypes.POINTER(sfft_desc), P, P, P, I32, ctypes.POINTER(sfft_tuning),
+                                      ctypes.POINTER(ctypes.c_double)]
+        lib.sfft_tuning_save.argtypes = [ctypes.c_char_p]
+        lib.sfft_tuning_load.argtypes = [ctypes.c_char_p]
         lib.sfft_subtract_noalloc.argtypes = [ctypes.POINTER(sfft_desc), P, P, P, P, P]
         lib.sfft_profile.argtypes = [P, I32]
         lib.sfft_stage_times.argtypes = [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(I32)]
@@ -100,7 +129,7 @@ def load_library(path: str = LIB_PATH):
         lib.sfft_cnn_last_error.restype = ctypes.c_char_p
         for name in EXPORTED:
             if name not in ("sfft_destroy", "sfft_status_string", "sfft_last_error", "sfft_cnn_destroy",
-                            "sfft_cnn_last_error"):
+                            "sfft_cnn_last_error", "sfft_batch_destroy"):
                 getattr(lib, name).restype = ctypes.c_int
         _lib = lib
         return lib
@@ -218,19 +247,97 @@ def sfft_sync_status(plan: Plan):
     _check(load_library().sfft_sync_status(plan.handle), plan.handle)
 
 
-def sfft_batch(desc: sfft_desc, n_sci, n_tmpl, sci, tmpl, masks, ny, nx, coeffs, diff, want_info=True,
-               stream=None):
-    """All S x T pairs; lists of device tensors (science-major pairs for masks/coeffs/diff)."""
-    npairs = n_sci * n_tmpl
-    P = ctypes.c_void_p
-    arr = lambda xs: (P * len(xs))(*[_ptr(x) for x in xs])
-    i32 = lambda xs: (ctypes.c_int32 * len(xs))(*xs)
-    infos = (sfft_fit_info * npairs)() if want_info else None
-    rc = load_library().sfft_batch(ctypes.byref(desc), n_sci, n_tmpl, arr(sci), arr(tmpl),
-                                   arr(masks) if masks is not None else None, i32(ny), i32(nx),
-                                   arr(coeffs), arr(diff), infos, _stream(stream))
-    _check(rc)
+def make_pair(sci, tmpl, mask, coeffs, diff, ny, nx, pitch=0, x0=None) -> sfft_pair:
+    q = sfft_pair()
+    q.sci, q.tmpl, q.mask, q.x0 = _ptr(sci), _ptr(tmpl), _ptr(mask), _ptr(x0)
+    q.coeffs, q.diff = _ptr(coeffs), _ptr(diff)
+    q.ny, q.nx, q.pitch = ny, nx, pitch
+    return q
+
+
+def _pairs(pairs):
+    return (sfft_pair * len(pairs))(*pairs)
+
+
+def sfft_batch(desc: sfft_desc, n_sci: int, n_tmpl: int, pairs, want_info=True, stream=None):
+    """One-shot run of all S x T pairs (science-major list of sfft_pair); returns the infos."""
+    infos = (sfft_fit_info * len(pairs))() if want_info else None
+    _check(load_library().sfft_batch(ctypes.byref(desc), n_sci, n_tmpl, _pairs(pairs), infos, _stream(stream)))
     return list(infos) if infos is not None else None
+
+
+class Batch:
+    """Owns one ``sfft_batch_t``; created by :func:`sfft_batch_create`."""
+
+    def __init__(self, handle, npairs):
+        self.handle, self.npairs = handle, npairs
+
+    def close(self):
+        if self.handle:
+            load_library().sfft_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def sfft_batch_create(desc: sfft_desc, pairs, lanes: int = 0, flags: int = 0, stream=None) -> Batch:
+    h = ctypes.c_void_p()
+    _check(load_library().sfft_batch_create(ctypes.byref(h), ctypes.byref(desc), _pairs(pairs), len(pairs), lanes,
+                                            flags, _stream(stream)))
+    return Batch(h.value, len(pairs))
+
+
+def sfft_batch_run(batch: Batch):
+    _check(load_library().sfft_batch_run(batch.handle))
+
+
+def sfft_batch_info(batch: Batch, raise_on_error: bool = False):
+    infos = (sfft_fit_info * batch.npairs)()
+    rc = load_library().sfft_batch_info(batch.handle, infos)
+    if raise_on_error or rc not in (OK, ERR_NOT_SPD):
+        _check(rc)
+    return list(infos)
+
+
+def sfft_batch_destroy(batch: Batch):
+    batch.close()
+
+
+def sfft_tuning_get(desc: sfft_desc):
+    t = sfft_tuning()
+    cached = ctypes.c_int32()
+    _check(load_library().sfft_tuning_get(ctypes.byref(desc), ctypes.byref(t), ctypes.byref(cached)))
+    return t, bool(cached.value)
+
+
+def sfft_tuning_set(desc: sfft_desc, t: sfft_tuning):
+    _check(load_library().sfft_tuning_set(ctypes.byref(desc), ctypes.byref(t)))
+
+
+def sfft_autotune(desc: sfft_desc, sci, tmpl, mask, trials: int = 3):
+    t = sfft_tuning()
+    ms = ctypes.c_double()
+    _check(load_library().sfft_autotune(ctypes.byref(desc), _ptr(sci), _ptr(tmpl), _ptr(mask), trials,
+                                        ctypes.byref(t), ctypes.byref(ms)))
+    return t, ms.value
+
+
+def sfft_tuning_save(path: str):
+    _check(load_library().sfft_tuning_save(path.encode()))
+
+
+def sfft_tuning_load(path: str):
+    _check(load_library().sfft_tuning_load(path.encode()))
 
 
 def sfft_profile(plan: Plan, enable: bool = True):

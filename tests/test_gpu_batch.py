@@ -1,0 +1,140 @@
+"""Batches of S x T pairs with uneven cutout sizes: lanes, graph replay, per-pair status,
+and the autotuner -- all through the C ABI, checked against single-pair plans and the
+FP64 oracle."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2509_18544_gb300 import build as sfft_build
+from paper_2509_18544_gb300 import sfft, synth
+
+pytestmark = pytest.mark.gpu
+
+DEV = torch.device("cuda:0")
+L, DK, DB = 5, 1, 1
+FRAME = 320
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    sfft_build.build()
+    sfft.load_library()
+
+
+def _cutouts(sizes, seed):
+    """Per pair: science/template/mask frames of FRAME x FRAME and the cutout origin; the
+    pair's cutout (ny, nx) sits at (oy, ox) and is addressed with the frame's pitch."""
+    out = []
+    for k, (ny, nx) in enumerate(sizes):
+        S, T, M = synth.roman_pair(FRAME, FRAME, seed=seed + k, n_stars=120)
+        oy, ox = 8 * (k % 3), 4 * (k % 5)
+        out.append(dict(S=torch.from_numpy(S).to(DEV), T=torch.from_numpy(T).to(DEV),
+                        M=torch.from_numpy(M).to(DEV), ny=ny, nx=nx, oy=oy, ox=ox))
+    return out
+
+
+def _view(t, c):
+    return t.reshape(-1)[c["oy"] * FRAME + c["ox"]:]
+
+
+def _pairs(cuts, n, x0=None):
+    pairs, coeffs, diffs = [], [], []
+    for k, c in enumerate(cuts):
+        th = torch.full((n,), float("nan"), dtype=torch.float64, device=DEV)
+        D = torch.full((c["ny"], FRAME), float("nan"), dtype=torch.float32, device=DEV)
+        pairs.append(sfft.make_pair(_view(c["S"], c), _view(c["T"], c), _view(c["M"], c), th, D, c["ny"], c["nx"],
+                                    pitch=FRAME, x0=None if x0 is None else x0[k]))
+        coeffs.append(th)
+        diffs.append(D)
+    return pairs, coeffs, diffs
+
+
+def _single(c, n, solver=sfft.SOLVE_CHOLESKY, x0=None):
+    d = sfft.make_desc(c["ny"], c["nx"], L, DK, DB, pitch=FRAME, solver=solver)
+    with sfft.sfft_plan(d) as p:
+        th = torch.empty(n, dtype=torch.float64, device=DEV)
+        D = torch.full((c["ny"], FRAME), float("nan"), dtype=torch.float32, device=DEV)
+        sfft.sfft_fit(p, _view(c["S"], c), _view(c["T"], c), _view(c["M"], c), x0, th)
+        sfft.sfft_subtract(p, _view(c["S"], c), _view(c["T"], c), th, D)
+        torch.cuda.synchronize()
+    return th, D
+
+
+SIZES = [(128, 128), (192, 160), (256, 256), (160, 224), (128, 256), (256, 192)]   # 3 x 2 pairs
+
+
+@pytest.mark.parametrize("flags,lanes", [(0, 1), (0, 3), (sfft.BATCH_GRAPH, 4)])
+def test_batch_matches_single_pair_plans(flags, lanes):
+    cuts = _cutouts(SIZES, seed=40)
+    n = oracle.n_unknowns(L, DK, DB)
+    pairs, coeffs, diffs = _pairs(cuts, n)
+    base = sfft.make_desc(128, 128, L, DK, DB)
+    with sfft.sfft_batch_create(base, pairs, lanes=lanes, flags=flags) as b:
+        infos = sfft.sfft_batch_info(b)
+        for k, c in enumerate(cuts):
+            th, D = _single(c, n)
+            assert infos[k].status == 0
+            # same kernels, same launch shapes: identical results
+            assert torch.equal(coeffs[k], th)
+            assert torch.equal(diffs[k][:, :c["nx"]], D[:, :c["nx"]])
+        # a replay reproduces the first run bit for bit, after the outputs were cleared
+        first = [t.clone() for t in coeffs]
+        for t in coeffs:
+            t.fill_(float("nan"))
+        sfft.sfft_batch_run(b)
+        sfft.sfft_batch_info(b)
+        for k in range(len(cuts)):
+            assert torch.equal(coeffs[k], first[k])
+
+
+def test_batch_results_match_oracle_and_report_a_singular_pair():
+    cuts = _cutouts(SIZES[:4], seed=60)
+    cuts[2]["T"] = torch.zeros_like(cuts[2]["T"])          # no template: rank-deficient design
+    n = oracle.n_unknowns(L, DK, DB)
+    pairs, coeffs, diffs = _pairs(cuts, n)
+    infos = sfft.sfft_batch(sfft.make_desc(128, 128, L, DK, DB), 2, 2, pairs)
+    assert [i.status for i in infos] == [0, 0, sfft.ERR_NOT_SPD, 0]
+    for k in (0, 1, 3):
+        c = cuts[k]
+        sl = (slice(c["oy"], c["oy"] + c["ny"]), slice(c["ox"], c["ox"] + c["nx"]))
+        S, T, M = (c[a][sl].cpu().numpy() for a in ("S", "T", "M"))
+        ref = oracle.fit(S, T, M, L, DK, DB)
+        th = coeffs[k].cpu().numpy()
+        assert np.linalg.norm(th - ref) <= 1e-6 * np.linalg.norm(ref)
+        Dref = oracle.subtract(S, T, th, L, DK, DB)
+        assert np.abs(diffs[k][:, :c["nx"]].cpu().numpy() - Dref).max() <= 1e-5 * np.abs(T).max()
+
+
+def test_graph_batch_with_pcg_warm_starts():
+    cuts = _cutouts(SIZES, seed=80)
+    n = oracle.n_unknowns(L, DK, DB)
+    # warm starts: the cold solutions perturbed by 1e-3
+    cold = [_single(c, n)[0] for c in cuts]
+    x0 = [t * (1 + 1e-3) for t in cold]
+    pairs, coeffs, _ = _pairs(cuts, n, x0=x0)
+    base = sfft.make_desc(128, 128, L, DK, DB, solver=sfft.SOLVE_PCG)
+    with sfft.sfft_batch_create(base, pairs, lanes=3, flags=sfft.BATCH_GRAPH) as b:
+        for _ in range(2):
+            sfft.sfft_batch_run(b)
+        infos = sfft.sfft_batch_info(b)
+    for k in range(len(cuts)):
+        assert infos[k].status == 0 and infos[k].fallback == 0
+        assert infos[k].start_residual < 1e-2
+        assert torch.linalg.norm(coeffs[k] - cold[k]) <= 1e-6 * torch.linalg.norm(cold[k])
+
+
+def test_autotune_stores_a_valid_shape_that_fits_correctly():
+    S, T, M = synth.roman_pair(512, 512, seed=5)
+    St, Tt, Mt = (torch.from_numpy(a).to(DEV) for a in (S, T, M))
+    d = sfft.make_desc(512, 512, 11, 2, 2)
+    t, ms = sfft.sfft_autotune(d, St, Tt, Mt, trials=2)
+    got, cached = sfft.sfft_tuning_get(d)
+    assert cached and ms > 0
+    assert (got.ycorr_bins, got.ycorr_split, got.ycorr_scalar, got.subtract_ctas) == \
+        (t.ycorr_bins, t.ycorr_split, t.ycorr_scalar, t.subtract_ctas)
+    with sfft.sfft_plan(d) as p:
+        th = torch.empty(p.n, dtype=torch.float64, device=DEV)
+        sfft.sfft_fit(p, St, Tt, Mt, None, th)
+    ref = oracle.fit(S, T, M, 11, 2, 2)
+    assert np.linalg.norm(th.cpu().numpy() - ref) <= 1e-6 * np.linalg.norm(ref)
