@@ -144,15 +144,16 @@ def run_ours(args, world, rank, local):
     stream = torch.cuda.current_stream(dev)
     n = L * L * (DK + 1) * (DK + 2) // 2 + (DB + 1) * (DB + 2) // 2
 
-    def timed(step, steps):
+    def timed(step, steps, name):
         """ms of `steps` calls of step(), CUDA events on the launching stream, barriers and
-        synchronisation on both sides."""
+        synchronisation on both sides; the loop is an NVTX range `name` (for profilers)."""
         barrier()
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        for _ in range(steps):
-            step()
+        with torch.cuda.nvtx.range(name):
+            for _ in range(steps):
+                step()
         e1.record(stream)
         torch.cuda.synchronize()
         barrier()
@@ -178,7 +179,7 @@ def run_ours(args, world, rank, local):
     info = sfft.sfft_fit(plan, *dev_pairs[0], None, coeffs[0], want_info=True)
     sfft.sfft_stage_times(plan)  # reset the accumulators
     sfft.sfft_profile(plan, True)
-    plain_ms = timed(plain_step, args.steps)
+    plain_ms = timed(plain_step, args.steps, "plain")
     stages, calls = sfft.sfft_stage_times(plan)
     sfft.sfft_profile(plan, False)
     plain_value = args.steps * args.pairs * world / (plain_ms / 1e3)
@@ -215,7 +216,7 @@ def run_ours(args, world, rank, local):
     clocks = ClockSampler(local)
     launches0 = sfft.sfft_launch_count()
     clocks.start()
-    ms = timed(batched_step, args.steps)
+    ms = timed(batched_step, args.steps, "batched")
     clk = clocks.stop()
     launches = sfft.sfft_launch_count() - launches0
     value = args.steps * args.pairs * world / (ms / 1e3)
@@ -239,7 +240,7 @@ def run_ours(args, world, rank, local):
     for _ in range(2):
         e2e_step()
     e2e_steps = max(2, args.steps // 2)
-    e2e_ms = timed(e2e_step, e2e_steps)
+    e2e_ms = timed(e2e_step, e2e_steps, "e2e")
     e2e_value = e2e_steps * args.pairs * world / (e2e_ms / 1e3)
     h2d = args.pairs * sum(t.numel() * t.element_size() for t in host[0])
     d2h = args.pairs * (host_D[0].numel() * 4 + n * 8)

@@ -217,14 +217,70 @@ __global__ void __launch_bounds__(256, 2) k_ycorr_f32(const cpx<float> *__restri
 // conj(a) w is split into two packed accumulators P += {a.re, a.re} * w and
 // Q += {a.im, a.im} * w (re = P.x + Q.y, im = P.y - Q.x at the fold), which halves the FMA
 // instruction count without any operand shuffles.
+//
+// Its tile is stored [frequency][image][row] (row stride RP complex values), so a thread's
+// A and B rows are contiguous and every row offset in the inner loop is an immediate; RP is
+// even and 2 mod 4, which keeps the 16-byte A loads aligned and spreads the eight images a
+// quarter-warp reads over distinct banks.  Each staging thread owns one (frequency, image)
+// column of the tile and a fixed set of rows, so no index is divided per element; A rows
+// past the end of the row chunk are staged as zeros instead of being masked per row.
+__host__ __device__ __forceinline__ int tile_rp(int rows) { return ((rows + 3) & ~3) + 2; }
+
+__device__ __forceinline__ void cp_async8(void *smem, const void *gmem) {
+    unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem));
+}
+
+// stages rows [0, rows) = frame rows y0 - G .. of frequencies k0 .. k0 + kcnt - 1 into the
+// [kk][img][row] tile; A images (img < nk) read zero at rows >= G + a_valid
+__device__ __forceinline__ void stage_tile_t(const cpx<float> *__restrict__ spec, const Geometry &g, int s, int k0,
+                                             int kcnt, int kg, int cw, int y0, int rows, int RP, int a_valid,
+                                             cpx<float> *buf) {
+    const int NPT = kg * cw, ny = g.ny, NI = g.nimg_pad;
+    int p0, pstep, r0, rstep;
+    if ((int)blockDim.x >= NPT) {
+        p0 = threadIdx.x % NPT;
+        pstep = NPT;
+        r0 = threadIdx.x / NPT;
+        rstep = blockDim.x / NPT;
+        if (r0 >= rstep) r0 = rows;  // leftover threads stage nothing
+    } else {
+        p0 = threadIdx.x;
+        pstep = blockDim.x;
+        r0 = 0;
+        rstep = 1;
+    }
+    const size_t row_stride = (size_t)g.nkf * NI;
+    for (int p = p0; p < NPT; p += pstep) {
+        const int kk = p / cw, img = p - kk * cw;
+        if (kk >= kcnt) continue;  // frequency past the spectrum: no thread reads it
+        const cpx<float> *src = spec + ((size_t)s * ny * g.nkf + k0 + kk) * NI + img;
+        cpx<float> *dst = buf + (size_t)p * RP;
+        const int zfrom = img < g.nk ? g.G + a_valid : rows;
+        int yy = y0 - g.G + r0;
+        yy = yy >= 0 && yy < ny ? yy : ((yy % ny) + ny) % ny;
+        for (int r = r0; r < rows; r += rstep) {
+            if (r >= zfrom)
+                dst[r] = cpx<float>{0.f, 0.f};
+            else
+                cp_async8(dst + r, src + (size_t)yy * row_stride);
+            yy += rstep;
+            if (yy >= ny) yy = rstep < ny ? yy - ny : yy % ny;
+        }
+    }
+    cp_async_commit();
+}
+
 template <int C, int TYP>
-__global__ void __launch_bounds__(256, 1) k_ycorr_f32x2(const cpx<float> *__restrict__ spec, Geometry g, Launch ln,
+__global__ void __launch_bounds__(256, (C <= 11 ? 2 : 1)) k_ycorr_f32x2(const cpx<float> *__restrict__ spec, Geometry g, Launch ln,
                                                        double *__restrict__ ypart) {
+    static_assert(TYP % 2 == 0, "A rows are loaded in pairs");
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int YT = g.ytile, G = g.G, ny = g.ny;
-    const int rows = YT + 2 * G;
+    const int rows = YT + 2 * G, RP = tile_rp(rows);
+    const int cw = ln.cw;
     cpx<float> *buf0 = reinterpret_cast<cpx<float> *>(smem_raw);
-    cpx<float> *buf1 = buf0 + (size_t)rows * ln.kg * ln.cw;
+    cpx<float> *buf1 = buf0 + (size_t)ln.kg * cw * RP;
     const int s = blockIdx.x / ln.ysplit, ych = blockIdx.x % ln.ysplit;
     const int k0 = blockIdx.y * ln.kg;
     const int kcnt = min(ln.kg, g.nkf - k0);
@@ -233,34 +289,35 @@ __global__ void __launch_bounds__(256, 1) k_ycorr_f32x2(const cpx<float> *__rest
     const int tid = threadIdx.x;
     const int kl = tid / ln.items, it = tid - kl * ln.items;
     const bool active = kl < kcnt;
-    Item m = decode_item(g, active ? it : 0, ln.ws_only);
+    Item m = decode_item(g, active ? it : 0, false);
     float2 P[C], Q[C], hi[C], lo[C];
 #pragma unroll
     for (int c = 0; c < C; c++) P[c] = Q[c] = hi[c] = lo[c] = make_float2(0.f, 0.f);
-    const int rs = ln.kg * ln.cw;
-    if (ya < yb) stage_tile(spec, g, s, k0, kcnt, ln.kg, ya, rows, ln.ws_only, ln.cw, buf0);
+    if (ya < yb) stage_tile_t(spec, g, s, k0, kcnt, ln.kg, cw, ya, rows, RP, min(YT, yb - ya), buf0);
     int cur = 0;
     for (int y0 = ya; y0 < yb; y0 += YT) {
         cp_async_wait_all();
         __syncthreads();
-        cpx<float> *tile = cur ? buf1 : buf0;
-        if (y0 + YT < yb) stage_tile(spec, g, s, k0, kcnt, ln.kg, y0 + YT, rows, ln.ws_only, ln.cw, cur ? buf0 : buf1);
+        const cpx<float> *tile = cur ? buf1 : buf0;
+        if (y0 + YT < yb)
+            stage_tile_t(spec, g, s, k0, kcnt, ln.kg, cw, y0 + YT, rows, RP, min(YT, yb - y0 - YT), cur ? buf0 : buf1);
         if (active) {
             const int yvalid = min(YT, yb - y0);
-            const float2 *ta = reinterpret_cast<const float2 *>(tile + (size_t)kl * ln.cw + m.A);
-            const float2 *tb = reinterpret_cast<const float2 *>(tile + (size_t)kl * ln.cw + m.B);
+            const float4 *ta = reinterpret_cast<const float4 *>(tile + (size_t)(kl * cw + m.A) * RP + G);
+            const float2 *tb = reinterpret_cast<const float2 *>(tile + (size_t)(kl * cw + m.B) * RP + G + m.dylo);
             for (int yy = 0; yy < yvalid; yy += TYP) {
                 float2 ar[TYP], ai[TYP];
 #pragma unroll
-                for (int t = 0; t < TYP; t++) {
-                    float2 v = ta[(size_t)(G + yy + t) * rs];
-                    bool ok = yy + t < yvalid;
-                    ar[t] = make_float2(ok ? v.x : 0.f, ok ? v.x : 0.f);
-                    ai[t] = make_float2(ok ? v.y : 0.f, ok ? v.y : 0.f);
+                for (int t = 0; t < TYP; t += 2) {
+                    const float4 v = ta[(yy + t) >> 1];  // rows yy + t, yy + t + 1 (zero past the chunk)
+                    ar[t] = make_float2(v.x, v.x);
+                    ai[t] = make_float2(v.y, v.y);
+                    ar[t + 1] = make_float2(v.z, v.z);
+                    ai[t + 1] = make_float2(v.w, v.w);
                 }
                 float2 w[C + TYP - 1];
 #pragma unroll
-                for (int q = 0; q < C + TYP - 1; q++) w[q] = tb[(size_t)(G + yy + m.dylo + q) * rs];
+                for (int q = 0; q < C + TYP - 1; q++) w[q] = tb[yy + q];
 #pragma unroll
                 for (int t = 0; t < TYP; t++)
 #pragma unroll
@@ -452,8 +509,9 @@ cudaError_t run(const Geometry &g, int precision, const void *spec, double *ypar
         note_launch();
         k_ycorr_f64<C><<<grid, threads, sm, st>>>((const cpx<double> *)spec, g, ln, ypart);
     } else {
-        size_t sm = 2 * rows * ln.kg * ln.cw * sizeof(cpx<float>);
-        // packed FP32x2 variant unless the tuning picked the scalar one
+        // packed FP32x2 variant (transposed tile) unless the tuning picked the scalar one
+        size_t sm = g.ycorr_scalar ? 2 * rows * ln.kg * ln.cw * sizeof(cpx<float>)
+                                   : 2 * (size_t)tile_rp((int)rows) * ln.kg * ln.cw * sizeof(cpx<float>);
         auto kern = g.ycorr_scalar ? k_ycorr_f32<C> : k_ycorr_f32x2<C, 4>;
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e == cudaSuccess)
