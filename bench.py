@@ -45,8 +45,31 @@ def parse():
     ap.add_argument("--pairs", type=int, default=4, help="pairs per step per rank")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--train-samples", type=int, default=2048, help="warm-start network training fits")
+    ap.add_argument("--frame", type=int, default=NY, help="frame side (smaller frames are for profiling runs)")
+    ap.add_argument("--plain-only", action="store_true", help="time the plain form only (profiling runs)")
     ap.add_argument("--train-epochs", type=int, default=40)
     return ap.parse_args()
+
+
+def pair_seeds(rank: int, pairs: int):
+    """Seeds of this rank's pairs: ranks draw disjoint pairs (weak scaling, no shared data)."""
+    return [1000 + 100 * rank + i for i in range(pairs)]
+
+
+def max_over_ranks(v: float, world: int, device=None) -> float:
+    """Largest value over the ranks (the timed region ends when the slowest rank ends)."""
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def weak_value(steps: int, pairs: int, world: int, ms: float) -> float:
+    """Whole-job difference images per second: every rank's pairs over the slowest rank's time."""
+    return steps * pairs * world / (ms / 1e3)
 
 
 def dist_env():
@@ -132,14 +155,9 @@ def run_ours(args, world, rank, local):
         if world > 1:
             dist.barrier()
 
-    def max_over_ranks(v):
-        if world == 1:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
-
-    pairs = [synth.roman_pair(NY, NX, seed=1000 + 100 * rank + i) for i in range(args.pairs)]
+    NY = NX = args.frame
+    workload = WORKLOAD if args.frame == 4088 else WORKLOAD.replace("4088x4088", "%dx%d" % (NY, NX))
+    pairs = [synth.roman_pair(NY, NX, seed=sd) for sd in pair_seeds(rank, args.pairs)]
     dev_pairs = [tuple(torch.from_numpy(a).to(dev) for a in p) for p in pairs]
     stream = torch.cuda.current_stream(dev)
     n = L * L * (DK + 1) * (DK + 2) // 2 + (DB + 1) * (DB + 2) // 2
@@ -157,7 +175,7 @@ def run_ours(args, world, rank, local):
         e1.record(stream)
         torch.cuda.synchronize()
         barrier()
-        return max_over_ranks(e0.elapsed_time(e1))
+        return max_over_ranks(e0.elapsed_time(e1), world, dev)
 
     # ================= plain: one plan, pairs in sequence, FP64 Cholesky
     plan = sfft.sfft_plan(sfft.make_desc(NY, NX, L, DK, DB), stream=stream)
@@ -182,7 +200,21 @@ def run_ours(args, world, rank, local):
     plain_ms = timed(plain_step, args.steps, "plain")
     stages, calls = sfft.sfft_stage_times(plan)
     sfft.sfft_profile(plan, False)
-    plain_value = args.steps * args.pairs * world / (plain_ms / 1e3)
+    plain_value = weak_value(args.steps, args.pairs, world, plain_ms)
+    if args.plain_only:
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": round(plain_value, 3), "unit": UNIT, "n_gpus": world,
+                              "steps": args.steps, "warmup": args.warmup,
+                              "ms_per_step": round(plain_ms / args.steps, 3), "higher_is_better": True,
+                              "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                              "config": {"workload": workload, "mode": "plain only (profiling run)",
+                                         "pairs_per_step_per_rank": args.pairs},
+                              "stages_ms_per_pair": {k: round(v / max(calls, 1), 4) for k, v in stages.items()}}),
+                  flush=True)
+        plan.close()
+        if world > 1:
+            dist.destroy_process_group()
+        return
 
     # ================= batched + learned: CNN warm starts, graph-captured PCG batch in lanes
     t0 = time.perf_counter()
@@ -219,7 +251,7 @@ def run_ours(args, world, rank, local):
     ms = timed(batched_step, args.steps, "batched")
     clk = clocks.stop()
     launches = sfft.sfft_launch_count() - launches0
-    value = args.steps * args.pairs * world / (ms / 1e3)
+    value = weak_value(args.steps, args.pairs, world, ms)
     binfos = sfft.sfft_batch_info(batch)
 
     # ---- end to end through the public API with pinned host buffers (batched + learned)
@@ -241,7 +273,7 @@ def run_ours(args, world, rank, local):
         e2e_step()
     e2e_steps = max(2, args.steps // 2)
     e2e_ms = timed(e2e_step, e2e_steps, "e2e")
-    e2e_value = e2e_steps * args.pairs * world / (e2e_ms / 1e3)
+    e2e_value = weak_value(e2e_steps, args.pairs, world, e2e_ms)
     h2d = args.pairs * sum(t.numel() * t.element_size() for t in host[0])
     d2h = args.pairs * (host_D[0].numel() * 4 + n * 8)
 
@@ -270,7 +302,7 @@ def run_ours(args, world, rank, local):
         "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 3), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "frame": "%dx%d" % (NY, NX), "L": L, "dk": DK, "db": DB,
+        "config": {"workload": workload, "frame": "%dx%d" % (NY, NX), "L": L, "dk": DK, "db": DB,
                    "pairs_per_step_per_rank": args.pairs,
                    "mode": "batched+learned: CNN warm starts, %d-lane CUDA-graph batch, autotuned, cluster PCG "
                            "(FP32 Cholesky preconditioner, FP64 residuals), FP32 spectra, one compensated "

@@ -70,15 +70,19 @@ typedef struct {
     int32_t dk;            /* kernel spatial polynomial degree, >= 0 */
     int32_t db;            /* background polynomial degree, >= 0 */
     int32_t dtype;         /* SFFT_F32 or SFFT_F64 (science, template and difference image) */
-    int32_t precision;     /* SFFT_PREC_FP32: FP32 products/FFTs/correlations, FP64 from the
-                              lag tables on; SFFT_PREC_FP64: FP64 throughout */
+    int32_t precision;     /* SFFT_PREC_SPLIT: FP32 products and FFTs, cross-spectra summed in
+                              FP32 per 64-row tile and folded into split hi/lo pairs, FP64 from
+                              the lag tables on, and one refinement pass with a compensated
+                              residual (coefficients within ~1e-6 of the FP64 answer);
+                              SFFT_PREC_FP32: the same kernels without refinement (faster,
+                              ~1e-6 .. 4e-5); SFFT_PREC_FP64: FP64 throughout */
     int32_t solver;        /* SFFT_SOLVE_CHOLESKY (FP64 Cholesky + one refinement step) */
     int32_t max_iter;      /* PCG iteration cap (0 = default) */
     double tol;            /* PCG relative-residual tolerance (0 = default 1e-12) */
     size_t workspace_cap;  /* bytes the plan may allocate; 0 = no cap */
     int32_t seg;           /* row-segment FFT length P (0 = default 256); P >= 2(L-1)+1 */
     int32_t refine;        /* residual refinement passes after the solve: 0 = default (1 for
-                              SFFT_PREC_FP32, none for SFFT_PREC_FP64), < 0 = none, > 0 = count.
+                              SFFT_PREC_SPLIT, none otherwise), < 0 = none, > 0 = count.
                               A pass forms the residual image of the fit on the masked frames,
                               correlates it with the basis through the same segment spectra,
                               and corrects theta with the existing factorisation. */

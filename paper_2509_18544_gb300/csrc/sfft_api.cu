@@ -117,13 +117,12 @@ bool make_geometry(const sfft_desc &d, Geometry &g, char *err, size_t errlen) {
         if (yc > max_yc) yc = max_yc;
         g.ychunks_ws = yc < 1 ? 1 : yc;
     }
-    g.refine = d.refine < 0 ? 0 : (d.refine > 0 ? d.refine : (d.precision == SFFT_PREC_FP64 ? 0 : 1));
+    g.refine = d.refine < 0 ? 0 : (d.refine > 0 ? d.refine : (d.precision == SFFT_PREC_SPLIT ? 1 : 0));
     if (d.db > 4) return snprintf(err, errlen, "db=%d > 4 not supported", d.db), false;
     g.mom_rows = 128;
     g.mom_ctas = ((d.nx + 255) / 256) * ((d.ny + g.mom_rows - 1) / g.mom_rows);
     g.nmom = npoly(2 * d.db) + npoly(d.db);
     g.pmax = d.dk > 2 * d.db ? d.dk : 2 * d.db;
-    if (d.precision == SFFT_PREC_SPLIT) return snprintf(err, errlen, "split precision not built yet"), false;
     return true;
 }
 

@@ -90,26 +90,60 @@ __device__ __forceinline__ int wrapi(int v, int n) {
 template <class R, int LL>
 size_t stream_smem(int np, int db) {
     using W = Win<R, LL>;
-    return sizeof(R) * ((size_t)np * W::RING * W::WCS + (size_t)kBand * LL * np * LL + (size_t)kBand * (db + 1));
+    const int npx = np > db + 1 ? np : db + 1;
+    return sizeof(R) * ((size_t)np * W::RING * W::WCS + (size_t)kBand * LL * np * LL + (size_t)kBand * (db + 1) +
+                        (size_t)npx * W::WC);
+}
+
+// xh^p of the strip's window columns (x0 - h ..), p < npx: xps[p][c]
+template <class R, int LL>
+__device__ __forceinline__ void fill_xps(const Geometry &g, const R *__restrict__ xpow_g, int x0, int npx, R *xps) {
+    using W = Win<R, LL>;
+    for (int e = threadIdx.x; e < npx * W::WC; e += blockDim.x) {
+        const int p = e / W::WC, c = e - p * W::WC;
+        xps[e] = xpow_g[(size_t)p * g.nx + wrapi(x0 - W::h + c, g.nx)];
+    }
 }
 
 // Stages `count` consecutive source rows starting at (unwrapped) row ys0 into their ring
-// slots, as np planes xh^p T (T_m when `masked`).
+// slots, as np planes xh^p T (T_m when `masked`).  Each thread first issues the loads of
+// kBatch elements, then forms and stores their planes, so a band costs a few load
+// latencies rather than one per element.
 template <class R, class In, int LL>
 __device__ __forceinline__ void stage_rows(const In *__restrict__ tmpl, const uint8_t *__restrict__ mask, bool masked,
-                                           const Geometry &g, const R *__restrict__ xpow_g, int x0, int ys0, int count,
+                                           const Geometry &g, const R *xps, int x0, int ys0, int count,
                                            int ring_origin, R *Tp) {
     using W = Win<R, LL>;
-    const int np = g.dk + 1, nx = g.nx;
-    for (int e = threadIdx.x; e < count * W::WC; e += blockDim.x) {
-        const int r = e / W::WC, c = e - r * W::WC;
-        const int ys = ys0 + r;
-        const int yy = wrapi(ys, g.ny), xx = wrapi(x0 - W::h + c, nx);
-        const size_t u = (size_t)yy * g.pitch + xx;
-        const R tv = (masked && mask && mask[u]) ? (R)0 : (R)tmpl[u];
-        R *dst = Tp + (size_t)((ys - ring_origin) % W::RING) * W::WCS + skew<R>(c);
-        dst[0] = tv;
-        for (int p = 1; p < np; p++) dst[(size_t)p * W::RING * W::WCS] = tv * xpow_g[(size_t)p * nx + xx];
+    constexpr int kBatch = 8;
+    const int np = g.dk + 1, nx = g.nx, total = count * W::WC;
+    for (int base = 0; base < total; base += kBatch * (int)blockDim.x) {
+        In tv[kBatch];
+        unsigned char bad[kBatch];
+        int col[kBatch], slot[kBatch];
+#pragma unroll
+        for (int i = 0; i < kBatch; i++) {
+            const int e = base + i * (int)blockDim.x + (int)threadIdx.x;
+            col[i] = -1;
+            tv[i] = (In)0;
+            bad[i] = 0;
+            if (e < total) {
+                const int r = e / W::WC, c = e - r * W::WC;
+                const int ys = ys0 + r;
+                const size_t u = (size_t)wrapi(ys, g.ny) * g.pitch + wrapi(x0 - W::h + c, nx);
+                tv[i] = tmpl[u];
+                bad[i] = masked && mask ? mask[u] : 0;
+                col[i] = c;
+                slot[i] = (ys - ring_origin) % W::RING;
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < kBatch; i++) {
+            if (col[i] < 0) continue;
+            const R t = bad[i] ? (R)0 : (R)tv[i];
+            R *dst = Tp + (size_t)slot[i] * W::WCS + skew<R>(col[i]);
+            dst[0] = t;
+            for (int p = 1; p < np; p++) dst[(size_t)p * W::RING * W::WCS] = t * xps[p * W::WC + col[i]];
+        }
     }
 }
 
@@ -149,6 +183,8 @@ __global__ void __launch_bounds__(32 * kBand) k_subtract(const In *__restrict__ 
     R *Tp = reinterpret_cast<R *>(smem_raw);   // [np][RING][WCS]
     R *cf = Tp + np * W::RING * W::WCS;         // [kBand][LL][np][LL]
     R *byp = cf + kBand * LL * np * LL;         // [kBand][db+1]
+    R *xps = byp + kBand * (g.db + 1);          // [npx][WC]
+    const int npx = np > g.db + 1 ? np : g.db + 1;
 
     const int x0 = blockIdx.x * Tile<R>::kCols;
     const int yc0 = blockIdx.y * rows_per_chunk, yc1 = min(ny, yc0 + rows_per_chunk);
@@ -157,11 +193,24 @@ __global__ void __launch_bounds__(32 * kBand) k_subtract(const In *__restrict__ 
     const int ty = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int cx = lane * kRX;
 
-    stage_rows<R, In, LL>(tmpl, mask, residual, g, xpow_g, x0, yc0 - h, W::RING, ring_origin, Tp);
+    fill_xps<R, LL>(g, xpow_g, x0, npx, xps);
+    __syncthreads();
+    stage_rows<R, In, LL>(tmpl, mask, residual, g, xps, x0, yc0 - h, W::RING, ring_origin, Tp);
     for (int yb = yc0; yb < yc1; yb += kBand) {
         stage_coeffs<R, LL>(g, cfold, yb, cf, byp);
         __syncthreads();
         const int y = yb + ty;
+        // this row's science values and mask bytes, loaded before the convolution
+        In sv[kRX];
+        unsigned char mv[kRX];
+#pragma unroll
+        for (int r = 0; r < kRX; r++) {
+            const int x = x0 + cx + r;
+            const bool ok = y < yc1 && x < nx;
+            const size_t u = (size_t)y * g.pitch + x;
+            sv[r] = ok ? sci[u] : (In)0;
+            mv[r] = ok && residual && mask ? mask[u] : 0;
+        }
         R out[kRX];
 #pragma unroll
         for (int r = 0; r < kRX; r++) out[r] = (R)0;
@@ -190,13 +239,13 @@ __global__ void __launch_bounds__(32 * kBand) k_subtract(const In *__restrict__ 
                 const int x = x0 + cx + r;
                 if (x < nx) {
                     R bg = (R)0;
-                    for (int p = 0; p <= g.db; p++) bg += bp[p] * xpow_g[(size_t)p * nx + x];
+                    for (int p = 0; p <= g.db; p++) bg += bp[p] * xps[p * W::WC + cx + r + h];
                     const size_t u = (size_t)y * g.pitch + x;
                     if (residual) {
-                        const R m = (mask && mask[u]) ? (R)0 : (R)1;
-                        diff[u] = (In)(m * ((R)sci[u] - bg) - out[r]);
+                        const R m = mv[r] ? (R)0 : (R)1;
+                        diff[u] = (In)(m * ((R)sv[r] - bg) - out[r]);
                     } else {
-                        diff[u] = (In)((R)sci[u] - out[r] - bg);
+                        diff[u] = (In)((R)sv[r] - out[r] - bg);
                     }
                 }
             }
@@ -204,7 +253,7 @@ __global__ void __launch_bounds__(32 * kBand) k_subtract(const In *__restrict__ 
         __syncthreads();
         // the next band reads source rows up to yb + 2 kBand + h - 1; the kBand new ones
         // replace rows yb - h .. yb - h + kBand - 1, which no later band reads
-        if (yb + kBand < yc1) stage_rows<R, In, LL>(tmpl, mask, residual, g, xpow_g, x0, yb + kBand + h, kBand,
+        if (yb + kBand < yc1) stage_rows<R, In, LL>(tmpl, mask, residual, g, xps, x0, yb + kBand + h, kBand,
                                                     ring_origin, Tp);
     }
 }
@@ -259,6 +308,8 @@ __global__ void __launch_bounds__(16 * kBand, 2) k_residual_comp(const In *__res
     float *Tp = reinterpret_cast<float *>(smem_raw);
     float *cf = Tp + np * W::RING * W::WCS;
     float *byp = cf + kBand * LL * np * LL;
+    float *xps = byp + kBand * (g.db + 1);
+    const int npx = np > g.db + 1 ? np : g.db + 1;
 
     const int x0 = blockIdx.x * Tile<float>::kCols;
     const int yc0 = blockIdx.y * rows_per_chunk, yc1 = min(ny, yc0 + rows_per_chunk);
@@ -267,7 +318,9 @@ __global__ void __launch_bounds__(16 * kBand, 2) k_residual_comp(const In *__res
     const int ty = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int cx = lane * kRX;
 
-    stage_rows<float, In, LL>(tmpl, mask, true, g, xpow_g, x0, yc0 - h, W::RING, ring_origin, Tp);
+    fill_xps<float, LL>(g, xpow_g, x0, npx, xps);
+    __syncthreads();
+    stage_rows<float, In, LL>(tmpl, mask, true, g, xps, x0, yc0 - h, W::RING, ring_origin, Tp);
     for (int yb = yc0; yb < yc1; yb += kBand) {
         stage_coeffs<float, LL>(g, cfold, yb, cf, byp);
         __syncthreads();
@@ -287,7 +340,7 @@ __global__ void __launch_bounds__(16 * kBand, 2) k_residual_comp(const In *__res
                         split_input<In>(sci[u], sh[k], sl[k]);
                         const float *bp = byp + (k ? ty + kHalf : ty) * (g.db + 1);
                         float b = 0.f;
-                        for (int p = 0; p <= g.db; p++) b = fmaf(bp[p], xpow_g[(size_t)p * nx + x], b);
+                        for (int p = 0; p <= g.db; p++) b = fmaf(bp[p], xps[p * W::WC + cx + r + h], b);
                         bg[k] = b;
                     }
                 }
@@ -348,7 +401,7 @@ __global__ void __launch_bounds__(16 * kBand, 2) k_residual_comp(const In *__res
         }
         __syncthreads();
         if (yb + kBand < yc1)
-            stage_rows<float, In, LL>(tmpl, mask, true, g, xpow_g, x0, yb + kBand + h, kBand, ring_origin, Tp);
+            stage_rows<float, In, LL>(tmpl, mask, true, g, xps, x0, yb + kBand + h, kBand, ring_origin, Tp);
     }
 }
 

@@ -187,7 +187,7 @@ class Plan:
         self.close()
 
 
-def make_desc(ny, nx, L, dk, db, dtype=F32, precision=PREC_FP32, solver=SOLVE_CHOLESKY, pitch=0,
+def make_desc(ny, nx, L, dk, db, dtype=F32, precision=PREC_SPLIT, solver=SOLVE_CHOLESKY, pitch=0,
               max_iter=0, tol=0.0, workspace_cap=0, seg=0, refine=0) -> sfft_desc:
     d = sfft_desc()
     d.ny, d.nx, d.pitch, d.L, d.dk, d.db = ny, nx, pitch, L, dk, db
