@@ -125,6 +125,7 @@ __global__ void __launch_bounds__(MAXT, MINB) k_segment_fft(const In *__restrict
     int *ik = reinterpret_cast<int *>(mv + 2 * kP);     // [nimg_pad] kind
     int *ip = ik + NI;                                  // [nimg_pad] p
     int *iq = ip + NI;                                  // [nimg_pad] q
+    int *wcol = iq + NI;                                // [P] frame column of each window column
 
     for (int i = tid; i < kP; i += nthr) {
         tw[i] = tw_g[i];
@@ -134,6 +135,7 @@ __global__ void __launch_bounds__(MAXT, MINB) k_segment_fft(const In *__restrict
         int xw = wrapi(x0 - G + i, nx);
         for (int p = 0; p <= maxdeg; p++) xpow[p * kP + i] = xpow_g[(size_t)p * nx + xw];
         ones[i] = (R)1;
+        wcol[i] = xw;
     }
     for (int i = tid; i < NI; i += nthr) {
         // kinds: 0 = A (W_i on own columns), 1 = B W_i, 2 = Psi_r, 3 = S_m, 4 = zero pad
@@ -151,14 +153,16 @@ __global__ void __launch_bounds__(MAXT, MINB) k_segment_fft(const In *__restrict
     }
 
     const int ybeg = blockIdx.y * kRowsPerCta, yend = min(ny, ybeg + kRowsPerCta);
-    // window positions loaded per thread per pass (2 rows x P positions)
+    // window positions loaded per thread per pass (2 rows x P positions): position
+    // q = tid + c nthr is row q / P, window column q % P; its wrapped frame column is fixed
+    // for the whole kernel, so it is computed once
     constexpr int kMaxPf = 4;
     const int npos = 2 * kP;
-    auto load_pos = [&](int q, int ybase, R &t_out, R &s_out, R &m_out) {
-        int r = q / kP, j = q - r * kP, y = ybase + r;
+    auto load_pos = [&](int c, int ybase, R &t_out, R &s_out, R &m_out) {
+        const int q = tid + c * nthr;
+        const int y = ybase + (q >> 8);
         if (y < yend) {
-            int xw = wrapi(x0 - G + j, nx);
-            size_t u = (size_t)y * g.pitch + xw;
+            const size_t u = (size_t)y * g.pitch + wcol[q & (kP - 1)];
             R good = (mask && mask[u]) ? (R)0 : (R)1;
             t_out = good * (R)tmpl[u];
             s_out = good * (R)sci[u];
@@ -167,8 +171,21 @@ __global__ void __launch_bounds__(MAXT, MINB) k_segment_fft(const In *__restrict
             t_out = s_out = m_out = (R)0;
         }
     };
+    __syncthreads();  // wcol
     // prologue: window of the first pass straight to shared memory
-    for (int q = tid; q < npos; q += nthr) load_pos(q, ybeg, tv[q], sv[q], mv[q]);
+#pragma unroll
+    for (int c = 0; c < kMaxPf; c++) {
+        const int q = tid + c * nthr;
+        if (q < npos) load_pos(c, ybeg, tv[q], sv[q], mv[q]);
+    }
+    for (int q = tid + kMaxPf * nthr; q < npos; q += nthr) {  // only with fewer than 128 threads
+        const int r = q >> 8, y = ybeg + r;
+        const size_t u = (size_t)y * g.pitch + wrapi(x0 - G + (q & (kP - 1)), nx);
+        const R good = y < yend ? ((mask && mask[u]) ? (R)0 : (R)1) : (R)0;
+        tv[q] = y < yend ? good * (R)tmpl[u] : (R)0;
+        sv[q] = y < yend ? good * (R)sci[u] : (R)0;
+        mv[q] = good;
+    }
     __syncthreads();
 
     const int r_fft = tid / per_row, rem = tid - r_fft * per_row;
@@ -180,7 +197,7 @@ __global__ void __launch_bounds__(MAXT, MINB) k_segment_fft(const In *__restrict
 #pragma unroll
         for (int c = 0; c < kMaxPf; c++) {
             int q = tid + c * nthr;
-            if (more && q < npos) load_pos(q, y0 + 2, pft[c], pfs[c], pfm[c]);
+            if (more && q < npos) load_pos(c, y0 + 2, pft[c], pfs[c], pfm[c]);
         }
         // FFT lanes of this warp: each half-warp is one FFT of a row that exists
         auto half_active = [&](int base) {
@@ -229,17 +246,33 @@ __global__ void __launch_bounds__(MAXT, MINB) k_segment_fft(const In *__restrict
         // unpack the packed real pairs; each row segment is one contiguous block
         const int per_out = nkf * NI;
         const int nrow = min(2, yend - y0);
-        for (int idx = tid; idx < nrow * per_out; idx += nthr) {
-            const int rr = idx / per_out, r2 = idx - rr * per_out;
-            const int k = r2 / NI, img = r2 - k * NI;
-            const cpx<R> *e = ex + (rr * g.nfft + (img >> 1)) * kEx;
-            cpx<R> zk = e[k], zc = e[(kP - k) & (kP - 1)];
-            cpx<R> out;
-            if ((img & 1) == 0)
-                out = {(R)0.5 * (zk.re + zc.re), (R)0.5 * (zk.im - zc.im)};
-            else
-                out = {(R)0.5 * (zk.im + zc.im), (R)0.5 * (zc.re - zk.re)};
-            spec[((size_t)s * ny + (y0 + rr)) * per_out + r2] = out;
+        if (nthr % NI == 0) {
+            // every thread keeps one image and walks the bins (consecutive threads write
+            // consecutive values), so no index is divided per value
+            const int img = tid % NI, kstep = nthr / NI;
+            const bool odd = img & 1;
+            for (int rr = 0; rr < nrow; rr++) {
+                const cpx<R> *e = ex + (rr * g.nfft + (img >> 1)) * kEx;
+                cpx<R> *o = spec + ((size_t)s * ny + (y0 + rr)) * per_out + img;
+                for (int k = tid / NI; k < nkf; k += kstep) {
+                    const cpx<R> zk = e[k], zc = e[(kP - k) & (kP - 1)];
+                    o[(size_t)k * NI] = odd ? cpx<R>{(R)0.5 * (zk.im + zc.im), (R)0.5 * (zc.re - zk.re)}
+                                            : cpx<R>{(R)0.5 * (zk.re + zc.re), (R)0.5 * (zk.im - zc.im)};
+                }
+            }
+        } else {
+            for (int idx = tid; idx < nrow * per_out; idx += nthr) {
+                const int rr = idx / per_out, r2 = idx - rr * per_out;
+                const int k = r2 / NI, img = r2 - k * NI;
+                const cpx<R> *e = ex + (rr * g.nfft + (img >> 1)) * kEx;
+                cpx<R> zk = e[k], zc = e[(kP - k) & (kP - 1)];
+                cpx<R> out;
+                if ((img & 1) == 0)
+                    out = {(R)0.5 * (zk.re + zc.re), (R)0.5 * (zk.im - zc.im)};
+                else
+                    out = {(R)0.5 * (zk.im + zc.im), (R)0.5 * (zc.re - zk.re)};
+                spec[((size_t)s * ny + (y0 + rr)) * per_out + r2] = out;
+            }
         }
         // the next pass's window (its FFT readers are past the barrier above)
 #pragma unroll
@@ -302,7 +335,7 @@ template <class R>
 size_t segfft_smem(const Geometry &g) {
     const int maxdeg = g.dk > g.db ? g.dk : g.db;
     return sizeof(cpx<R>) * (2 * kP + (size_t)2 * g.nfft * kEx) +
-           sizeof(R) * ((size_t)(maxdeg + 2) * kP + 6 * kP) + sizeof(int) * 3 * g.nimg_pad;
+           sizeof(R) * ((size_t)(maxdeg + 2) * kP + 6 * kP) + sizeof(int) * (3 * g.nimg_pad + kP);
 }
 
 template <class R, class In>
