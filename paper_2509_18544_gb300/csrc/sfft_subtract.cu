@@ -69,16 +69,26 @@ template <class R> struct Tile {
     static constexpr int kRX = 32 / (int)sizeof(R);   // consecutive pixels per lane
     static constexpr int kCols = 32 * kRX;            // strip width
 };
-// Lanes read register windows starting kRX columns apart; one pad word every 8 floats
-// (every 4 doubles) puts the 32 lanes' (16 half-warp lanes') reads on distinct banks.
-template <class R>
-__device__ __forceinline__ int skew(int c) { return sizeof(R) == 4 ? c + (c >> 3) : c + (c >> 2); }
-template <class R, int LL> struct Win {
+// Lanes read register windows starting kRX columns apart.  FP32: the window is read as
+// 16-byte vectors, and a 4-word pad after every 32 words puts the 8 lanes of a quarter-warp
+// (starting 8 words apart) on distinct banks.  FP64: one pad word every 4 doubles puts the
+// 16 lanes of a half-warp on distinct bank pairs.
+// (VEC = false: FP32 windows read as scalars, one pad word every 8 floats, for kernels that
+// pack two rows' values into FP32x2 operands.)
+template <class R, bool VEC = true>
+__device__ __forceinline__ int skew(int c) {
+    return sizeof(R) == 4 ? (VEC ? c + 4 * (c >> 5) : c + (c >> 3)) : c + (c >> 2);
+}
+template <class R, int LL, bool VEC = true> struct Win {
     static constexpr int h = LL / 2;
-    static constexpr int WC = Tile<R>::kCols + 2 * h;                               // window columns
-    static constexpr int WCS = sizeof(R) == 4 ? WC + WC / 8 + 1 : WC + WC / 4 + 1;  // skewed row length
-    static constexpr int RING = kBand + 2 * h;                                       // ring rows
-    static constexpr int NW = Tile<R>::kRX + LL - 1;                                 // register window
+    static constexpr int WC = Tile<R>::kCols + 2 * h;                                           // window columns
+    static constexpr int WCS = sizeof(R) == 4 ? (VEC ? (WC + 4 * ((WC + 31) / 32) + 3) / 4 * 4 : WC + WC / 8 + 1)
+                                              : WC + WC / 4 + 1;                                 // padded row
+    static constexpr int RING = kBand + 2 * h;                                                   // ring rows
+    static constexpr int NW = Tile<R>::kRX + LL - 1;                                             // register window
+    static constexpr int NW4 = (NW + 3) / 4;                                                     // 16-byte loads of it
+    static constexpr int LLP = (LL + 3) / 4 * 4;                                                 // coefficient row stride
+    static_assert(NW4 * 4 >= NW && LLP >= LL, "window and coefficient rows cover their values");
 };
 
 __device__ __forceinline__ int wrapi(int v, int n) {
@@ -87,11 +97,11 @@ __device__ __forceinline__ int wrapi(int v, int n) {
     return v < 0 ? v + n : v;
 }
 
-template <class R, int LL>
+template <class R, int LL, bool VEC = true>
 size_t stream_smem(int np, int db) {
-    using W = Win<R, LL>;
+    using W = Win<R, LL, VEC>;
     const int npx = np > db + 1 ? np : db + 1;
-    return sizeof(R) * ((size_t)np * W::RING * W::WCS + (size_t)kBand * LL * np * LL + (size_t)kBand * (db + 1) +
+    return sizeof(R) * ((size_t)np * W::RING * W::WCS + (size_t)kBand * LL * np * W::LLP + (size_t)kBand * (db + 1) +
                         (size_t)npx * W::WC);
 }
 
@@ -109,11 +119,11 @@ __device__ __forceinline__ void fill_xps(const Geometry &g, const R *__restrict_
 // slots, as np planes xh^p T (T_m when `masked`).  Each thread first issues the loads of
 // kBatch elements, then forms and stores their planes, so a band costs a few load
 // latencies rather than one per element.
-template <class R, class In, int LL>
+template <class R, class In, int LL, bool VEC = true>
 __device__ __forceinline__ void stage_rows(const In *__restrict__ tmpl, const uint8_t *__restrict__ mask, bool masked,
                                            const Geometry &g, const R *xps, int x0, int ys0, int count,
                                            int ring_origin, R *Tp) {
-    using W = Win<R, LL>;
+    using W = Win<R, LL, VEC>;
     constexpr int kBatch = 8;
     const int np = g.dk + 1, nx = g.nx, total = count * W::WC;
     for (int base = 0; base < total; base += kBatch * (int)blockDim.x) {
@@ -140,7 +150,7 @@ __device__ __forceinline__ void stage_rows(const In *__restrict__ tmpl, const ui
         for (int i = 0; i < kBatch; i++) {
             if (col[i] < 0) continue;
             const R t = bad[i] ? (R)0 : (R)tv[i];
-            R *dst = Tp + (size_t)slot[i] * W::WCS + skew<R>(col[i]);
+            R *dst = Tp + (size_t)slot[i] * W::WCS + skew<R, VEC>(col[i]);
             dst[0] = t;
             for (int p = 1; p < np; p++) dst[(size_t)p * W::RING * W::WCS] = t * xps[p * W::WC + col[i]];
         }
@@ -151,6 +161,7 @@ __device__ __forceinline__ void stage_rows(const In *__restrict__ tmpl, const ui
 // background x-power sums.
 template <class R, int LL>
 __device__ __forceinline__ void stage_coeffs(const Geometry &g, const R *__restrict__ cfold, int yb, R *cf, R *byp) {
+    using W = Win<R, LL>;
     constexpr int h = LL / 2;
     const int np = g.dk + 1, ny = g.ny;
     const int ncf = kBand * LL * np * LL;
@@ -160,12 +171,50 @@ __device__ __forceinline__ void stage_coeffs(const Geometry &g, const R *__restr
         rest /= np;
         int dyi = rest % LL, ry = rest / LL;
         int ys = wrapi(yb + ry - (dyi - h), ny);  // source row y - dy
-        cf[e] = cfold[(((size_t)ys * LL + dyi) * np + p) * LL + dxi];
+        cf[((ry * LL + dyi) * np + p) * W::LLP + dxi] = cfold[(((size_t)ys * LL + dyi) * np + p) * LL + dxi];
     }
     const R *bgf = cfold + (size_t)ny * LL * LL * np;
     for (int e = threadIdx.x; e < kBand * (g.db + 1); e += blockDim.x) {
         int ry = e / (g.db + 1), p = e % (g.db + 1);
         byp[e] = bgf[(size_t)min(yb + ry, ny - 1) * (g.db + 1) + p];
+    }
+}
+
+// window of one lane: wp[m] = row[c0 + m], m < NW (FP32: 16-byte loads; FP64: scalar)
+template <class R, int LL>
+__device__ __forceinline__ void load_window(const R *row, int c0, R (&wp)[Win<R, LL>::NW4 * 4]) {
+    using W = Win<R, LL>;
+    if constexpr (sizeof(R) == 4) {
+#pragma unroll
+        for (int k = 0; k < W::NW4; k++) {
+            const float4 v = *reinterpret_cast<const float4 *>(row + skew<R>(c0 + 4 * k));
+            wp[4 * k] = v.x;
+            wp[4 * k + 1] = v.y;
+            wp[4 * k + 2] = v.z;
+            wp[4 * k + 3] = v.w;
+        }
+    } else {
+#pragma unroll
+        for (int m = 0; m < W::NW; m++) wp[m] = row[skew<R>(c0 + m)];
+    }
+}
+
+// coefficients c[0 .. LL) of one (row, dy, p) triple (FP32: 16-byte loads of the padded row)
+template <class R, int LL>
+__device__ __forceinline__ void load_coeffs(const R *c, R (&cc)[Win<R, LL>::LLP]) {
+    using W = Win<R, LL>;
+    if constexpr (sizeof(R) == 4) {
+#pragma unroll
+        for (int k = 0; k < W::LLP / 4; k++) {
+            const float4 v = *reinterpret_cast<const float4 *>(c + 4 * k);
+            cc[4 * k] = v.x;
+            cc[4 * k + 1] = v.y;
+            cc[4 * k + 2] = v.z;
+            cc[4 * k + 3] = v.w;
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < LL; k++) cc[k] = c[k];
     }
 }
 
@@ -177,12 +226,12 @@ __global__ void __launch_bounds__(32 * kBand) k_subtract(const In *__restrict__ 
                                                         int rows_per_chunk, const R *__restrict__ cfold,
                                                         const R *__restrict__ xpow_g, In *__restrict__ diff) {
     using W = Win<R, LL>;
-    constexpr int h = W::h, kRX = Tile<R>::kRX, NW = W::NW;
+    constexpr int h = W::h, kRX = Tile<R>::kRX;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int np = g.dk + 1, nx = g.nx, ny = g.ny;
     R *Tp = reinterpret_cast<R *>(smem_raw);   // [np][RING][WCS]
-    R *cf = Tp + np * W::RING * W::WCS;         // [kBand][LL][np][LL]
-    R *byp = cf + kBand * LL * np * LL;         // [kBand][db+1]
+    R *cf = Tp + np * W::RING * W::WCS;         // [kBand][LL][np][LLP]
+    R *byp = cf + kBand * LL * np * W::LLP;     // [kBand][db+1]
     R *xps = byp + kBand * (g.db + 1);          // [npx][WC]
     const int npx = np > g.db + 1 ? np : g.db + 1;
 
@@ -219,13 +268,13 @@ __global__ void __launch_bounds__(32 * kBand) k_subtract(const In *__restrict__ 
             const int slot = (y + h - dyi - ring_origin) % W::RING;
             for (int p = 0; p < np; p++) {
                 const R *trow = Tp + (p * W::RING + slot) * W::WCS;
-                R wp[NW];
-#pragma unroll
-                for (int m = 0; m < NW; m++) wp[m] = trow[skew<R>(cx + m)];
-                const R *c = cf + ((ty * LL + dyi) * np + p) * LL;
+                R wp[W::NW4 * 4];
+                load_window<R, LL>(trow, cx, wp);
+                R ccs[W::LLP];
+                load_coeffs<R, LL>(cf + ((ty * LL + dyi) * np + p) * W::LLP, ccs);
 #pragma unroll
                 for (int dxi = 0; dxi < LL; dxi++) {
-                    const R cc = c[dxi];
+                    const R cc = ccs[dxi];
                     // source column x - dx -> window index r - dx + h = r + (LL - 1) - dxi
 #pragma unroll
                     for (int r = 0; r < kRX; r++) out[r] += cc * wp[r + (LL - 1) - dxi];
@@ -262,11 +311,13 @@ __global__ void __launch_bounds__(32 * kBand) k_subtract(const In *__restrict__ 
 // Residual of the fit for the FP32 path, R = S_m - sum a (w T_m)(u - d) - m sum b w, in
 // compensated arithmetic.  At a star core |S| is ~100x the residual, so plain FP32 sums
 // leave rounding errors of order u |S| in R; fitted back onto the basis by the refinement
-// step they bound the coefficients near 1e-6.  The terms that carry |S| are those near the
-// kernel centre, where both the kernel and the star's profile peak: for |dx|, |dy| <= kCore
-// every product is split exactly (p + e = c w, e from an FMA) and the running sum is a
-// hi + lo pair updated by an error-free two-sum (Knuth).  The outer lags, whose terms are
-// the product of two wings, accumulate in plain FP32 in a separate sum.  R then carries
+// step they bound the coefficients near 1e-6.  The terms that carry |S| are those of the
+// constant (x power 0) kernel plane near the kernel centre, where both the kernel and the
+// star's profile peak: for p = 0 and |dx|, |dy| <= kCore every product is split exactly
+// (p + e = c w, e from an FMA) and the running sum is a hi + lo pair updated by an
+// error-free two-sum (Knuth).  The outer lags, whose terms are the product of two wings, and
+// the xh^p planes (p >= 1, the kernel's spatial variation) accumulate in plain FP32 in a
+// separate sum.  R then carries
 // about the rounding of its operands (the folded coefficients and xh^p T_m, each rounded
 // once to FP32).  Each thread holds two output rows (ty, ty + kBand / 2) of a band as the
 // two lanes of packed FP32x2 operations.
@@ -300,14 +351,14 @@ __global__ void __launch_bounds__(16 * kBand, 2) k_residual_comp(const In *__res
                                                                  int rows_per_chunk, const float *__restrict__ cfold,
                                                                  const float *__restrict__ xpow_g,
                                                                  In *__restrict__ resid) {
-    using W = Win<float, LL>;
-    constexpr int h = W::h, kRX = Tile<float>::kRX, NW = W::NW;
+    using W = Win<float, LL, false>;
+    constexpr int h = W::h, kRX = Tile<float>::kRX;
     constexpr int kHalf = kBand / 2;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int np = g.dk + 1, nx = g.nx, ny = g.ny;
     float *Tp = reinterpret_cast<float *>(smem_raw);
     float *cf = Tp + np * W::RING * W::WCS;
-    float *byp = cf + kBand * LL * np * LL;
+    float *byp = cf + kBand * LL * np * W::LLP;
     float *xps = byp + kBand * (g.db + 1);
     const int npx = np > g.db + 1 ? np : g.db + 1;
 
@@ -320,7 +371,7 @@ __global__ void __launch_bounds__(16 * kBand, 2) k_residual_comp(const In *__res
 
     fill_xps<float, LL>(g, xpow_g, x0, npx, xps);
     __syncthreads();
-    stage_rows<float, In, LL>(tmpl, mask, true, g, xps, x0, yc0 - h, W::RING, ring_origin, Tp);
+    stage_rows<float, In, LL, false>(tmpl, mask, true, g, xps, x0, yc0 - h, W::RING, ring_origin, Tp);
     for (int yb = yc0; yb < yc1; yb += kBand) {
         stage_coeffs<float, LL>(g, cfold, yb, cf, byp);
         __syncthreads();
@@ -356,12 +407,14 @@ __global__ void __launch_bounds__(16 * kBand, 2) k_residual_comp(const In *__res
             const bool core_row = dyi >= h - kCore && dyi <= h + kCore;
             for (int p = 0; p < np; p++) {
                 const float *ta = Tp + (p * W::RING + sa) * W::WCS, *tb = Tp + (p * W::RING + sb) * W::WCS;
-                float2 wp[NW];
+                float2 wp[W::NW];
 #pragma unroll
-                for (int m = 0; m < NW; m++) wp[m] = make_float2(ta[skew<float>(cx + m)], tb[skew<float>(cx + m)]);
-                const float *ca = cf + ((ty * LL + dyi) * np + p) * LL;
-                const float *cb = cf + (((ty + kHalf) * LL + dyi) * np + p) * LL;
-                if (core_row) {
+                for (int m = 0; m < W::NW; m++)
+                    wp[m] = make_float2(ta[skew<float, false>(cx + m)], tb[skew<float, false>(cx + m)]);
+                float ca[W::LLP], cb[W::LLP];
+                load_coeffs<float, LL>(cf + ((ty * LL + dyi) * np + p) * W::LLP, ca);
+                load_coeffs<float, LL>(cf + (((ty + kHalf) * LL + dyi) * np + p) * W::LLP, cb);
+                if (core_row && p == 0) {
 #pragma unroll
                     for (int dxi = 0; dxi < LL; dxi++) {
                         const float2 cc = make_float2(ca[dxi], cb[dxi]);
@@ -401,7 +454,7 @@ __global__ void __launch_bounds__(16 * kBand, 2) k_residual_comp(const In *__res
         }
         __syncthreads();
         if (yb + kBand < yc1)
-            stage_rows<float, In, LL>(tmpl, mask, true, g, xps, x0, yb + kBand + h, kBand, ring_origin, Tp);
+            stage_rows<float, In, LL, false>(tmpl, mask, true, g, xps, x0, yb + kBand + h, kBand, ring_origin, Tp);
     }
 }
 
@@ -438,7 +491,8 @@ cudaError_t run(const Geometry &g, const void *sci, const void *tmpl, const uint
     if constexpr (std::is_same<R, float>::value) {
         if (residual) {
             auto kc = k_residual_comp<In, LL>;
-            cudaError_t e = cudaFuncSetAttribute(kc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            const size_t smc = stream_smem<float, LL, false>(np, g.db);
+            cudaError_t e = cudaFuncSetAttribute(kc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smc);
             if (e == cudaSuccess)
                 e = cudaFuncSetAttribute(kc, cudaFuncAttributePreferredSharedMemoryCarveout,
                                          cudaSharedmemCarveoutMaxShared);
@@ -446,7 +500,7 @@ cudaError_t run(const Geometry &g, const void *sci, const void *tmpl, const uint
             const int rpc = rows_per_chunk(g, strips, g.sub_per_sm > 0 ? g.sub_per_sm : 2);
             dim3 grid(strips, (g.ny + rpc - 1) / rpc);
             note_launch();
-            kc<<<grid, 16 * kBand, sm, st>>>((const In *)sci, (const In *)tmpl, mask, g, rpc, (const float *)cfold,
+            kc<<<grid, 16 * kBand, smc, st>>>((const In *)sci, (const In *)tmpl, mask, g, rpc, (const float *)cfold,
                                               (const float *)xpow, (In *)diff);
             return cudaGetLastError();
         }
