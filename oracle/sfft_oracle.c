@@ -119,7 +119,8 @@ static double *make_basis(int ny, int nx, const double *S, const double *T, cons
         for (int x = 0; x < nx; x++) {
             size_t u = (size_t)y * nx + x;
             double m = (mask && mask[u]) ? 0.0 : 1.0;
-            double tm = m * T[u], sm = m * S[u];
+            /* a masked pixel is zero in the fit whatever it holds (NaN included) */
+            double tm = m != 0.0 ? T[u] : 0.0, sm = m != 0.0 ? S[u] : 0.0;
             for (int i = 0; i < nk; i++) img[(size_t)i * np + u] = mono_at(i, y, x, ny, nx) * tm;
             for (int r = 0; r < nb; r++) img[(size_t)(nk + r) * np + u] = mono_at(r, y, x, ny, nx) * m;
             img[(size_t)(nk + nb) * np + u] = sm;
@@ -266,13 +267,13 @@ static double basis_value(int k, int y, int x, int ny, int nx, const double *S, 
         int i = k / ns, l = k % ns, dy = l / L - h, dx = l % L - h;
         int ys = wrap(y - dy, ny), xs = wrap(x - dx, nx);
         size_t u = (size_t)ys * nx + xs;
-        double m = (mask && mask[u]) ? 0.0 : 1.0;
-        return mono_at(i, ys, xs, ny, nx) * m * T[u];
+        if (mask && mask[u]) return 0.0;
+        return mono_at(i, ys, xs, ny, nx) * T[u];
     }
     size_t u = (size_t)y * nx + x;
-    double m = (mask && mask[u]) ? 0.0 : 1.0;
-    if (k < nker + oracle_npoly(db)) return mono_at(k - nker, y, x, ny, nx) * m;
-    return m * S[u];
+    if (mask && mask[u]) return 0.0;
+    if (k < nker + oracle_npoly(db)) return mono_at(k - nker, y, x, ny, nx);
+    return S[u];
 }
 
 /* N and b as explicit dot products of materialised basis images (tiny frames only). */

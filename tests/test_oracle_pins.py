@@ -268,3 +268,24 @@ def test_golden_hand_worked_example():
     assert np.allclose(D.ravel(), vals["D_L1_DK0_DB0"], rtol=0, atol=1e-13)
     th3 = oracle.fit(S, T, None, 1, 0, 0)
     assert np.allclose(th3, vals["theta_L1_DK0_DB0_nomask"], rtol=1e-14, atol=0)
+
+
+def test_masked_pixels_never_enter_the_fit_whatever_they_hold():
+    # the mask reading: masked pixels of S and T are zero in the fit, so NaN there changes nothing
+    S, T = synth.gaussian_pair(seed=3)[:2]
+    M = np.zeros(S.shape, np.uint8)
+    M[5, 7] = M[20, 31] = M[40, 2] = 1
+    Sz, Tz = S.copy(), T.copy()
+    Sz[M == 1] = 0.0
+    Tz[M == 1] = 0.0
+    Sn, Tn = S.copy(), T.copy()
+    Sn[5, 7] = np.nan
+    Tn[20, 31] = np.nan
+    Tn[40, 2] = np.inf
+    a = oracle.fit(Sz, Tz, M, 5, 1, 1)
+    b = oracle.fit(Sn, Tn, M, 5, 1, 1)
+    assert np.array_equal(a, b)
+    rows = np.arange(0, 26 * 3 + 3, 7)
+    ea = oracle.normal_entries(Sz, Tz, M, 5, 1, 1, rows, rows[::-1])
+    eb = oracle.normal_entries(Sn, Tn, M, 5, 1, 1, rows, rows[::-1])
+    assert np.array_equal(ea, eb)
