@@ -44,9 +44,10 @@ __global__ void __launch_bounds__(256) k_moments(const In *__restrict__ sci, con
     if (x < g.nx) {
         int cnt = 0;
         for (int y = ya; y < yb; y++) {
-            size_t u = (size_t)y * g.pitch + x;
-            R m = (mask && mask[u]) ? (R)0 : (R)1;
-            R sm = m * (R)sci[u];
+            const size_t u = (size_t)y * g.pitch + x;
+            const bool bad = mask && mask[u];
+            const R m = bad ? (R)0 : (R)1;
+            const R sm = bad ? (R)0 : (R)sci[u];  // a masked pixel never enters, whatever it holds
 #pragma unroll
             for (int b = 0; b <= 2 * kMaxDB; b++) {
                 if (b <= db2) {
@@ -164,21 +165,33 @@ __global__ void k_ysum(const double2 *__restrict__ ypart, Geometry g, bool pairs
     ysum[idx] = s;
 }
 
-// refinement pass: sum the W_i x S_m partials of every segment and row chunk into ysum
-__global__ void k_ysum_ws(const float4 *__restrict__ wspart, Geometry g, double2 *__restrict__ ysum) {
+// refinement pass: sum the W_i x S_m partials of every segment and row chunk into ysum;
+// one warp per output, the lanes take interleaved partials and a fixed shuffle tree adds
+// them (the same order on every run)
+__global__ void __launch_bounds__(256) k_ysum_ws(const float4 *__restrict__ wspart, Geometry g,
+                                                 double2 *__restrict__ ysum) {
     const int L = g.L;
-    size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;  // (k, i, c)
-    size_t per = (size_t)g.nkf * g.nk * L;
-    if (idx >= per) return;
-    const int c = (int)(idx % L), i = (int)((idx / L) % g.nk), k = (int)(idx / ((size_t)L * g.nk));
-    double2 s = make_double2(0.0, 0.0);
-    for (int sy = 0; sy < g.nseg * g.ychunks_ws; sy++) {
-        float4 v = wspart[(size_t)sy * per + idx];
-        s.x += (double)v.x + (double)v.z;
-        s.y += (double)v.y + (double)v.w;
+    const size_t idx = ((size_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;  // (k, i, c)
+    const int lane = threadIdx.x & 31;
+    const size_t per = (size_t)g.nkf * g.nk * L;
+    if (idx >= per) return;  // whole warps leave together
+    const int nsy = g.nseg * g.ychunks_ws;
+    double sx = 0.0, syv = 0.0;
+    for (int sy = lane; sy < nsy; sy += 32) {
+        const float4 v = wspart[(size_t)sy * per + idx];
+        sx += (double)v.x + (double)v.z;
+        syv += (double)v.y + (double)v.w;
     }
-    const int ent = g.npair * (2 * L - 1) + (i * (g.nb + 1) + g.nb) * L + c;
-    ysum[(size_t)k * g.nent + ent] = s;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        sx += __shfl_xor_sync(0xffffffffu, sx, o);
+        syv += __shfl_xor_sync(0xffffffffu, syv, o);
+    }
+    if (lane == 0) {
+        const int c = (int)(idx % L), i = (int)((idx / L) % g.nk), k = (int)(idx / ((size_t)L * g.nk));
+        const int ent = g.npair * (2 * L - 1) + (i * (g.nb + 1) + g.nb) * L + c;
+        ysum[(size_t)k * g.nent + ent] = make_double2(sx, syv);
+    }
 }
 
 __global__ void k_lagx(const double2 *__restrict__ ysum, const double2 *__restrict__ tw_x, Geometry g, bool ws_only,
@@ -296,8 +309,8 @@ cudaError_t launch_lag_tables(const Geometry &g, const double *ypart, double *ys
     size_t total = (size_t)g.nkf * g.nent;
     note_launch();
     if (ws_only && pairs) {
-        size_t per = (size_t)g.nkf * g.nk * g.L;
-        k_ysum_ws<<<(unsigned)((per + 255) / 256), 256, 0, st>>>((const float4 *)ypart, g, (double2 *)ysum);
+        size_t per = (size_t)g.nkf * g.nk * g.L;  // one warp each
+        k_ysum_ws<<<(unsigned)((per * 32 + 255) / 256), 256, 0, st>>>((const float4 *)ypart, g, (double2 *)ysum);
     } else {
         k_ysum<<<(unsigned)((total + 255) / 256), 256, 0, st>>>((const double2 *)ypart, g, pairs, (double2 *)ysum);
     }

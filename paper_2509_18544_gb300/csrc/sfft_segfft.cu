@@ -163,10 +163,11 @@ __global__ void __launch_bounds__(MAXT, MINB) k_segment_fft(const In *__restrict
         const int y = ybase + (q >> 8);
         if (y < yend) {
             const size_t u = (size_t)y * g.pitch + wcol[q & (kP - 1)];
-            R good = (mask && mask[u]) ? (R)0 : (R)1;
-            t_out = good * (R)tmpl[u];
-            s_out = good * (R)sci[u];
-            m_out = good;
+            const bool bad = mask && mask[u];
+            // selects, not products: a masked pixel never enters, whatever value it holds
+            t_out = bad ? (R)0 : (R)tmpl[u];
+            s_out = bad ? (R)0 : (R)sci[u];
+            m_out = bad ? (R)0 : (R)1;
         } else {
             t_out = s_out = m_out = (R)0;
         }
@@ -181,10 +182,10 @@ __global__ void __launch_bounds__(MAXT, MINB) k_segment_fft(const In *__restrict
     for (int q = tid + kMaxPf * nthr; q < npos; q += nthr) {  // only with fewer than 128 threads
         const int r = q >> 8, y = ybeg + r;
         const size_t u = (size_t)y * g.pitch + wrapi(x0 - G + (q & (kP - 1)), nx);
-        const R good = y < yend ? ((mask && mask[u]) ? (R)0 : (R)1) : (R)0;
-        tv[q] = y < yend ? good * (R)tmpl[u] : (R)0;
-        sv[q] = y < yend ? good * (R)sci[u] : (R)0;
-        mv[q] = good;
+        const bool use = y < yend && !(mask && mask[u]);
+        tv[q] = use ? (R)tmpl[u] : (R)0;
+        sv[q] = use ? (R)sci[u] : (R)0;
+        mv[q] = use ? (R)1 : (R)0;
     }
     __syncthreads();
 

@@ -89,6 +89,9 @@ template <class R, int LL, bool VEC = true> struct Win {
     static constexpr int NW4 = (NW + 3) / 4;                                                     // 16-byte loads of it
     static constexpr int LLP = (LL + 3) / 4 * 4;                                                 // coefficient row stride
     static_assert(NW4 * 4 >= NW && LLP >= LL, "window and coefficient rows cover their values");
+    // floats of the np template planes, rounded up to 16 bytes so that the coefficient rows
+    // after them can be read as 16-byte vectors
+    __host__ __device__ static constexpr int planes(int np) { return (np * RING * WCS + 3) & ~3; }
 };
 
 __device__ __forceinline__ int wrapi(int v, int n) {
@@ -101,7 +104,7 @@ template <class R, int LL, bool VEC = true>
 size_t stream_smem(int np, int db) {
     using W = Win<R, LL, VEC>;
     const int npx = np > db + 1 ? np : db + 1;
-    return sizeof(R) * ((size_t)np * W::RING * W::WCS + (size_t)kBand * LL * np * W::LLP + (size_t)kBand * (db + 1) +
+    return sizeof(R) * ((size_t)W::planes(np) + (size_t)kBand * LL * np * W::LLP + (size_t)kBand * (db + 1) +
                         (size_t)npx * W::WC);
 }
 
@@ -230,7 +233,7 @@ __global__ void __launch_bounds__(32 * kBand) k_subtract(const In *__restrict__ 
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int np = g.dk + 1, nx = g.nx, ny = g.ny;
     R *Tp = reinterpret_cast<R *>(smem_raw);   // [np][RING][WCS]
-    R *cf = Tp + np * W::RING * W::WCS;         // [kBand][LL][np][LLP]
+    R *cf = Tp + W::planes(np);                 // [kBand][LL][np][LLP], 16-byte aligned
     R *byp = cf + kBand * LL * np * W::LLP;     // [kBand][db+1]
     R *xps = byp + kBand * (g.db + 1);          // [npx][WC]
     const int npx = np > g.db + 1 ? np : g.db + 1;
@@ -291,8 +294,7 @@ __global__ void __launch_bounds__(32 * kBand) k_subtract(const In *__restrict__ 
                     for (int p = 0; p <= g.db; p++) bg += bp[p] * xps[p * W::WC + cx + r + h];
                     const size_t u = (size_t)y * g.pitch + x;
                     if (residual) {
-                        const R m = mv[r] ? (R)0 : (R)1;
-                        diff[u] = (In)(m * ((R)sv[r] - bg) - out[r]);
+                        diff[u] = (In)((mv[r] ? (R)0 : (R)sv[r] - bg) - out[r]);
                     } else {
                         diff[u] = (In)((R)sv[r] - out[r] - bg);
                     }
@@ -357,7 +359,7 @@ __global__ void __launch_bounds__(16 * kBand, 2) k_residual_comp(const In *__res
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int np = g.dk + 1, nx = g.nx, ny = g.ny;
     float *Tp = reinterpret_cast<float *>(smem_raw);
-    float *cf = Tp + np * W::RING * W::WCS;
+    float *cf = Tp + W::planes(np);  // 16-byte aligned
     float *byp = cf + kBand * LL * np * W::LLP;
     float *xps = byp + kBand * (g.db + 1);
     const int npx = np > g.db + 1 ? np : g.db + 1;

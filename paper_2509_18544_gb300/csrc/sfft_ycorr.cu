@@ -442,23 +442,30 @@ __global__ void __launch_bounds__(256) k_ycorr_ws(const cpx<float> *__restrict__
     }
     int y = ya;
     while (y < yb) {
+        // the block's loads first (C entering values of R and C values of W_i), so that they
+        // are all in flight together; rows past the chunk read as zero
+        float2 rin[C], av[C];
+#pragma unroll
+        for (int u = 0; u < C; u++) {
+            const bool ok = y + u < yb;
+            int yy = y + u + h;
+            yy = yy >= ny ? yy - ny : yy;
+            const cpx<float> v = ok ? base[(size_t)yy * rowstride + slot] : cpx<float>{0.f, 0.f};
+            const cpx<float> a = ok ? base[(size_t)(y + u) * rowstride + i] : cpx<float>{0.f, 0.f};
+            rin[u] = make_float2(v.re, v.im);
+            av[u] = make_float2(a.re, a.im);
+        }
 #pragma unroll
         for (int u = 0; u < C; u++) {
             // entering value R(y + h) goes to slot (C - 1 + u) % C; lag dy = c - h sits in slot (c + u) % C
-            if (y + u < yb) {
-                int yy = y + u + h;
-                yy = yy >= ny ? yy - ny : yy;
-                cpx<float> v = base[(size_t)yy * rowstride + slot];
-                w[(C - 1 + u) % C] = make_float2(v.re, v.im);
-                cpx<float> av = base[(size_t)(y + u) * rowstride + i];
+            w[(C - 1 + u) % C] = rin[u];
 #pragma unroll
-                for (int c = 0; c < C; c++) {
-                    const float2 b = w[(c + u) % C];
-                    acc[c].x = fmaf(av.re, b.x, acc[c].x);
-                    acc[c].x = fmaf(av.im, b.y, acc[c].x);
-                    acc[c].y = fmaf(av.re, b.y, acc[c].y);
-                    acc[c].y = fmaf(-av.im, b.x, acc[c].y);
-                }
+            for (int c = 0; c < C; c++) {
+                const float2 b = w[(c + u) % C];
+                acc[c].x = fmaf(av[u].x, b.x, acc[c].x);
+                acc[c].x = fmaf(av[u].y, b.y, acc[c].x);
+                acc[c].y = fmaf(av[u].x, b.y, acc[c].y);
+                acc[c].y = fmaf(-av[u].y, b.x, acc[c].y);
             }
         }
         // rotate so that slot 0 again holds R(y_next - h): the unrolled block advanced C rows,

@@ -255,3 +255,21 @@ def test_fp32_mode_without_refinement(ny, nx, L, dk, db, masked, dtype):
     assert info.status == 0
     assert np.linalg.norm(th - th_ref) <= 1e-4 * np.linalg.norm(th_ref)
     assert np.abs(D - D_ref).max() <= 1e-5 * np.abs(T).max()
+
+
+@pytest.mark.parametrize("precision", [sfft.PREC_SPLIT, sfft.PREC_FP64])
+def test_masked_pixels_never_enter_the_fit_whatever_they_hold(precision):
+    """NaN or Inf at masked pixels of S and T leaves the coefficients unchanged (bit for bit)
+    against zeros there: masked pixels are selected out, not multiplied by zero."""
+    S, T, M = _inputs(200, 230, True, np.float32, seed=21)
+    Sz, Tz = S.copy(), T.copy()
+    Sz[M == 1] = 0
+    Tz[M == 1] = 0
+    Sn, Tn = S.copy(), T.copy()
+    ys, xs = np.nonzero(M)
+    Sn[ys[::2], xs[::2]] = np.nan
+    Tn[ys[1::2], xs[1::2]] = np.inf
+    th_z, _, iz = gpu_fit_subtract(Sz, Tz, M, 5, 2, 1, precision=precision)
+    th_n, _, inn = gpu_fit_subtract(Sn, Tn, M, 5, 2, 1, precision=precision)
+    assert iz.status == 0 and inn.status == 0
+    assert np.array_equal(th_z, th_n)
