@@ -48,6 +48,12 @@ def parse():
     ap.add_argument("--frame", type=int, default=NY, help="frame side (smaller frames are for profiling runs)")
     ap.add_argument("--plain-only", action="store_true", help="time the plain form only (profiling runs)")
     ap.add_argument("--train-epochs", type=int, default=40)
+    ap.add_argument("--pcg-cluster", type=int, default=0, choices=[0, 8, 16],
+                    help="PCG cluster size for the batched form (0: the tuner's / largest available)")
+    ap.add_argument("--workload", default="roman4088", choices=["roman4088", "sxt48", "learned256"],
+                    help="roman4088: the headline line; sxt48: 8 x 6 science/template pairs of uneven "
+                         "cutout sizes, batched vs sequential; learned256: 256 batched 2048^2 pairs "
+                         "with and without the network's warm starts")
     return ap.parse_args()
 
 
@@ -231,6 +237,10 @@ def run_ours(args, world, rank, local):
     sfft.sfft_cnn_warm_start(cnn, stamps, args.pairs, n, x0)
     bpairs = [sfft.make_pair(S, T, M, th, D, NY, NX, x0=x0[k])
               for k, ((S, T, M), th, D) in enumerate(zip(dev_pairs, bcoeffs, bdiffs))]
+    if args.pcg_cluster:
+        tn = sfft.sfft_tuning()
+        tn.pcg_cluster = args.pcg_cluster
+        sfft.sfft_tuning_set(sfft.make_desc(NY, NX, L, DK, DB, solver=sfft.SOLVE_PCG), tn)
     t0 = time.perf_counter()
     batch = sfft.sfft_batch_create(sfft.make_desc(NY, NX, L, DK, DB, solver=sfft.SOLVE_PCG), bpairs,
                                    lanes=min(args.pairs, 4), flags=sfft.BATCH_GRAPH | sfft.BATCH_AUTOTUNE,
@@ -321,7 +331,8 @@ def run_ours(args, world, rank, local):
                     "fallbacks": sum(i.fallback for i in binfos)},
         "batch": {"create_s": round(create_s, 2),
                   "tuning": {"ycorr_bins": tuning.ycorr_bins, "ycorr_split": tuning.ycorr_split,
-                             "ycorr_scalar": tuning.ycorr_scalar, "subtract_ctas": tuning.subtract_ctas}},
+                             "ycorr_scalar": tuning.ycorr_scalar, "subtract_ctas": tuning.subtract_ctas,
+                             "pcg_cluster": tuning.pcg_cluster}},
         "roofline": roofline,
         "segment_fft_hbm": {"bound": "hbm", "achieved": round(seg_bytes / (seg_ms * 1e-3) / 1e9, 1),
                             "peak": hbm, "unit": "GB/s", "frac": round(seg_bytes / (seg_ms * 1e-3) / 1e9 / hbm, 4)},
@@ -391,11 +402,159 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
+# ----------------------------------------------------------------------------- other workloads
+def _timed_once(step, stream, reps=3):
+    import torch
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def run_sxt48(args):
+    """8 science x 6 template pairs, each a cutout of its own size from {512, 1024, 1536, 2048}^2
+    (L = 11, DK = 2, DB = 1): the whole batch as one graph over 4 lanes (autotuned, PCG) against
+    the 48 pairs fitted one after another on single plans (FP64 Cholesky)."""
+    import torch
+    from paper_2509_18544_gb300 import build as sfft_build
+    from paper_2509_18544_gb300 import sfft, synth
+    sfft_build.build()
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    n_sci, n_tmpl, Lk, dk, db = 8, 6, 11, 2, 1
+    sizes = synth.cutout_sizes(n_sci * n_tmpl, seed=2000)
+    pairs = [tuple(torch.from_numpy(a).to(dev) for a in synth.roman_pair(z, z, seed=2000 + k))
+             for k, z in enumerate(sizes)]
+    n = Lk * Lk * (dk + 1) * (dk + 2) // 2 + (db + 1) * (db + 2) // 2
+    th = [torch.empty(n, dtype=torch.float64, device=dev) for _ in pairs]
+    Ds = [torch.empty_like(p[0]) for p in pairs]
+    plans = {z: sfft.sfft_plan(sfft.make_desc(z, z, Lk, dk, db), stream=stream) for z in set(sizes)}
+
+    def plain_step():
+        for (S, T, M), z, t, D in zip(pairs, sizes, th, Ds):
+            sfft.sfft_fit(plans[z], S, T, M, None, t, want_info=False)
+            sfft.sfft_subtract(plans[z], S, T, t, D)
+
+    plain_step()
+    plain_ms = _timed_once(plain_step, stream, args.steps)
+    bth = [torch.empty(n, dtype=torch.float64, device=dev) for _ in pairs]
+    bD = [torch.empty_like(p[0]) for p in pairs]
+    bp = [sfft.make_pair(S, T, M, t, D, z, z) for (S, T, M), z, t, D in zip(pairs, sizes, bth, bD)]
+    t0 = time.perf_counter()
+    batch = sfft.sfft_batch_create(sfft.make_desc(512, 512, Lk, dk, db, solver=sfft.SOLVE_PCG), bp, lanes=4,
+                                   flags=sfft.BATCH_GRAPH | sfft.BATCH_AUTOTUNE, stream=stream)
+    create_s = time.perf_counter() - t0
+    for _ in range(args.warmup):
+        sfft.sfft_batch_run(batch)
+    ms = _timed_once(lambda: sfft.sfft_batch_run(batch), stream, args.steps)
+    infos = sfft.sfft_batch_info(batch)
+    worst = max(float(torch.linalg.norm(a - b) / torch.linalg.norm(b)) for a, b in zip(bth, th))
+    print(json.dumps({"metric": "S x T batch throughput (difference images/s)", "value": round(48 / (ms / 1e3), 2),
+                      "unit": "difference images/s", "workload": "sxt48: 8 x 6 pairs, cutouts %s px^2, L=11 DK=2 DB=1"
+                      % sorted(set(sizes)), "sizes": sizes, "batched_ms": round(ms, 2),
+                      "sequential_plain_ms": round(plain_ms, 2), "sequential_plain_value": round(48 / (plain_ms / 1e3), 2),
+                      "batched_over_sequential": round(plain_ms / ms, 3), "create_s": round(create_s, 2),
+                      "max_rel_coeff_diff_vs_sequential": worst,
+                      "statuses": sorted(set(i.status for i in infos)),
+                      "pcg_fallbacks": sum(i.fallback for i in infos)}), flush=True)
+    batch.close()
+    for p in plans.values():
+        p.close()
+
+
+def run_learned256(args):
+    """The warm-start network trained on `--train-samples` fits, driving PCG over a batch of
+    256 2048^2 pairs (16 distinct seeded pairs, each used 16 times), against the same batch
+    from cold starts and against sequential FP64-Cholesky fits."""
+    import numpy as np
+    import torch
+    from paper_2509_18544_gb300 import build as sfft_build
+    from paper_2509_18544_gb300 import learned, sfft, synth
+    sfft_build.build()
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    z, npairs, ndistinct = 2048, 256, 16
+    t0 = time.perf_counter()
+    st, tg, _ = learned.make_training_set(args.train_samples, seed=1000, size=256)
+    cnn, losses = learned.train(st, tg, epochs=args.train_epochs, batch=64, lr=1e-3, stream=stream)
+    train_s = time.perf_counter() - t0
+    del st, tg
+    data = [tuple(torch.from_numpy(a).to(dev) for a in synth.roman_pair(z, z, seed=4000 + k)) for k in range(ndistinct)]
+    n = L * L * (DK + 1) * (DK + 2) // 2 + (DB + 1) * (DB + 2) // 2
+    stamps = torch.from_numpy(np.repeat(synth.psf_stamps(synth.roman_field())[None], npairs, 0)).to(dev)
+    x0 = torch.zeros((npairs, n), dtype=torch.float64, device=dev)
+    sfft.sfft_cnn_warm_start(cnn, stamps[:64], 64, n, x0[:64])
+
+    def make(with_x0):
+        th = [torch.empty(n, dtype=torch.float64, device=dev) for _ in range(npairs)]
+        Ds = [torch.empty((z, z), dtype=torch.float32, device=dev) for _ in range(npairs)]
+        ps = [sfft.make_pair(*data[k % ndistinct], th[k], Ds[k], z, z, x0=x0[k] if with_x0 else None)
+              for k in range(npairs)]
+        b = sfft.sfft_batch_create(sfft.make_desc(z, z, L, DK, DB, solver=sfft.SOLVE_PCG), ps, lanes=8,
+                                   flags=sfft.BATCH_GRAPH | sfft.BATCH_AUTOTUNE, stream=stream)
+        return b, th
+
+    warm, th_w = make(True)
+    cold, th_c = make(False)
+
+    def warm_step():
+        for s0 in range(0, npairs, 64):
+            sfft.sfft_cnn_warm_start(cnn, stamps[s0:s0 + 64], 64, n, x0[s0:s0 + 64])
+        sfft.sfft_batch_run(warm)
+
+    for _ in range(args.warmup):
+        warm_step()
+        sfft.sfft_batch_run(cold)
+    warm_ms = _timed_once(warm_step, stream, args.steps)
+    cold_ms = _timed_once(lambda: sfft.sfft_batch_run(cold), stream, args.steps)
+    iw, ic = sfft.sfft_batch_info(warm), sfft.sfft_batch_info(cold)
+    # sequential FP64-Cholesky fits of the distinct pairs, scaled to the batch
+    with sfft.sfft_plan(sfft.make_desc(z, z, L, DK, DB), stream=stream) as plan:
+        thp = torch.empty(n, dtype=torch.float64, device=dev)
+        Dp = torch.empty((z, z), dtype=torch.float32, device=dev)
+
+        def plain_step():
+            for S, T, M in data:
+                sfft.sfft_fit(plan, S, T, M, None, thp, want_info=False)
+                sfft.sfft_subtract(plan, S, T, thp, Dp)
+
+        plain_step()
+        plain_ms = _timed_once(plain_step, stream, args.steps) * npairs / ndistinct
+        # the judge of the warm-started result: the FP64 Cholesky solution of pair 0
+        sfft.sfft_fit(plan, *data[0], None, thp)
+        ref = thp.clone()
+    err = float(torch.linalg.norm(th_w[0] - ref) / torch.linalg.norm(ref))
+    print(json.dumps({"metric": "2048^2 difference images/s, PCG batch with learned warm starts",
+                      "value": round(npairs / (warm_ms / 1e3), 2), "unit": "difference images/s",
+                      "workload": "learned256: 256 pairs of 2048^2 (16 distinct), L=11 DK=2 DB=2, 8 lanes, graph",
+                      "warm_ms": round(warm_ms, 2), "cold_ms": round(cold_ms, 2), "plain_sequential_ms": round(plain_ms, 2),
+                      "cold_value": round(npairs / (cold_ms / 1e3), 2), "plain_value": round(npairs / (plain_ms / 1e3), 2),
+                      "mean_iterations_warm": sum(i.iterations for i in iw) / npairs,
+                      "mean_iterations_cold": sum(i.iterations for i in ic) / npairs,
+                      "mean_start_residual_warm": sum(i.start_residual for i in iw) / npairs,
+                      "fallbacks_warm": sum(i.fallback for i in iw), "fallbacks_cold": sum(i.fallback for i in ic),
+                      "warm_vs_cholesky_rel": err, "train_samples": args.train_samples, "train_s": round(train_s, 1),
+                      "loss_first": losses[0], "loss_last": losses[-1]}), flush=True)
+    warm.close()
+    cold.close()
+    cnn.close()
+
+
 def main():
     args = parse()
     world, rank, local = dist_env()
     if args.impl == "reference":
         run_reference(args, world, rank)
+        return
+    if args.workload == "sxt48":
+        run_sxt48(args)
+        return
+    if args.workload == "learned256":
+        run_learned256(args)
         return
     run_ours(args, world, rank, local)
 

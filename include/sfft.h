@@ -188,7 +188,10 @@ typedef struct {
     int32_t ycorr_split;      /* y-correlation row chunks */
     int32_t ycorr_scalar;     /* 1: scalar FP32 y-correlation kernel, 0: packed FP32x2 */
     int32_t subtract_ctas;    /* subtract / residual CTAs per SM the grid is sized for (1 .. 4) */
-    int32_t reserved[4];
+    int32_t pcg_cluster;      /* CTAs in the PCG solver's cluster: 8 or 16 (0 = the largest the
+                                 device allows); a smaller cluster is easier to place among the
+                                 other lanes of a batch */
+    int32_t reserved[3];
 } sfft_tuning;
 /* The cached entry for desc (zeros and *cached = 0 when there is none). */
 sfft_status sfft_tuning_get(const sfft_desc *desc, sfft_tuning *t, int32_t *cached);

@@ -69,6 +69,9 @@ bool apply_tuning(const sfft_tuning &t, Geometry &g, char *err, size_t errlen) {
     if (t.subtract_ctas < 0 || t.subtract_ctas > 4)
         return snprintf(err, errlen, "subtract_ctas %d outside [0, 4]", t.subtract_ctas), false;
     g.sub_per_sm = t.subtract_ctas > 0 ? t.subtract_ctas : 2;
+    if (t.pcg_cluster != 0 && t.pcg_cluster != 8 && t.pcg_cluster != 16)
+        return snprintf(err, errlen, "pcg_cluster must be 0, 8 or 16"), false;
+    g.pcg_cluster = t.pcg_cluster;
     return true;
 }
 
@@ -220,13 +223,14 @@ sfft_status sfft_tuning_save(const char *path) {
     FILE *f = fopen(path, "w");
     if (!f) return errf("sfft_tuning_save: cannot open %s", path), SFFT_ERR_INVALID_ARG;
     std::lock_guard<std::mutex> lk(g_tune_mu);
-    fprintf(f, "# ny nx pitch L dk db dtype precision solver refine : ycorr_bins ycorr_split ycorr_scalar subtract_ctas\n");
+    fprintf(f, "# ny nx pitch L dk db dtype precision solver refine : ycorr_bins ycorr_split ycorr_scalar subtract_ctas "
+               "pcg_cluster\n");
     for (auto &kv : g_tune) {
         const Key &k = kv.first;
         const sfft_tuning &t = kv.second;
-        fprintf(f, "%d %d %d %d %d %d %d %d %d %d : %d %d %d %d\n", std::get<0>(k), std::get<1>(k), std::get<2>(k),
+        fprintf(f, "%d %d %d %d %d %d %d %d %d %d : %d %d %d %d %d\n", std::get<0>(k), std::get<1>(k), std::get<2>(k),
                 std::get<3>(k), std::get<4>(k), std::get<5>(k), std::get<6>(k), std::get<7>(k), std::get<8>(k),
-                std::get<9>(k), t.ycorr_bins, t.ycorr_split, t.ycorr_scalar, t.subtract_ctas);
+                std::get<9>(k), t.ycorr_bins, t.ycorr_split, t.ycorr_scalar, t.subtract_ctas, t.pcg_cluster);
     }
     const bool ok = fclose(f) == 0;
     return ok ? SFFT_OK : (errf("sfft_tuning_save: write failed"), SFFT_ERR_INVALID_ARG);
@@ -246,11 +250,11 @@ sfft_status sfft_tuning_load(const char *path) {
         memset(&d, 0, sizeof d);
         sfft_tuning t;
         memset(&t, 0, sizeof t);
-        int n = sscanf(line, "%d %d %d %d %d %d %d %d %d %d : %d %d %d %d", &d.ny, &d.nx, &d.pitch, &d.L, &d.dk, &d.db,
-                       &d.dtype, &d.precision, &d.solver, &d.refine, &t.ycorr_bins, &t.ycorr_split, &t.ycorr_scalar,
-                       &t.subtract_ctas);
-        if (n != 14) {
-            errf("sfft_tuning_load: %s:%d: expected 14 fields", path, lineno);
+        int n = sscanf(line, "%d %d %d %d %d %d %d %d %d %d : %d %d %d %d %d", &d.ny, &d.nx, &d.pitch, &d.L, &d.dk,
+                       &d.db, &d.dtype, &d.precision, &d.solver, &d.refine, &t.ycorr_bins, &t.ycorr_split,
+                       &t.ycorr_scalar, &t.subtract_ctas, &t.pcg_cluster);
+        if (n != 15) {
+            errf("sfft_tuning_load: %s:%d: expected 15 fields", path, lineno);
             result = SFFT_ERR_INVALID_ARG;
             break;
         }

@@ -61,6 +61,7 @@ struct Geometry {
     int kg_max;                // most y-correlation frequencies per CTA the thread and smem limits allow
     int ycorr_scalar;          // 1: scalar FP32 y-correlation kernel instead of packed FP32x2
     int sub_per_sm;            // subtract / residual CTAs per SM the grid is sized for
+    int pcg_cluster;           // PCG cluster size asked for (0: the largest available)
 };
 
 bool make_geometry(const sfft_desc &d, Geometry &g, char *err, size_t errlen);

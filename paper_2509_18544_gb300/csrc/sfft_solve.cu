@@ -345,8 +345,13 @@ cudaError_t launch_cholesky_solve(const Geometry &g, const double *N, const doub
     }
     SolveArgs A{N, b, R, x, r, z, scal, bar, status, n, 1, dinv, Rf, dinvf};
     void *params[] = {&A, (void *)&skip};
+    // As the fallback of PCG (skip != NULL) the factor usually returns at once, but a
+    // cooperative launch starts only when all its CTAs can be resident: one CTA per SM would
+    // wait for every other stream's kernels to drain.  16 CTAs keep it cheap to schedule;
+    // the tile loop runs with any grid, only a real fallback is slower.
+    const int grid = skip ? (g_coop_grid < 16 ? g_coop_grid : 16) : g_coop_grid;
     note_launch();
-    e = cudaLaunchCooperativeKernel((const void *)k_cholesky_factor, dim3(g_coop_grid), dim3(CT), params, 0, st);
+    e = cudaLaunchCooperativeKernel((const void *)k_cholesky_factor, dim3(grid), dim3(CT), params, 0, st);
     if (e != cudaSuccess) return e;
     // FP64 substitution, then one refinement step with the FP32 factor
     if ((e = sweeps<double>(R, dinv, n, b, x, false, status, skip, st)) != cudaSuccess) return e;

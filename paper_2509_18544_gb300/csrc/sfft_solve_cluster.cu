@@ -395,17 +395,23 @@ __global__ void __launch_bounds__(CTH) k_pcg_cluster(FastArgs A) {
             solve_small(gal, m, gco);
         }
         __syncthreads();
+        // x = alpha x0 + sum_r beta_r e_r; its residual r = b - N x from the products already
+        // at hand (N x = alpha N x0 + sum_r beta_r N e_r, the background columns of N), so
+        // the warm start costs one matrix-vector product, not two
         for (int i = rank * CTH + tid; i < n; i += CL * CTH) {
-            const int r = i - A.nker;
-            A.x[i] = gco[0] * A.x0[i] + (r >= 0 && r < m - 1 ? gco[1 + r] : 0.0);
+            const int rr = i - A.nker;
+            A.x[i] = gco[0] * A.x0[i] + (rr >= 0 && rr < m - 1 ? gco[1 + rr] : 0.0);
+            double nxi = gco[0] * __ldcg(A.q + i);
+            for (int k = 1; k < m; k++) nxi = fma(gco[k], A.N[(size_t)i * n + A.nker + k - 1], nxi);
+            A.r[i] = A.b[i] - nxi;
         }
     } else {
-        for (int i = rank * CTH + tid; i < n; i += CL * CTH) A.x[i] = 0.0;
+        // cold start: x = 0 and r = b, no product needed
+        for (int i = rank * CTH + tid; i < n; i += CL * CTH) {
+            A.x[i] = 0.0;
+            A.r[i] = A.b[i];
+        }
     }
-    cl.sync();
-    matvec(A.x, A.q);
-    cl.sync();
-    for (int i = rank * CTH + tid; i < n; i += CL * CTH) A.r[i] = A.b[i] - __ldcg(A.q + i);
     cl.sync();
     const double bb = dot(A.b, A.b);
     apply_M(A.r, A.z);
@@ -490,8 +496,9 @@ int pcg_cluster_size(const Geometry &g) {
         }
     }
     if (g_cluster == 0) return 0;
-    if (pcg_smem(ntiles, nblk, g_cluster) > 200 * 1024) return 0;  // factor does not fit: no fast path
-    return g_cluster;
+    const int CL = g.pcg_cluster > 0 && g.pcg_cluster < g_cluster ? g.pcg_cluster : g_cluster;
+    if (pcg_smem(ntiles, nblk, CL) > 200 * 1024) return 0;  // factor does not fit: no fast path
+    return CL;
 }
 
 size_t pcg_factor_floats(const Geometry &g) {

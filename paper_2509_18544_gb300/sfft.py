@@ -62,7 +62,7 @@ class sfft_pair(ctypes.Structure):
 class sfft_tuning(ctypes.Structure):
     _fields_ = [("ycorr_bins", ctypes.c_int32), ("ycorr_split", ctypes.c_int32),
                 ("ycorr_scalar", ctypes.c_int32), ("subtract_ctas", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 4)]
+                ("pcg_cluster", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
 
 
 BATCH_GRAPH, BATCH_AUTOTUNE = 1, 2

@@ -131,8 +131,8 @@ def test_autotune_stores_a_valid_shape_that_fits_correctly():
     t, ms = sfft.sfft_autotune(d, St, Tt, Mt, trials=2)
     got, cached = sfft.sfft_tuning_get(d)
     assert cached and ms > 0
-    assert (got.ycorr_bins, got.ycorr_split, got.ycorr_scalar, got.subtract_ctas) == \
-        (t.ycorr_bins, t.ycorr_split, t.ycorr_scalar, t.subtract_ctas)
+    assert (got.ycorr_bins, got.ycorr_split, got.ycorr_scalar, got.subtract_ctas, got.pcg_cluster) == \
+        (t.ycorr_bins, t.ycorr_split, t.ycorr_scalar, t.subtract_ctas, t.pcg_cluster)
     with sfft.sfft_plan(d) as p:
         th = torch.empty(p.n, dtype=torch.float64, device=DEV)
         sfft.sfft_fit(p, St, Tt, Mt, None, th)

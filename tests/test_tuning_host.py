@@ -12,42 +12,42 @@ def _lib():
     sfft.load_library()
 
 
-def _t(bins=0, split=0, scalar=0, ctas=0):
+def _t(bins=0, split=0, scalar=0, ctas=0, cluster=0):
     t = sfft.sfft_tuning()
-    t.ycorr_bins, t.ycorr_split, t.ycorr_scalar, t.subtract_ctas = bins, split, scalar, ctas
+    t.ycorr_bins, t.ycorr_split, t.ycorr_scalar, t.subtract_ctas, t.pcg_cluster = bins, split, scalar, ctas, cluster
     return t
 
 
 def _fields(t):
-    return (t.ycorr_bins, t.ycorr_split, t.ycorr_scalar, t.subtract_ctas)
+    return (t.ycorr_bins, t.ycorr_split, t.ycorr_scalar, t.subtract_ctas, t.pcg_cluster)
 
 
 def test_set_get_and_validation():
     d = sfft.make_desc(1000, 900, 11, 2, 2)
     t, cached = sfft.sfft_tuning_get(d)
-    assert not cached and _fields(t) == (0, 0, 0, 0)
-    sfft.sfft_tuning_set(d, _t(3, 3, 1, 3))
+    assert not cached and _fields(t) == (0, 0, 0, 0, 0)
+    sfft.sfft_tuning_set(d, _t(3, 3, 1, 3, 8))
     t, cached = sfft.sfft_tuning_get(d)
-    assert cached and _fields(t) == (3, 3, 1, 3)
+    assert cached and _fields(t) == (3, 3, 1, 3, 8)
     # entries are per descriptor
     assert not sfft.sfft_tuning_get(sfft.make_desc(1000, 900, 11, 2, 1))[1]
-    for bad in (_t(bins=10_000), _t(split=10_000), _t(scalar=2), _t(ctas=5), _t(bins=-1)):
+    for bad in (_t(bins=10_000), _t(split=10_000), _t(scalar=2), _t(ctas=5), _t(bins=-1), _t(cluster=4)):
         with pytest.raises(sfft.SfftError):
             sfft.sfft_tuning_set(d, bad)
-    assert _fields(sfft.sfft_tuning_get(d)[0]) == (3, 3, 1, 3)
+    assert _fields(sfft.sfft_tuning_get(d)[0]) == (3, 3, 1, 3, 8)
 
 
 def test_save_and_load_round_trip(tmp_path):
     d1 = sfft.make_desc(512, 512, 11, 2, 2)
     d2 = sfft.make_desc(2048, 1536, 7, 1, 1, solver=sfft.SOLVE_PCG)
     sfft.sfft_tuning_set(d1, _t(2, 1, 0, 1))
-    sfft.sfft_tuning_set(d2, _t(3, 4, 1, 2))
+    sfft.sfft_tuning_set(d2, _t(3, 4, 1, 2, 16))
     path = str(tmp_path / "tuning.txt")
     sfft.sfft_tuning_save(path)
     sfft.sfft_tuning_set(d1, _t(1, 1, 1, 4))
     sfft.sfft_tuning_load(path)
-    assert _fields(sfft.sfft_tuning_get(d1)[0]) == (2, 1, 0, 1)
-    assert _fields(sfft.sfft_tuning_get(d2)[0]) == (3, 4, 1, 2)
+    assert _fields(sfft.sfft_tuning_get(d1)[0]) == (2, 1, 0, 1, 0)
+    assert _fields(sfft.sfft_tuning_get(d2)[0]) == (3, 4, 1, 2, 16)
     bad = tmp_path / "bad.txt"
     bad.write_text("512 512 0 11 2 2 0 0 0 0 : 1 2\n")
     with pytest.raises(sfft.SfftError):
