@@ -264,28 +264,32 @@ def run_ours(args, world, rank, local):
     value = weak_value(args.steps, args.pairs, world, ms)
     binfos = sfft.sfft_batch_info(batch)
 
-    # ---- end to end through the public API with pinned host buffers (batched + learned)
-    host = [tuple(torch.from_numpy(a).pin_memory() for a in p) for p in pairs]
-    host_D = [torch.empty((NY, NX), dtype=torch.float32).pin_memory() for _ in pairs]
-    host_th = [torch.empty(n, dtype=torch.float64).pin_memory() for _ in pairs]
+    # ---- end to end through the public API with pinned host buffers (batched + learned): a
+    # second batch whose pairs carry their host buffers, so each lane copies its pair's inputs
+    # in before the fit and D and theta out after the subtraction, overlapping other lanes
+    host = [dict(sci=torch.from_numpy(S).pin_memory(), tmpl=torch.from_numpy(T).pin_memory(),
+                 mask=torch.from_numpy(M).pin_memory(), coeffs=torch.empty(n, dtype=torch.float64).pin_memory(),
+                 diff=torch.empty((NY, NX), dtype=torch.float32).pin_memory()) for S, T, M in pairs]
+    e2e_in = [tuple(torch.empty_like(t) for t in p) for p in dev_pairs]
+    e2e_th = [torch.empty(n, dtype=torch.float64, device=dev) for _ in pairs]
+    e2e_D = [torch.empty((NY, NX), dtype=torch.float32, device=dev) for _ in pairs]
+    e2e_pairs = [sfft.make_pair(dS, dT, dM, th, D, NY, NX, x0=x0[k], host=host[k])
+                 for k, ((dS, dT, dM), th, D) in enumerate(zip(e2e_in, e2e_th, e2e_D))]
+    e2e_batch = sfft.sfft_batch_create(sfft.make_desc(NY, NX, L, DK, DB, solver=sfft.SOLVE_PCG), e2e_pairs,
+                                       lanes=min(args.pairs, 4), flags=sfft.BATCH_GRAPH, stream=stream)
 
     def e2e_step():
-        for (hS, hT, hM), (dS, dT, dM) in zip(host, dev_pairs):
-            dS.copy_(hS, non_blocking=True)
-            dT.copy_(hT, non_blocking=True)
-            dM.copy_(hM, non_blocking=True)
-        batched_step()
-        for D, th, oD, oth in zip(bdiffs, bcoeffs, host_D, host_th):
-            oD.copy_(D, non_blocking=True)
-            oth.copy_(th, non_blocking=True)
+        sfft.sfft_cnn_warm_start(cnn, stamps, args.pairs, n, x0)
+        sfft.sfft_batch_run(e2e_batch)
 
     for _ in range(2):
         e2e_step()
     e2e_steps = max(2, args.steps // 2)
     e2e_ms = timed(e2e_step, e2e_steps, "e2e")
     e2e_value = weak_value(e2e_steps, args.pairs, world, e2e_ms)
-    h2d = args.pairs * sum(t.numel() * t.element_size() for t in host[0])
-    d2h = args.pairs * (host_D[0].numel() * 4 + n * 8)
+    h2d = args.pairs * sum(host[0][k].numel() * host[0][k].element_size() for k in ("sci", "tmpl", "mask"))
+    d2h = args.pairs * (host[0]["diff"].numel() * 4 + n * 8)
+    e2e_batch.close()
 
     # ---- roofline of the dominant kernel (y-direction lag correlation, ALU bound), from the
     # plain pass's per-stage events on the plan's stream

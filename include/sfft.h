@@ -155,6 +155,15 @@ typedef struct {
     int32_t ny, nx;           /* cutout size */
     int32_t pitch;            /* row pitch of the frames the cutouts lie in (elements; 0 = nx) */
     int32_t reserved;
+    /* Optional pinned host buffers (same pitch as the device ones).  With sci_host set, a run
+     * first copies sci_host, tmpl_host and (if both are set) mask_host into sci, tmpl and mask,
+     * and after the subtraction copies coeffs into coeffs_host and diff into diff_host (each
+     * when set).  The copies run on the pair's lane, so one pair's transfers overlap other
+     * pairs' work. */
+    const void *sci_host, *tmpl_host;
+    const uint8_t *mask_host;
+    double *coeffs_host;
+    void *diff_host;
 } sfft_pair;
 typedef struct sfft_batch_s *sfft_batch_t;
 enum {

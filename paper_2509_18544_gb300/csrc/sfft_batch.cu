@@ -153,6 +153,19 @@ cudaError_t queue_batch(sfft_batch_t b, sfft_status *st) {
             if (e != cudaSuccess) break;
             const sfft_pair &q = b->pairs[pi];
             sfft_plan_t p = b->plan_of[pi];
+            const size_t elt = b->base.dtype == SFFT_F64 ? 8 : 4;
+            const size_t pitch = q.pitch ? q.pitch : q.nx;
+            if (q.sci_host) {  // this pair's inputs, on its own lane
+                e = cudaMemcpy2DAsync(const_cast<void *>(q.sci), pitch * elt, q.sci_host, pitch * elt, q.nx * elt, q.ny,
+                                      cudaMemcpyHostToDevice, b->ls[l]);
+                if (e == cudaSuccess && q.tmpl_host)
+                    e = cudaMemcpy2DAsync(const_cast<void *>(q.tmpl), pitch * elt, q.tmpl_host, pitch * elt,
+                                          q.nx * elt, q.ny, cudaMemcpyHostToDevice, b->ls[l]);
+                if (e == cudaSuccess && q.mask && q.mask_host)
+                    e = cudaMemcpy2DAsync(const_cast<uint8_t *>(q.mask), pitch, q.mask_host, pitch, q.nx, q.ny,
+                                          cudaMemcpyHostToDevice, b->ls[l]);
+                if (e != cudaSuccess) break;
+            }
             sfft_status s = sfft_fit(p, q.sci, q.tmpl, q.mask, q.x0, q.coeffs, nullptr);
             if (s == SFFT_OK) s = sfft_subtract(p, q.sci, q.tmpl, q.coeffs, q.diff);
             if (s != SFFT_OK) {
@@ -160,6 +173,12 @@ cudaError_t queue_batch(sfft_batch_t b, sfft_status *st) {
                 e = cudaErrorUnknown;
                 break;
             }
+            if (q.coeffs_host)
+                e = cudaMemcpyAsync(q.coeffs_host, q.coeffs, sizeof(double) * p->g.n, cudaMemcpyDeviceToHost, b->ls[l]);
+            if (e == cudaSuccess && q.diff_host)
+                e = cudaMemcpy2DAsync(q.diff_host, pitch * elt, q.diff, pitch * elt, q.nx * elt, q.ny,
+                                      cudaMemcpyDeviceToHost, b->ls[l]);
+            if (e != cudaSuccess) break;
             // the pair's outcome: status word, solver flags and norms into its record
             double *r = b->rec + (size_t)pi * kRec;
             e = cudaMemcpyAsync(r, p->ws.status, sizeof(int), cudaMemcpyDeviceToDevice, b->ls[l]);

@@ -56,7 +56,9 @@ class sfft_pair(ctypes.Structure):
     _fields_ = [("sci", ctypes.c_void_p), ("tmpl", ctypes.c_void_p), ("mask", ctypes.c_void_p),
                 ("x0", ctypes.c_void_p), ("coeffs", ctypes.c_void_p), ("diff", ctypes.c_void_p),
                 ("ny", ctypes.c_int32), ("nx", ctypes.c_int32), ("pitch", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("reserved", ctypes.c_int32),
+                ("sci_host", ctypes.c_void_p), ("tmpl_host", ctypes.c_void_p), ("mask_host", ctypes.c_void_p),
+                ("coeffs_host", ctypes.c_void_p), ("diff_host", ctypes.c_void_p)]
 
 
 class sfft_tuning(ctypes.Structure):
@@ -247,11 +249,16 @@ def sfft_sync_status(plan: Plan):
     _check(load_library().sfft_sync_status(plan.handle), plan.handle)
 
 
-def make_pair(sci, tmpl, mask, coeffs, diff, ny, nx, pitch=0, x0=None) -> sfft_pair:
+def make_pair(sci, tmpl, mask, coeffs, diff, ny, nx, pitch=0, x0=None, host=None) -> sfft_pair:
+    """host: optional dict of pinned host tensors (sci, tmpl, mask, coeffs, diff) that a run
+    copies in before the fit and out after the subtraction."""
     q = sfft_pair()
     q.sci, q.tmpl, q.mask, q.x0 = _ptr(sci), _ptr(tmpl), _ptr(mask), _ptr(x0)
     q.coeffs, q.diff = _ptr(coeffs), _ptr(diff)
     q.ny, q.nx, q.pitch = ny, nx, pitch
+    if host:
+        q.sci_host, q.tmpl_host = _ptr(host.get("sci")), _ptr(host.get("tmpl"))
+        q.mask_host, q.coeffs_host, q.diff_host = _ptr(host.get("mask")), _ptr(host.get("coeffs")), _ptr(host.get("diff"))
     return q
 
 

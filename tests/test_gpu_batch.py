@@ -138,3 +138,31 @@ def test_autotune_stores_a_valid_shape_that_fits_correctly():
         sfft.sfft_fit(p, St, Tt, Mt, None, th)
     ref = oracle.fit(S, T, M, 11, 2, 2)
     assert np.linalg.norm(th.cpu().numpy() - ref) <= 1e-6 * np.linalg.norm(ref)
+
+
+def test_batch_with_host_buffers_copies_in_and_out_on_the_lanes():
+    """Pairs that carry pinned host buffers: each run copies the cutouts in (2-D copies with the
+    frames' pitch) and theta and D out; the host results equal single-pair device runs."""
+    cuts = _cutouts(SIZES[:4], seed=100)
+    n = oracle.n_unknowns(L, DK, DB)
+    pairs, refs = [], []
+    for k, c in enumerate(cuts):
+        refs.append(_single(c, n))
+        hs = {a: c[a].cpu().pin_memory() for a in ("S", "T", "M")}
+        dev = {a: torch.zeros_like(c[a]) for a in ("S", "T", "M")}      # the copies land here
+        th = torch.empty(n, dtype=torch.float64, device=DEV)
+        D = torch.empty((c["ny"], FRAME), dtype=torch.float32, device=DEV)
+        host = dict(sci=_view(hs["S"], c), tmpl=_view(hs["T"], c), mask=_view(hs["M"], c),
+                    coeffs=torch.full((n,), float("nan"), dtype=torch.float64).pin_memory(),
+                    diff=torch.full((c["ny"], FRAME), float("nan"), dtype=torch.float32).pin_memory())
+        c.update(host=host, keep=(hs, dev, th, D))
+        pairs.append(sfft.make_pair(_view(dev["S"], c), _view(dev["T"], c), _view(dev["M"], c), th, D,
+                                    c["ny"], c["nx"], pitch=FRAME, host=host))
+    with sfft.sfft_batch_create(sfft.make_desc(128, 128, L, DK, DB), pairs, lanes=2, flags=sfft.BATCH_GRAPH) as b:
+        for c in cuts:
+            c["host"]["coeffs"].fill_(float("nan"))
+        sfft.sfft_batch_run(b)
+        sfft.sfft_batch_info(b)
+    for c, (th, D) in zip(cuts, refs):
+        assert torch.equal(c["host"]["coeffs"], th.cpu())
+        assert torch.equal(c["host"]["diff"][:, :c["nx"]], D[:, :c["nx"]].cpu())
