@@ -151,6 +151,7 @@ static size_t carve(const Geometry &g, int precision, int dtype, void *base, Wor
         o.ypart = c.take<double>(base, 2 * (main_v > ws_v ? main_v : ws_v));
     }
     o.resid = g.refine ? c.take<char>(base, (size_t)g.ny * g.pitch * (dtype_size)) : nullptr;
+    o.rspec = g.refine && precision != SFFT_PREC_FP64 ? c.take<char>(base, (size_t)g.nseg * g.ny * g.nkf * cpx_sz) : nullptr;
     o.ysum = c.take<double>(base, (size_t)g.nkf * g.nent * 2);
     o.lagww = c.take<double>(base, (size_t)g.npair * (2 * g.L - 1) * (2 * g.L - 1));
     o.lagwg = c.take<double>(base, (size_t)g.nk * g.nb * g.L * g.L);
@@ -447,7 +448,7 @@ static sfft_status queue_normal(sfft_plan_t p, const void *sci, const void *tmpl
     if (e != cudaSuccess) return cuda_fail(p, e, "moments launch");
     {
         StageTimer t(p, ST_YCORR);
-        e = launch_ycorr(g, p->desc.precision, w.spec, w.ypart, false, st);
+        e = launch_ycorr(g, p->desc.precision, w.spec, w.ypart, false, nullptr, st);
     }
     if (e != cudaSuccess) return cuda_fail(p, e, "y-correlation launch");
     {
@@ -477,9 +478,9 @@ static cudaError_t queue_refine(sfft_plan_t p, const void *sci, const void *tmpl
     cudaError_t e = launch_subtract(g, p->desc.dtype, p->desc.precision, sci, tmpl, mask, true, coeffs, w.xpow,
                                     w.ypow, w.cfold, w.resid, st);
     if (e == cudaSuccess) e = launch_segment_fft_single(g, p->desc.dtype, p->desc.precision, w.resid, w.tw_fft, slot,
-                                                        w.spec, st);
+                                                        w.spec, w.rspec, st);
     if (e == cudaSuccess) e = launch_moments(g, p->desc.dtype, p->desc.precision, w.resid, mask, w.ypow, w.mom_part, st);
-    if (e == cudaSuccess) e = launch_ycorr(g, p->desc.precision, w.spec, w.ypart, true, st);
+    if (e == cudaSuccess) e = launch_ycorr(g, p->desc.precision, w.spec, w.ypart, true, w.rspec, st);
     if (e == cudaSuccess)
         e = launch_lag_tables(g, w.ypart, w.ysum, w.tw_x, w.lagww, w.lagwg, w.lagws, w.mom_part, w.mom, true,
                               p->desc.precision != SFFT_PREC_FP64, st);

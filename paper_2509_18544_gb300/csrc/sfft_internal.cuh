@@ -77,6 +77,7 @@ struct Workspace {
     void *spec = nullptr;        // [nseg][ny][nkf][nimg_pad] complex (R)
     double *ypart = nullptr;     // [nseg][ysplit][nkf][nent] complex FP64 (re, im interleaved)
     void *resid = nullptr;       // [ny][nx] residual image of the refinement pass (input dtype)
+    void *rspec = nullptr;       // FP32 path: [nseg][ny][nkf] complex spectrum of the residual (compact)
     double *ysum = nullptr;      // [nkf][nent] complex FP64
     double *lagww = nullptr;     // [npair][2L-1][2L-1]
     double *lagwg = nullptr;     // [nk][nb][L][L]
@@ -141,10 +142,10 @@ cudaError_t launch_moments(const Geometry &g, int dtype, int precision, const vo
                            const uint8_t *mask, const void *ypow, double *mom_part, cudaStream_t st);
 // K1 for one image (the refinement residual) written into image slot `slot` of spec
 cudaError_t launch_segment_fft_single(const Geometry &g, int dtype, int precision, const void *img,
-                                      const void *tw_fft, int slot, void *spec, cudaStream_t st);
+                                      const void *tw_fft, int slot, void *spec, void *rspec, cudaStream_t st);
 // K2: y-direction correlations at the kernel lags, per segment and frequency -> ypart
 // (ws_only: only the W x S_m items)
-cudaError_t launch_ycorr(const Geometry &g, int precision, const void *spec, double *ypart, bool ws_only,
+cudaError_t launch_ycorr(const Geometry &g, int precision, const void *spec, double *ypart, bool ws_only, const void *rspec,
                          cudaStream_t st);
 // K3: segment sum + x-direction inverse DFT at the kernel lags -> lag tables (ws_only: W x S_m only)
 cudaError_t launch_lag_tables(const Geometry &g, const double *ypart, double *ysum, const double *tw_x,

@@ -294,7 +294,7 @@ __global__ void __launch_bounds__(MAXT, MINB) k_segment_fft(const In *__restrict
 template <class R, class In>
 __global__ void __launch_bounds__(128) k_segment_fft_single(const In *__restrict__ img, Geometry g,
                                                            const cpx<R> *__restrict__ tw_g, int slot,
-                                                           cpx<R> *__restrict__ spec) {
+                                                           cpx<R> *__restrict__ spec, cpx<R> *__restrict__ rspec) {
     __shared__ cpx<R> tw[kP], twl[kP];
     __shared__ cpx<R> ex[8][kEx];
     const int G = g.G, nx = g.nx, ny = g.ny, NI = g.nimg_pad, nkf = g.nkf;
@@ -322,12 +322,14 @@ __global__ void __launch_bounds__(128) k_segment_fft_single(const In *__restrict
     for (int k2 = 0; k2 < 16; k2++) e[t + 16 * k2] = v[k2];
     __syncwarp(msk);
     if (act) {
+        // compact [segment][row][bin] buffer when given (coalesced), else the image slot
+        const size_t stride = rspec ? 1 : NI;
+        cpx<R> *o = rspec ? rspec : spec + slot;
         for (int k = t; k < nkf; k += 16) {
             cpx<R> zk = e[k], zc = e[(kP - k) & (kP - 1)];
-            spec[(((size_t)s * ny + y) * nkf + k) * NI + slot] = {(R)0.5 * (zk.re + zc.re), (R)0.5 * (zk.im - zc.im)};
+            o[(((size_t)s * ny + y) * nkf + k) * stride] = {(R)0.5 * (zk.re + zc.re), (R)0.5 * (zk.im - zc.im)};
             if (y + 1 < ny)
-                spec[(((size_t)s * ny + y + 1) * nkf + k) * NI + slot] = {(R)0.5 * (zk.im + zc.im),
-                                                                         (R)0.5 * (zc.re - zk.re)};
+                o[(((size_t)s * ny + y + 1) * nkf + k) * stride] = {(R)0.5 * (zk.im + zc.im), (R)0.5 * (zc.re - zk.re)};
         }
     }
 }
@@ -361,20 +363,20 @@ cudaError_t run(const Geometry &g, const void *sci, const void *tmpl, const uint
 }  // namespace
 
 cudaError_t launch_segment_fft_single(const Geometry &g, int dtype, int precision, const void *img, const void *tw_fft,
-                                      int slot, void *spec, cudaStream_t st) {
+                                      int slot, void *spec, void *rspec, cudaStream_t st) {
     if (g.P != kP) return cudaErrorInvalidValue;
     dim3 grid(g.nseg, (g.ny + 15) / 16);
     note_launch();
     if (precision == SFFT_PREC_FP64) {
         if (dtype == SFFT_F64)
-            k_segment_fft_single<double, double><<<grid, 128, 0, st>>>((const double *)img, g, (const cpx<double> *)tw_fft, slot, (cpx<double> *)spec);
+            k_segment_fft_single<double, double><<<grid, 128, 0, st>>>((const double *)img, g, (const cpx<double> *)tw_fft, slot, (cpx<double> *)spec, (cpx<double> *)rspec);
         else
-            k_segment_fft_single<double, float><<<grid, 128, 0, st>>>((const float *)img, g, (const cpx<double> *)tw_fft, slot, (cpx<double> *)spec);
+            k_segment_fft_single<double, float><<<grid, 128, 0, st>>>((const float *)img, g, (const cpx<double> *)tw_fft, slot, (cpx<double> *)spec, (cpx<double> *)rspec);
     } else {
         if (dtype == SFFT_F64)
-            k_segment_fft_single<float, double><<<grid, 128, 0, st>>>((const double *)img, g, (const cpx<float> *)tw_fft, slot, (cpx<float> *)spec);
+            k_segment_fft_single<float, double><<<grid, 128, 0, st>>>((const double *)img, g, (const cpx<float> *)tw_fft, slot, (cpx<float> *)spec, (cpx<float> *)rspec);
         else
-            k_segment_fft_single<float, float><<<grid, 128, 0, st>>>((const float *)img, g, (const cpx<float> *)tw_fft, slot, (cpx<float> *)spec);
+            k_segment_fft_single<float, float><<<grid, 128, 0, st>>>((const float *)img, g, (const cpx<float> *)tw_fft, slot, (cpx<float> *)spec, (cpx<float> *)rspec);
     }
     return cudaGetLastError();
 }

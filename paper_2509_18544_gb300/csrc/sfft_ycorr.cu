@@ -413,8 +413,8 @@ __global__ void __launch_bounds__(256) k_ycorr_f64(const cpx<double> *__restrict
 // window (the loop is unrolled by C so the rotation is free).  Output: (hi, lo) float pairs
 // per (segment, chunk, frequency, i, dy) -> wspart.
 template <int C>
-__global__ void __launch_bounds__(256) k_ycorr_ws(const cpx<float> *__restrict__ spec, Geometry g, int ychunks,
-                                                 float4 *__restrict__ wspart) {
+__global__ void __launch_bounds__(256) k_ycorr_ws(const cpx<float> *__restrict__ spec, const cpx<float> *__restrict__ rspec,
+                                                 Geometry g, int ychunks, float4 *__restrict__ wspart) {
     const int nk = g.nk, nkf = g.nkf, ny = g.ny, NI = g.nimg_pad, h = g.h;
     const int slot = 2 * nk + g.nb;
     const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -428,6 +428,7 @@ __global__ void __launch_bounds__(256) k_ycorr_ws(const cpx<float> *__restrict__
     const int ya = ych * chunk, yb = min(ny, ya + chunk);
     const size_t rowstride = (size_t)nkf * NI;  // complex values between consecutive rows
     const cpx<float> *base = spec + ((size_t)s * ny * nkf + k) * NI;
+    const cpx<float> *rbase = rspec + (size_t)s * ny * nkf + k;  // the residual, compact: row stride nkf
     float2 acc[C], hi[C], lo[C], w[C];
 #pragma unroll
     for (int c = 0; c < C; c++) {
@@ -437,7 +438,7 @@ __global__ void __launch_bounds__(256) k_ycorr_ws(const cpx<float> *__restrict__
 #pragma unroll
     for (int c = 0; c < C - 1; c++) {
         int yy = ((ya - h + c) % ny + ny) % ny;
-        cpx<float> v = base[(size_t)yy * rowstride + slot];
+        cpx<float> v = rbase[(size_t)yy * nkf];
         w[c] = make_float2(v.re, v.im);
     }
     int y = ya;
@@ -450,7 +451,7 @@ __global__ void __launch_bounds__(256) k_ycorr_ws(const cpx<float> *__restrict__
             const bool ok = y + u < yb;
             int yy = y + u + h;
             yy = yy >= ny ? yy - ny : yy;
-            const cpx<float> v = ok ? base[(size_t)yy * rowstride + slot] : cpx<float>{0.f, 0.f};
+            const cpx<float> v = ok ? rbase[(size_t)yy * nkf] : cpx<float>{0.f, 0.f};
             const cpx<float> a = ok ? base[(size_t)(y + u) * rowstride + i] : cpx<float>{0.f, 0.f};
             rin[u] = make_float2(v.re, v.im);
             av[u] = make_float2(a.re, a.im);
@@ -489,16 +490,18 @@ __global__ void __launch_bounds__(256) k_ycorr_ws(const cpx<float> *__restrict__
 }
 
 template <int C>
-cudaError_t run_ws(const Geometry &g, const void *spec, float4 *wspart, cudaStream_t st) {
+cudaError_t run_ws(const Geometry &g, const void *spec, const void *rspec, float4 *wspart, cudaStream_t st) {
     const long total = (long)g.nseg * g.ychunks_ws * g.nkf * g.nk;
     note_launch();
-    k_ycorr_ws<C><<<(unsigned)((total + 255) / 256), 256, 0, st>>>((const cpx<float> *)spec, g, g.ychunks_ws, wspart);
+    k_ycorr_ws<C><<<(unsigned)((total + 255) / 256), 256, 0, st>>>((const cpx<float> *)spec, (const cpx<float> *)rspec, g,
+                                                                  g.ychunks_ws, wspart);
     return cudaGetLastError();
 }
 
 template <int C>
-cudaError_t run(const Geometry &g, int precision, const void *spec, double *ypart, bool ws_only, cudaStream_t st) {
-    if (ws_only && precision != SFFT_PREC_FP64) return run_ws<C>(g, spec, reinterpret_cast<float4 *>(ypart), st);
+cudaError_t run(const Geometry &g, int precision, const void *spec, double *ypart, bool ws_only, const void *rspec,
+                cudaStream_t st) {
+    if (ws_only && precision != SFFT_PREC_FP64) return run_ws<C>(g, spec, rspec, reinterpret_cast<float4 *>(ypart), st);
     Launch ln;
     ln.ws_only = ws_only;
     ln.items = ws_only ? g.nk : g.items_per_k;
@@ -533,16 +536,16 @@ cudaError_t run(const Geometry &g, int precision, const void *spec, double *ypar
 }  // namespace
 
 cudaError_t launch_ycorr(const Geometry &g, int precision, const void *spec, double *ypart, bool ws_only,
-                         cudaStream_t st) {
+                         const void *rspec, cudaStream_t st) {
     switch (g.C) {
-        case 1: return run<1>(g, precision, spec, ypart, ws_only, st);
-        case 3: return run<3>(g, precision, spec, ypart, ws_only, st);
-        case 5: return run<5>(g, precision, spec, ypart, ws_only, st);
-        case 7: return run<7>(g, precision, spec, ypart, ws_only, st);
-        case 9: return run<9>(g, precision, spec, ypart, ws_only, st);
-        case 11: return run<11>(g, precision, spec, ypart, ws_only, st);
-        case 13: return run<13>(g, precision, spec, ypart, ws_only, st);
-        case 15: return run<15>(g, precision, spec, ypart, ws_only, st);
+        case 1: return run<1>(g, precision, spec, ypart, ws_only, rspec, st);
+        case 3: return run<3>(g, precision, spec, ypart, ws_only, rspec, st);
+        case 5: return run<5>(g, precision, spec, ypart, ws_only, rspec, st);
+        case 7: return run<7>(g, precision, spec, ypart, ws_only, rspec, st);
+        case 9: return run<9>(g, precision, spec, ypart, ws_only, rspec, st);
+        case 11: return run<11>(g, precision, spec, ypart, ws_only, rspec, st);
+        case 13: return run<13>(g, precision, spec, ypart, ws_only, rspec, st);
+        case 15: return run<15>(g, precision, spec, ypart, ws_only, rspec, st);
         default: return cudaErrorInvalidValue;
     }
 }
