@@ -156,7 +156,11 @@ static size_t carve(const Geometry &g, int precision, int dtype, void *base, Wor
     o.lagww = c.take<double>(base, (size_t)g.npair * (2 * g.L - 1) * (2 * g.L - 1));
     o.lagwg = c.take<double>(base, (size_t)g.nk * g.nb * g.L * g.L);
     o.lagws = c.take<double>(base, (size_t)g.nk * g.L * g.L);
-    o.mom_part = c.take<double>(base, (size_t)g.mom_ctas * g.nmom);
+    {
+        // moment partials: of the moments kernel, or of the FP32 refinement's residual kernel
+        const size_t a = (size_t)g.mom_ctas * g.nmom, r = (size_t)residual_ctas_max(g) * g.nb;
+        o.mom_part = c.take<double>(base, a > r ? a : r);
+    }
     o.mom = c.take<double>(base, (size_t)g.nmom);
     o.N = c.take<double>(base, (size_t)g.n * g.n);
     o.b = c.take<double>(base, (size_t)g.n);
@@ -475,15 +479,18 @@ static cudaError_t queue_refine(sfft_plan_t p, const void *sci, const void *tmpl
     Workspace &w = p->ws;
     cudaStream_t st = p->stream;
     const int slot = 2 * g.nk + g.nb;
+    // the FP32 path's residual kernel also sums the residual's background moments into mom
+    const bool fp32 = p->desc.precision != SFFT_PREC_FP64;
     cudaError_t e = launch_subtract(g, p->desc.dtype, p->desc.precision, sci, tmpl, mask, true, coeffs, w.xpow,
-                                    w.ypow, w.cfold, w.resid, st);
+                                    w.ypow, w.cfold, w.resid, fp32 ? w.mom_part : nullptr, fp32 ? w.mom : nullptr, st);
     if (e == cudaSuccess) e = launch_segment_fft_single(g, p->desc.dtype, p->desc.precision, w.resid, w.tw_fft, slot,
                                                         w.spec, w.rspec, st);
-    if (e == cudaSuccess) e = launch_moments(g, p->desc.dtype, p->desc.precision, w.resid, mask, w.ypow, w.mom_part, st);
+    if (e == cudaSuccess && !fp32)
+        e = launch_moments(g, p->desc.dtype, p->desc.precision, w.resid, mask, w.ypow, w.mom_part, st);
     if (e == cudaSuccess) e = launch_ycorr(g, p->desc.precision, w.spec, w.ypart, true, w.rspec, st);
     if (e == cudaSuccess)
-        e = launch_lag_tables(g, w.ypart, w.ysum, w.tw_x, w.lagww, w.lagwg, w.lagws, w.mom_part, w.mom, true,
-                              p->desc.precision != SFFT_PREC_FP64, st);
+        e = launch_lag_tables(g, w.ypart, w.ysum, w.tw_x, w.lagww, w.lagwg, w.lagws, fp32 ? nullptr : w.mom_part,
+                              w.mom, true, fp32, st);
     if (e == cudaSuccess) e = launch_refine_rhs(g, w.lagws, w.mom, w.q, st);
     // correction x += N^{-1} c: with the cluster factor when the fast solver converged, else
     // with the FP32 copy of the FP64 Cholesky factor (each launch checks the flag)
@@ -578,7 +585,7 @@ sfft_status sfft_subtract(sfft_plan_t plan, const void *sci, const void *tmpl, c
     {
         StageTimer t(plan, ST_SUBTRACT);
         e = launch_subtract(plan->g, plan->desc.dtype, plan->desc.precision, sci, tmpl, nullptr, false, coeffs,
-                            plan->ws.xpow, plan->ws.ypow, plan->ws.cfold, diff, plan->stream);
+                            plan->ws.xpow, plan->ws.ypow, plan->ws.cfold, diff, nullptr, nullptr, plan->stream);
     }
     if (e != cudaSuccess) return cuda_fail(plan, e, "subtract launch");
     return SFFT_OK;

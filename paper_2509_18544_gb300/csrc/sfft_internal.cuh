@@ -109,6 +109,10 @@ size_t workspace_bytes(const Geometry &g, int precision, int dtype);
 // process-wide count of kernel launches (every launcher calls this before each launch)
 void note_launch(int count = 1);
 uint64_t launch_count();
+// mom[j] = sum over p < nparts of part[p nmom + j], j < nmom (fixed order)
+cudaError_t launch_mom_reduce(const double *part, int nparts, int nmom, double *mom, cudaStream_t st);
+// largest number of CTAs the FP32 residual kernel can have (sizes its moment partials)
+int residual_ctas_max(const Geometry &g);
 
 enum Stage { ST_SEGFFT = 0, ST_MOMENTS, ST_YCORR, ST_LAGS, ST_ASSEMBLE, ST_SOLVE, ST_SUBTRACT, ST_REFINE, ST_COUNT };
 
@@ -177,6 +181,6 @@ cudaError_t launch_pcg_cluster(const Geometry &g, const double *N, const double 
 // masked frames: S_m - sum a (w T_m)(u - d) - m sum b w
 cudaError_t launch_subtract(const Geometry &g, int dtype, int precision, const void *sci,
                             const void *tmpl, const uint8_t *mask, bool residual, const double *coeffs,
-                            const void *xpow, const void *ypow, void *cfold, void *diff, cudaStream_t st);
+                            const void *xpow, const void *ypow, void *cfold, void *diff, double *mom_part, double *mom, cudaStream_t st);
 
 }  // namespace sfft

@@ -318,8 +318,16 @@ cudaError_t launch_lag_tables(const Geometry &g, const double *ypart, double *ys
     note_launch();
     k_lagx<<<(nout + 127) / 128, 128, 0, st>>>((const double2 *)ysum, (const double2 *)tw_x, g, ws_only, lagww,
                                                lagwg, lagws);
+    if (mom_part) {  // the refinement of the FP32 path reduces its moments elsewhere
+        note_launch();
+        k_mom_reduce<<<g.nmom, 256, 0, st>>>(mom_part, g.mom_ctas, g.nmom, mom);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mom_reduce(const double *part, int nparts, int nmom, double *mom, cudaStream_t st) {
     note_launch();
-    k_mom_reduce<<<g.nmom, 256, 0, st>>>(mom_part, g.mom_ctas, g.nmom, mom);
+    k_mom_reduce<<<nmom, 256, 0, st>>>(part, nparts, nmom, mom);
     return cudaGetLastError();
 }
 

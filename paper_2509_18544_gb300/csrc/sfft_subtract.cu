@@ -324,6 +324,8 @@ __global__ void __launch_bounds__(32 * kBand) k_subtract(const In *__restrict__ 
 // once to FP32).  Each thread holds two output rows (ty, ty + kBand / 2) of a band as the
 // two lanes of packed FP32x2 operations.
 constexpr int kCore = 2;
+constexpr int kMaxDB = 4;               // background degree the fused moments support
+constexpr int kMaxMom = (kMaxDB + 1) * (kMaxDB + 2) / 2;
 
 __device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
 
@@ -346,13 +348,16 @@ __device__ __forceinline__ void split_input<float>(float v, float &hi, float &lo
     lo = 0.f;
 }
 
+// With mom_part, the kernel also writes this CTA's part of the residual's background moments
+// sum_u m(u) w_r(u) R(u) (r < nP(DB), in the monomial order): FP32 sums over a thread's
+// pixels of a row, FP64 across rows and warps; mom_part[cta nP(DB) + r].
 template <class In, int LL>
 __global__ void __launch_bounds__(16 * kBand, 2) k_residual_comp(const In *__restrict__ sci,
                                                                  const In *__restrict__ tmpl,
                                                                  const uint8_t *__restrict__ mask, Geometry g,
                                                                  int rows_per_chunk, const float *__restrict__ cfold,
                                                                  const float *__restrict__ xpow_g,
-                                                                 In *__restrict__ resid) {
+                                                                 In *__restrict__ resid, double *__restrict__ mom_part) {
     using W = Win<float, LL, false>;
     constexpr int h = W::h, kRX = Tile<float>::kRX;
     constexpr int kHalf = kBand / 2;
@@ -366,10 +371,17 @@ __global__ void __launch_bounds__(16 * kBand, 2) k_residual_comp(const In *__res
 
     const int x0 = blockIdx.x * Tile<float>::kCols;
     const int yc0 = blockIdx.y * rows_per_chunk, yc1 = min(ny, yc0 + rows_per_chunk);
-    if (yc0 >= ny) return;
+    const int cta = blockIdx.y * gridDim.x + blockIdx.x;
+    __shared__ double macc[kBand / 2][kMaxMom];  // per warp: moment sums of its rows
+    if (yc0 >= ny) {
+        if (mom_part)
+            for (int j = threadIdx.x; j < g.nb; j += blockDim.x) mom_part[(size_t)cta * g.nb + j] = 0.0;
+        return;
+    }
     const int ring_origin = yc0 - h;
     const int ty = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int cx = lane * kRX;
+    for (int e = threadIdx.x; e < (kBand / 2) * kMaxMom; e += blockDim.x) (&macc[0][0])[e] = 0.0;
 
     fill_xps<float, LL>(g, xpow_g, x0, npx, xps);
     __syncthreads();
@@ -379,6 +391,7 @@ __global__ void __launch_bounds__(16 * kBand, 2) k_residual_comp(const In *__res
         __syncthreads();
         const int ya = yb + ty, yb2 = ya + kHalf;
         float2 hi[kRX], lo[kRX], wing[kRX];
+        unsigned good = 0;  // bit 2 r + k: pixel r of row k exists and is not masked
         // start from m (S - bg): S split exactly into hi + lo, the background subtracted by two-sum
 #pragma unroll
         for (int r = 0; r < kRX; r++) {
@@ -390,6 +403,7 @@ __global__ void __launch_bounds__(16 * kBand, 2) k_residual_comp(const In *__res
                 if (y < yc1 && x < nx) {
                     const size_t u = (size_t)y * g.pitch + x;
                     if (!(mask && mask[u])) {
+                        good |= 1u << (2 * r + k);
                         split_input<In>(sci[u], sh[k], sl[k]);
                         const float *bp = byp + (k ? ty + kHalf : ty) * (g.db + 1);
                         float b = 0.f;
@@ -446,18 +460,71 @@ __global__ void __launch_bounds__(16 * kBand, 2) k_residual_comp(const In *__res
                 }
             }
         }
+        float ma[kMaxDB + 1], mb[kMaxDB + 1];  // sum over this thread's pixels of m R xh^p, rows a, b
+#pragma unroll
+        for (int p = 0; p <= kMaxDB; p++) ma[p] = mb[p] = 0.f;
 #pragma unroll
         for (int r = 0; r < kRX; r++) {
             const int x = x0 + cx + r;
             if (x >= nx) continue;
-            if (ya < yc1) resid[(size_t)ya * g.pitch + x] = (In)((double)hi[r].x + ((double)lo[r].x - (double)wing[r].x));
-            if (yb2 < yc1)
-                resid[(size_t)yb2 * g.pitch + x] = (In)((double)hi[r].y + ((double)lo[r].y - (double)wing[r].y));
+            const double ra = (double)hi[r].x + ((double)lo[r].x - (double)wing[r].x);
+            const double rb = (double)hi[r].y + ((double)lo[r].y - (double)wing[r].y);
+            if (ya < yc1) resid[(size_t)ya * g.pitch + x] = (In)ra;
+            if (yb2 < yc1) resid[(size_t)yb2 * g.pitch + x] = (In)rb;
+            if (mom_part) {
+                const float fa = (good >> (2 * r)) & 1u ? (float)ra : 0.f;
+                const float fb = (good >> (2 * r + 1)) & 1u ? (float)rb : 0.f;
+#pragma unroll
+                for (int p = 0; p <= kMaxDB; p++) {
+                    if (p > g.db) break;
+                    const float xv = xps[p * W::WC + cx + r + h];
+                    ma[p] = fmaf(fa, xv, ma[p]);
+                    mb[p] = fmaf(fb, xv, mb[p]);
+                }
+            }
+        }
+        if (mom_part) {
+#pragma unroll
+            for (int p = 0; p <= kMaxDB; p++) {
+                if (p > g.db) break;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    ma[p] += __shfl_xor_sync(0xffffffffu, ma[p], o);
+                    mb[p] += __shfl_xor_sync(0xffffffffu, mb[p], o);
+                }
+            }
+            if (lane == 0) {
+                const double yha = ny > 1 ? (2.0 * ya - (ny - 1)) / (double)(ny - 1) : 0.0;
+                const double yhb = ny > 1 ? (2.0 * yb2 - (ny - 1)) / (double)(ny - 1) : 0.0;
+                for (int j = 0; j < g.nb; j++) {
+                    int pr, qs;
+                    mono_pq(j, pr, qs);
+                    double wa = 1.0, wb = 1.0;
+                    for (int q = 0; q < qs; q++) wa *= yha, wb *= yhb;
+                    float va = 0.f, vb = 0.f;
+#pragma unroll
+                    for (int p = 0; p <= kMaxDB; p++)
+                        if (p == pr) va = ma[p], vb = mb[p];
+                    macc[ty][j] += wa * (double)va + wb * (double)vb;
+                }
+            }
         }
         __syncthreads();
         if (yb + kBand < yc1)
             stage_rows<float, In, LL, false>(tmpl, mask, true, g, xps, x0, yb + kBand + h, kBand, ring_origin, Tp);
     }
+    if (mom_part) {
+        __syncthreads();
+        for (int j = threadIdx.x; j < g.nb; j += blockDim.x) {
+            double v = 0.0;
+            for (int w = 0; w < kBand / 2; w++) v += macc[w][j];
+            mom_part[(size_t)cta * g.nb + j] = v;
+        }
+    }
+}
+
+int residual_ctas_max_impl(const Geometry &g) {
+    return ((g.nx + Tile<float>::kCols - 1) / Tile<float>::kCols) * ((g.ny + kBand - 1) / kBand);
 }
 
 int sm_count() {
@@ -481,7 +548,8 @@ int rows_per_chunk(const Geometry &g, int strips, int per_sm) {
 
 template <class R, class In, int LL>
 cudaError_t run(const Geometry &g, const void *sci, const void *tmpl, const uint8_t *mask, bool residual,
-                const double *coeffs, const void *xpow, void *cfold, void *diff, cudaStream_t st) {
+                const double *coeffs, const void *xpow, void *cfold, void *diff, double *mom_part, double *mom,
+                cudaStream_t st) {
     {
         size_t nt = (size_t)g.ny * LL * LL + g.ny;
         note_launch();
@@ -503,8 +571,12 @@ cudaError_t run(const Geometry &g, const void *sci, const void *tmpl, const uint
             dim3 grid(strips, (g.ny + rpc - 1) / rpc);
             note_launch();
             kc<<<grid, 16 * kBand, smc, st>>>((const In *)sci, (const In *)tmpl, mask, g, rpc, (const float *)cfold,
-                                              (const float *)xpow, (In *)diff);
-            return cudaGetLastError();
+                                              (const float *)xpow, (In *)diff, mom ? mom_part : nullptr);
+            e = cudaGetLastError();
+            // the residual's background moments go after the npoly(2 DB) mask moments
+            if (e == cudaSuccess && mom)
+                e = launch_mom_reduce(mom_part, (int)(grid.x * grid.y), g.nb, mom + npoly(2 * g.db), st);
+            return e;
         }
     }
     auto kern = k_subtract<R, In, LL>;
@@ -522,32 +594,36 @@ cudaError_t run(const Geometry &g, const void *sci, const void *tmpl, const uint
 
 template <class R, class In>
 cudaError_t dispatch_L(const Geometry &g, const void *sci, const void *tmpl, const uint8_t *mask, bool residual,
-                       const double *coeffs, const void *xpow, void *cfold, void *diff, cudaStream_t st) {
+                       const double *coeffs, const void *xpow, void *cfold, void *diff, double *mom_part, double *mom,
+                       cudaStream_t st) {
     switch (g.L) {
-        case 1: return run<R, In, 1>(g, sci, tmpl, mask, residual, coeffs, xpow, cfold, diff, st);
-        case 3: return run<R, In, 3>(g, sci, tmpl, mask, residual, coeffs, xpow, cfold, diff, st);
-        case 5: return run<R, In, 5>(g, sci, tmpl, mask, residual, coeffs, xpow, cfold, diff, st);
-        case 7: return run<R, In, 7>(g, sci, tmpl, mask, residual, coeffs, xpow, cfold, diff, st);
-        case 9: return run<R, In, 9>(g, sci, tmpl, mask, residual, coeffs, xpow, cfold, diff, st);
-        case 11: return run<R, In, 11>(g, sci, tmpl, mask, residual, coeffs, xpow, cfold, diff, st);
-        case 13: return run<R, In, 13>(g, sci, tmpl, mask, residual, coeffs, xpow, cfold, diff, st);
-        case 15: return run<R, In, 15>(g, sci, tmpl, mask, residual, coeffs, xpow, cfold, diff, st);
+        case 1: return run<R, In, 1>(g, sci, tmpl, mask, residual, coeffs, xpow, cfold, diff, mom_part, mom, st);
+        case 3: return run<R, In, 3>(g, sci, tmpl, mask, residual, coeffs, xpow, cfold, diff, mom_part, mom, st);
+        case 5: return run<R, In, 5>(g, sci, tmpl, mask, residual, coeffs, xpow, cfold, diff, mom_part, mom, st);
+        case 7: return run<R, In, 7>(g, sci, tmpl, mask, residual, coeffs, xpow, cfold, diff, mom_part, mom, st);
+        case 9: return run<R, In, 9>(g, sci, tmpl, mask, residual, coeffs, xpow, cfold, diff, mom_part, mom, st);
+        case 11: return run<R, In, 11>(g, sci, tmpl, mask, residual, coeffs, xpow, cfold, diff, mom_part, mom, st);
+        case 13: return run<R, In, 13>(g, sci, tmpl, mask, residual, coeffs, xpow, cfold, diff, mom_part, mom, st);
+        case 15: return run<R, In, 15>(g, sci, tmpl, mask, residual, coeffs, xpow, cfold, diff, mom_part, mom, st);
         default: return cudaErrorInvalidValue;
     }
 }
 
 }  // namespace
 
+int residual_ctas_max(const Geometry &g) { return residual_ctas_max_impl(g); }
+
 cudaError_t launch_subtract(const Geometry &g, int dtype, int precision, const void *sci, const void *tmpl,
                             const uint8_t *mask, bool residual, const double *coeffs, const void *xpow,
-                            const void *ypow, void *cfold, void *diff, cudaStream_t st) {
+                            const void *ypow, void *cfold, void *diff, double *mom_part, double *mom,
+                            cudaStream_t st) {
     (void)ypow;
     if (g.dk > 7 || g.db > 7) return cudaErrorInvalidValue;
     if (precision == SFFT_PREC_FP64)
-        return dtype == SFFT_F64 ? dispatch_L<double, double>(g, sci, tmpl, mask, residual, coeffs, xpow, cfold, diff, st)
-                                 : dispatch_L<double, float>(g, sci, tmpl, mask, residual, coeffs, xpow, cfold, diff, st);
-    return dtype == SFFT_F64 ? dispatch_L<float, double>(g, sci, tmpl, mask, residual, coeffs, xpow, cfold, diff, st)
-                             : dispatch_L<float, float>(g, sci, tmpl, mask, residual, coeffs, xpow, cfold, diff, st);
+        return dtype == SFFT_F64 ? dispatch_L<double, double>(g, sci, tmpl, mask, residual, coeffs, xpow, cfold, diff, mom_part, mom, st)
+                                 : dispatch_L<double, float>(g, sci, tmpl, mask, residual, coeffs, xpow, cfold, diff, mom_part, mom, st);
+    return dtype == SFFT_F64 ? dispatch_L<float, double>(g, sci, tmpl, mask, residual, coeffs, xpow, cfold, diff, mom_part, mom, st)
+                             : dispatch_L<float, float>(g, sci, tmpl, mask, residual, coeffs, xpow, cfold, diff, mom_part, mom, st);
 }
 
 }  // namespace sfft
@@ -658,11 +734,11 @@ extern "C" sfft_status sfft_subtract_noalloc(const sfft_desc *desc, const void *
     e = cudaGetLastError();
     if (e == cudaSuccess) {
         if (desc->precision == SFFT_PREC_FP64)
-            e = desc->dtype == SFFT_F64 ? dispatch_L<double, double>(g, sci, tmpl, nullptr, false, coeffs, xpow, cfold, diff, st)
-                                        : dispatch_L<double, float>(g, sci, tmpl, nullptr, false, coeffs, xpow, cfold, diff, st);
+            e = desc->dtype == SFFT_F64 ? dispatch_L<double, double>(g, sci, tmpl, nullptr, false, coeffs, xpow, cfold, diff, nullptr, nullptr, st)
+                                        : dispatch_L<double, float>(g, sci, tmpl, nullptr, false, coeffs, xpow, cfold, diff, nullptr, nullptr, st);
         else
-            e = desc->dtype == SFFT_F64 ? dispatch_L<float, double>(g, sci, tmpl, nullptr, false, coeffs, xpow, cfold, diff, st)
-                                        : dispatch_L<float, float>(g, sci, tmpl, nullptr, false, coeffs, xpow, cfold, diff, st);
+            e = desc->dtype == SFFT_F64 ? dispatch_L<float, double>(g, sci, tmpl, nullptr, false, coeffs, xpow, cfold, diff, nullptr, nullptr, st)
+                                        : dispatch_L<float, float>(g, sci, tmpl, nullptr, false, coeffs, xpow, cfold, diff, nullptr, nullptr, st);
     }
     if (e != cudaSuccess) {
         snprintf(err, sizeof err, "sfft_subtract_noalloc: %s", cudaGetErrorString(e));
