@@ -76,7 +76,7 @@ template <class R> struct Tile {
 // (VEC = false: FP32 windows read as scalars, one pad word every 8 floats, for kernels that
 // pack two rows' values into FP32x2 operands.)
 template <class R, bool VEC = true>
-__device__ __forceinline__ int skew(int c) {
+__host__ __device__ constexpr int skew(int c) {
     return sizeof(R) == 4 ? (VEC ? c + 4 * (c >> 5) : c + (c >> 3)) : c + (c >> 2);
 }
 template <class R, int LL, bool VEC = true> struct Win {
@@ -100,13 +100,48 @@ __device__ __forceinline__ int wrapi(int v, int n) {
     return v < 0 ? v + n : v;
 }
 
-template <class R, int LL, bool VEC = true>
-size_t stream_smem(int np, int db) {
+// Shared memory of the streaming kernels (byte offsets, each region on 16 bytes):
+//   Tp   [np][RING][WCS] R      the template ring, as np planes xh^p T
+//   cf   [kBand][LL][np][LLP] R the band's folded coefficients
+//   xo   [db+1][OC] R           xh^p of the strip's output columns
+//   ss   [kBand][OC] In         science values of the band's output rows
+//   sk   [RING][kCols] bytes    per ring row: 1 where the output column's pixel is masked
+//   byp  [kBand][db+1] R        the band's background x-power sums
+//   xps  [npx][WC] R            xh^p of the window columns
+// Output-side rows use the kernel's skewed column index, so that a lane's run of kRX
+// consecutive columns is read without bank conflicts.
+template <class R, class In, int LL, bool VEC = true> struct Layout {
     using W = Win<R, LL, VEC>;
-    const int npx = np > db + 1 ? np : db + 1;
-    return sizeof(R) * ((size_t)W::planes(np) + (size_t)kBand * LL * np * W::LLP + (size_t)kBand * (db + 1) +
-                        (size_t)npx * W::WC);
+    static constexpr int kC = Tile<R>::kCols;
+    static constexpr int OC = (skew<R, VEC>(kC - 1) + 4) & ~3;
+    __host__ __device__ static constexpr size_t al(size_t b) { return (b + 15) & ~(size_t)15; }
+    __host__ __device__ static constexpr size_t cf(int np) { return al(sizeof(R) * (size_t)W::planes(np)); }
+    __host__ __device__ static constexpr size_t xo(int np) {
+        return al(cf(np) + sizeof(R) * (size_t)kBand * LL * np * W::LLP);
+    }
+    __host__ __device__ static constexpr size_t ss(int np, int db) { return al(xo(np) + sizeof(R) * (size_t)(db + 1) * OC); }
+    __host__ __device__ static constexpr size_t sk(int np, int db) { return al(ss(np, db) + sizeof(In) * (size_t)kBand * OC); }
+    __host__ __device__ static constexpr size_t byp(int np, int db) { return al(sk(np, db) + (size_t)W::RING * kC); }
+    __host__ __device__ static constexpr size_t xps(int np, int db) {
+        return al(byp(np, db) + sizeof(R) * (size_t)kBand * (db + 1));
+    }
+    static size_t bytes(int np, int db) {
+        const int npx = np > db + 1 ? np : db + 1;
+        return xps(np, db) + sizeof(R) * (size_t)npx * W::WC;
+    }
+};
+
+// one 4- or 8-byte element, global to shared, asynchronously (completed by cp_async_wait)
+template <class T>
+__device__ __forceinline__ void cp_async_elem(T *smem, const T *gmem) {
+    static_assert(sizeof(T) == 4 || sizeof(T) == 8, "4- or 8-byte elements");
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    if constexpr (sizeof(T) == 4)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
 }
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
 // xh^p of the strip's window columns (x0 - h ..), p < npx: xps[p][c]
 template <class R, int LL>
@@ -118,16 +153,78 @@ __device__ __forceinline__ void fill_xps(const Geometry &g, const R *__restrict_
     }
 }
 
+// v = hi + lo exactly (FP64 inputs), or hi = v (FP32)
+template <class In>
+__device__ __forceinline__ void split_input(In v, float &hi, float &lo) {
+    hi = (float)v;
+    lo = (float)((double)v - (double)hi);
+}
+template <>
+__device__ __forceinline__ void split_input<float>(float v, float &hi, float &lo) {
+    hi = v;
+    lo = 0.f;
+}
+
+// xh^p of the strip's output columns, p <= db: xo[p][skew(c)]
+template <class R, int LL, bool VEC>
+__device__ __forceinline__ void fill_xo(const Geometry &g, const R *__restrict__ xpow_g, int x0, R *xo) {
+    using Ly = Layout<R, R, LL, VEC>;
+    for (int e = threadIdx.x; e < (g.db + 1) * Ly::kC; e += blockDim.x) {
+        const int p = e / Ly::kC, c = e % Ly::kC;
+        xo[p * Ly::OC + skew<R, VEC>(c)] = xpow_g[(size_t)p * g.nx + min(x0 + c, g.nx - 1)];
+    }
+}
+
+// Science values of output rows yb .. yb + kBand - 1 (rows before yc1, columns inside the
+// frame), copied asynchronously: ss[r][skew(c)].
+template <class R, class In, int LL, bool VEC>
+__device__ __forceinline__ void async_sci(const In *__restrict__ sci, const Geometry &g, int x0, int yb, int yc1,
+                                          In *ss) {
+    using Ly = Layout<R, In, LL, VEC>;
+    constexpr int total = kBand * Ly::kC;
+    for (int e = threadIdx.x; e < total; e += blockDim.x) {
+        const int r = e / Ly::kC, c = e % Ly::kC, y = yb + r, x = x0 + c;
+        if (y < yc1 && x < g.nx) cp_async_elem(ss + r * Ly::OC + skew<R, VEC>(c), sci + (size_t)y * g.pitch + x);
+    }
+}
+
+// n consecutive values starting at p (with VEC and FP32 values, 16-byte loads: the caller
+// guarantees that p is on 16 bytes)
+template <class R, int N, bool VEC>
+__device__ __forceinline__ void load_run(const R *p, R (&v)[N]) {
+    if constexpr (sizeof(R) == 4 && VEC && N % 4 == 0) {
+#pragma unroll
+        for (int k = 0; k < N / 4; k++) {
+            const float4 q = *reinterpret_cast<const float4 *>(p + 4 * k);
+            v[4 * k] = q.x;
+            v[4 * k + 1] = q.y;
+            v[4 * k + 2] = q.z;
+            v[4 * k + 3] = q.w;
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < N; k++) v[k] = p[k];
+    }
+}
+
+// the skip flags of a lane's kRX consecutive pixels, one byte each
+template <int N>
+__device__ __forceinline__ unsigned long long load_flags(const unsigned char *p) {
+    static_assert(N == 4 || N == 8, "runs of 4 or 8 pixels");
+    if constexpr (N == 8) return *reinterpret_cast<const unsigned long long *>(p);
+    else return *reinterpret_cast<const unsigned *>(p);
+}
+
 // Stages `count` consecutive source rows starting at (unwrapped) row ys0 into their ring
 // slots, as np planes xh^p T (T_m when `masked`).  Each thread first issues the loads of
 // kBatch elements, then forms and stores their planes, so a band costs a few load
 // latencies rather than one per element.
-template <class R, class In, int LL, bool VEC = true>
+template <class R, class In, int LL, bool VEC, int kBatch>
 __device__ __forceinline__ void stage_rows(const In *__restrict__ tmpl, const uint8_t *__restrict__ mask, bool masked,
                                            const Geometry &g, const R *xps, int x0, int ys0, int count,
-                                           int ring_origin, R *Tp) {
+                                           int ring_origin, R *Tp, unsigned char *sk) {
     using W = Win<R, LL, VEC>;
-    constexpr int kBatch = 8;
+    constexpr int kC = Tile<R>::kCols;
     const int np = g.dk + 1, nx = g.nx, total = count * W::WC;
     for (int base = 0; base < total; base += kBatch * (int)blockDim.x) {
         In tv[kBatch];
@@ -156,30 +253,39 @@ __device__ __forceinline__ void stage_rows(const In *__restrict__ tmpl, const ui
             R *dst = Tp + (size_t)slot[i] * W::WCS + skew<R, VEC>(col[i]);
             dst[0] = t;
             for (int p = 1; p < np; p++) dst[(size_t)p * W::RING * W::WCS] = t * xps[p * W::WC + col[i]];
+            // the row's mask flags at the strip's output columns
+            const int oc = col[i] - W::h;
+            if (oc >= 0 && oc < kC) sk[slot[i] * kC + oc] = bad[i] ? 1 : 0;
         }
     }
 }
 
-// Folded coefficients c_p(d, y - dy) of output rows yb .. yb + kBand - 1, and their
-// background x-power sums.
-template <class R, int LL>
-__device__ __forceinline__ void stage_coeffs(const Geometry &g, const R *__restrict__ cfold, int yb, R *cf, R *byp) {
+// Folded coefficients c_p(d, y - dy) of output rows yb .. yb + kBand - 1 and their
+// background x-power sums, copied asynchronously.  PAIRED: rows ry and ry + kBand / 2
+// interleaved, so that one 16-byte load gives two lags' (row a, row b) operand pairs:
+// cf[((ry mod kBand/2) LL + dyi) np + p][2 LLP] with element 2 dxi + (ry >= kBand/2).
+template <class R, int LL, bool PAIRED = false>
+__device__ __forceinline__ void async_coeffs(const Geometry &g, const R *__restrict__ cfold, int yb, R *cf, R *byp) {
     using W = Win<R, LL>;
-    constexpr int h = LL / 2;
+    constexpr int h = LL / 2, kHalf = kBand / 2;
     const int np = g.dk + 1, ny = g.ny;
-    const int ncf = kBand * LL * np * LL;
-    for (int e = threadIdx.x; e < ncf; e += blockDim.x) {
-        int dxi = e % LL, rest = e / LL;
-        int p = rest % np;
-        rest /= np;
-        int dyi = rest % LL, ry = rest / LL;
-        int ys = wrapi(yb + ry - (dyi - h), ny);  // source row y - dy
-        cf[((ry * LL + dyi) * np + p) * W::LLP + dxi] = cfold[(((size_t)ys * LL + dyi) * np + p) * LL + dxi];
+    // a warp per (row, dy): the np LL values of one source row and dy are contiguous
+    const int nq = np * LL, lane = threadIdx.x & 31;
+    for (int rd = threadIdx.x >> 5; rd < kBand * LL; rd += blockDim.x >> 5) {
+        const int ry = rd / LL, dyi = rd - ry * LL;
+        const int ys = wrapi(yb + ry - (dyi - h), ny);  // source row y - dy
+        const R *src = cfold + ((size_t)ys * LL + dyi) * nq;
+        for (int q = lane; q < nq; q += 32) {
+            const int p = q / LL, dxi = q - p * LL;
+            R *dst = PAIRED ? cf + (((ry % kHalf) * LL + dyi) * np + p) * 2 * W::LLP + 2 * dxi + ry / kHalf
+                            : cf + ((ry * LL + dyi) * np + p) * W::LLP + dxi;
+            cp_async_elem(dst, src + q);
+        }
     }
     const R *bgf = cfold + (size_t)ny * LL * LL * np;
     for (int e = threadIdx.x; e < kBand * (g.db + 1); e += blockDim.x) {
         int ry = e / (g.db + 1), p = e % (g.db + 1);
-        byp[e] = bgf[(size_t)min(yb + ry, ny - 1) * (g.db + 1) + p];
+        cp_async_elem(byp + e, bgf + (size_t)min(yb + ry, ny - 1) * (g.db + 1) + p);
     }
 }
 
@@ -224,18 +330,23 @@ __device__ __forceinline__ void load_coeffs(const R *c, R (&cc)[Win<R, LL>::LLP]
 // Difference image (residual = false) or the fit residual m (S - bg) - conv(T_m)
 // (residual = true), one warp per output row of a band.
 template <class R, class In, int LL>
-__global__ void __launch_bounds__(32 * kBand) k_subtract(const In *__restrict__ sci, const In *__restrict__ tmpl,
+__global__ void __launch_bounds__(32 * kBand, 2) k_subtract(const In *__restrict__ sci, const In *__restrict__ tmpl,
                                                         const uint8_t *__restrict__ mask, bool residual, Geometry g,
                                                         int rows_per_chunk, const R *__restrict__ cfold,
                                                         const R *__restrict__ xpow_g, In *__restrict__ diff) {
     using W = Win<R, LL>;
+    using Ly = Layout<R, In, LL>;
     constexpr int h = W::h, kRX = Tile<R>::kRX;
+    constexpr int kRowBatch = (kBand * W::WC + 32 * kBand - 1) / (32 * kBand);  // a band's new rows in one batch
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int np = g.dk + 1, nx = g.nx, ny = g.ny;
-    R *Tp = reinterpret_cast<R *>(smem_raw);   // [np][RING][WCS]
-    R *cf = Tp + W::planes(np);                 // [kBand][LL][np][LLP], 16-byte aligned
-    R *byp = cf + kBand * LL * np * W::LLP;     // [kBand][db+1]
-    R *xps = byp + kBand * (g.db + 1);          // [npx][WC]
+    R *Tp = reinterpret_cast<R *>(smem_raw);
+    R *cf = reinterpret_cast<R *>(smem_raw + Ly::cf(np));
+    R *xo = reinterpret_cast<R *>(smem_raw + Ly::xo(np));
+    In *ss = reinterpret_cast<In *>(smem_raw + Ly::ss(np, g.db));
+    unsigned char *sk = smem_raw + Ly::sk(np, g.db);
+    R *byp = reinterpret_cast<R *>(smem_raw + Ly::byp(np, g.db));
+    R *xps = reinterpret_cast<R *>(smem_raw + Ly::xps(np, g.db));
     const int npx = np > g.db + 1 ? np : g.db + 1;
 
     const int x0 = blockIdx.x * Tile<R>::kCols;
@@ -243,26 +354,20 @@ __global__ void __launch_bounds__(32 * kBand) k_subtract(const In *__restrict__ 
     if (yc0 >= ny) return;
     const int ring_origin = yc0 - h;
     const int ty = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int cx = lane * kRX;
+    const int cx = lane * kRX, ob = skew<R>(cx);  // skew(cx + r) = ob + r for r < kRX
 
     fill_xps<R, LL>(g, xpow_g, x0, npx, xps);
+    fill_xo<R, LL, true>(g, xpow_g, x0, xo);
     __syncthreads();
-    stage_rows<R, In, LL>(tmpl, mask, residual, g, xps, x0, yc0 - h, W::RING, ring_origin, Tp);
+    // every global load of a band happens in the staging phase before it: the coefficients
+    // and science values as asynchronous copies that complete while the template rows load
+    async_coeffs<R, LL>(g, cfold, yc0, cf, byp);
+    async_sci<R, In, LL, true>(sci, g, x0, yc0, yc1, ss);
+    stage_rows<R, In, LL, true, 8>(tmpl, mask, residual, g, xps, x0, yc0 - h, W::RING, ring_origin, Tp, sk);
+    cp_async_wait();
     for (int yb = yc0; yb < yc1; yb += kBand) {
-        stage_coeffs<R, LL>(g, cfold, yb, cf, byp);
         __syncthreads();
         const int y = yb + ty;
-        // this row's science values and mask bytes, loaded before the convolution
-        In sv[kRX];
-        unsigned char mv[kRX];
-#pragma unroll
-        for (int r = 0; r < kRX; r++) {
-            const int x = x0 + cx + r;
-            const bool ok = y < yc1 && x < nx;
-            const size_t u = (size_t)y * g.pitch + x;
-            sv[r] = ok ? sci[u] : (In)0;
-            mv[r] = ok && residual && mask ? mask[u] : 0;
-        }
         R out[kRX];
 #pragma unroll
         for (int r = 0; r < kRX; r++) out[r] = (R)0;
@@ -286,17 +391,31 @@ __global__ void __launch_bounds__(32 * kBand) k_subtract(const In *__restrict__ 
         }
         if (y < yc1) {
             const R *bp = byp + ty * (g.db + 1);
+            In svi[kRX];
+            R sv[kRX], bg[kRX];
+            // 16-byte loads only where the skew is the FP32 one (runs start on 4 elements)
+            load_run<In, kRX, sizeof(R) == 4>(ss + ty * Ly::OC + ob, svi);
+#pragma unroll
+            for (int r = 0; r < kRX; r++) sv[r] = (R)svi[r];
+            const unsigned long long mv =
+                residual ? load_flags<kRX>(sk + ((y - ring_origin) % W::RING) * Ly::kC + cx) : 0ull;
+#pragma unroll
+            for (int r = 0; r < kRX; r++) bg[r] = (R)0;
+            for (int p = 0; p <= g.db; p++) {
+                R xv[kRX];
+                load_run<R, kRX, sizeof(R) == 4>(xo + p * Ly::OC + ob, xv);
+#pragma unroll
+                for (int r = 0; r < kRX; r++) bg[r] += bp[p] * xv[r];
+            }
 #pragma unroll
             for (int r = 0; r < kRX; r++) {
                 const int x = x0 + cx + r;
                 if (x < nx) {
-                    R bg = (R)0;
-                    for (int p = 0; p <= g.db; p++) bg += bp[p] * xps[p * W::WC + cx + r + h];
                     const size_t u = (size_t)y * g.pitch + x;
                     if (residual) {
-                        diff[u] = (In)((mv[r] ? (R)0 : (R)sv[r] - bg) - out[r]);
+                        diff[u] = (In)((((mv >> (8 * r)) & 0xff) ? (R)0 : sv[r] - bg[r]) - out[r]);
                     } else {
-                        diff[u] = (In)((R)sv[r] - out[r] - bg);
+                        diff[u] = (In)(sv[r] - out[r] - bg[r]);
                     }
                 }
             }
@@ -304,8 +423,13 @@ __global__ void __launch_bounds__(32 * kBand) k_subtract(const In *__restrict__ 
         __syncthreads();
         // the next band reads source rows up to yb + 2 kBand + h - 1; the kBand new ones
         // replace rows yb - h .. yb - h + kBand - 1, which no later band reads
-        if (yb + kBand < yc1) stage_rows<R, In, LL>(tmpl, mask, residual, g, xps, x0, yb + kBand + h, kBand,
-                                                    ring_origin, Tp);
+        if (yb + kBand < yc1) {
+            async_coeffs<R, LL>(g, cfold, yb + kBand, cf, byp);
+            async_sci<R, In, LL, true>(sci, g, x0, yb + kBand, yc1, ss);
+            stage_rows<R, In, LL, true, kRowBatch>(tmpl, mask, residual, g, xps, x0, yb + kBand + h, kBand,
+                                                   ring_origin, Tp, sk);
+            cp_async_wait();
+        }
     }
 }
 
@@ -337,16 +461,6 @@ __device__ __forceinline__ void two_sum2(float2 a, float2 b, float2 &s, float2 &
     e = __fadd2_rn(__fadd2_rn(a, neg2(__fadd2_rn(s, neg2(bb)))), __fadd2_rn(b, neg2(bb)));
 }
 
-template <class In>
-__device__ __forceinline__ void split_input(In v, float &hi, float &lo) {
-    hi = (float)v;
-    lo = (float)((double)v - (double)hi);
-}
-template <>
-__device__ __forceinline__ void split_input<float>(float v, float &hi, float &lo) {
-    hi = v;
-    lo = 0.f;
-}
 
 // With mom_part, the kernel also writes this CTA's part of the residual's background moments
 // sum_u m(u) w_r(u) R(u) (r < nP(DB), in the monomial order): FP32 sums over a thread's
@@ -359,14 +473,19 @@ __global__ void __launch_bounds__(16 * kBand, 2) k_residual_comp(const In *__res
                                                                  const float *__restrict__ xpow_g,
                                                                  In *__restrict__ resid, double *__restrict__ mom_part) {
     using W = Win<float, LL, false>;
+    using Ly = Layout<float, In, LL, false>;
     constexpr int h = W::h, kRX = Tile<float>::kRX;
     constexpr int kHalf = kBand / 2;
+    constexpr int kRowBatch = (kBand * W::WC + 16 * kBand - 1) / (16 * kBand);  // a band's new rows in one batch
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int np = g.dk + 1, nx = g.nx, ny = g.ny;
     float *Tp = reinterpret_cast<float *>(smem_raw);
-    float *cf = Tp + W::planes(np);  // 16-byte aligned
-    float *byp = cf + kBand * LL * np * W::LLP;
-    float *xps = byp + kBand * (g.db + 1);
+    float *cf = reinterpret_cast<float *>(smem_raw + Ly::cf(np));
+    float *xo = reinterpret_cast<float *>(smem_raw + Ly::xo(np));
+    In *ss = reinterpret_cast<In *>(smem_raw + Ly::ss(np, g.db));
+    unsigned char *sk = smem_raw + Ly::sk(np, g.db);
+    float *byp = reinterpret_cast<float *>(smem_raw + Ly::byp(np, g.db));
+    float *xps = reinterpret_cast<float *>(smem_raw + Ly::xps(np, g.db));
     const int npx = np > g.db + 1 ? np : g.db + 1;
 
     const int x0 = blockIdx.x * Tile<float>::kCols;
@@ -380,36 +499,43 @@ __global__ void __launch_bounds__(16 * kBand, 2) k_residual_comp(const In *__res
     }
     const int ring_origin = yc0 - h;
     const int ty = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int cx = lane * kRX;
+    const int cx = lane * kRX, wsk = cx + lane;  // wsk = skew(cx), kRX = 8
+    static_assert(kRX == 8, "the window offsets assume 8 pixels per lane");
+    const float yscale = ny > 1 ? 1.f / (float)(ny - 1) : 0.f;
     for (int e = threadIdx.x; e < (kBand / 2) * kMaxMom; e += blockDim.x) (&macc[0][0])[e] = 0.0;
 
     fill_xps<float, LL>(g, xpow_g, x0, npx, xps);
+    fill_xo<float, LL, false>(g, xpow_g, x0, xo);
     __syncthreads();
-    stage_rows<float, In, LL, false>(tmpl, mask, true, g, xps, x0, yc0 - h, W::RING, ring_origin, Tp);
+    // every global load of a band happens in the staging phase before it: the coefficients
+    // and science values as asynchronous copies that complete while the template rows load
+    async_coeffs<float, LL, true>(g, cfold, yc0, cf, byp);
+    async_sci<float, In, LL, false>(sci, g, x0, yc0, yc1, ss);
+    stage_rows<float, In, LL, false, 8>(tmpl, mask, true, g, xps, x0, yc0 - h, W::RING, ring_origin, Tp, sk);
+    cp_async_wait();
     for (int yb = yc0; yb < yc1; yb += kBand) {
-        stage_coeffs<float, LL>(g, cfold, yb, cf, byp);
         __syncthreads();
         const int ya = yb + ty, yb2 = ya + kHalf;
         float2 hi[kRX], lo[kRX], wing[kRX];
         unsigned good = 0;  // bit 2 r + k: pixel r of row k exists and is not masked
+        const int sla = (ya - ring_origin) % W::RING, slb = (sla + kHalf) % W::RING;
+        const bool in_a = ya < yc1, in_b = yb2 < yc1;
+        const unsigned long long skip[2] = {in_a ? load_flags<kRX>(sk + sla * Ly::kC + cx) : ~0ull,
+                                            in_b ? load_flags<kRX>(sk + slb * Ly::kC + cx) : ~0ull};
         // start from m (S - bg): S split exactly into hi + lo, the background subtracted by two-sum
 #pragma unroll
         for (int r = 0; r < kRX; r++) {
-            const int x = x0 + cx + r;
             float sh[2] = {0.f, 0.f}, sl[2] = {0.f, 0.f}, bg[2] = {0.f, 0.f};
 #pragma unroll
             for (int k = 0; k < 2; k++) {
-                const int y = k ? yb2 : ya;
-                if (y < yc1 && x < nx) {
-                    const size_t u = (size_t)y * g.pitch + x;
-                    if (!(mask && mask[u])) {
-                        good |= 1u << (2 * r + k);
-                        split_input<In>(sci[u], sh[k], sl[k]);
-                        const float *bp = byp + (k ? ty + kHalf : ty) * (g.db + 1);
-                        float b = 0.f;
-                        for (int p = 0; p <= g.db; p++) b = fmaf(bp[p], xps[p * W::WC + cx + r + h], b);
-                        bg[k] = b;
-                    }
+                if (x0 + cx + r < nx && !((skip[k] >> (8 * r)) & 0xff)) {
+                    const int row = k ? ty + kHalf : ty;
+                    good |= 1u << (2 * r + k);
+                    split_input<In>(ss[row * Ly::OC + wsk + r], sh[k], sl[k]);
+                    const float *bp = byp + row * (g.db + 1);
+                    float b = 0.f;
+                    for (int p = 0; p <= g.db; p++) b = fmaf(bp[p], xo[p * Ly::OC + wsk + r], b);
+                    bg[k] = b;
                 }
             }
             float2 s, e;
@@ -422,18 +548,23 @@ __global__ void __launch_bounds__(16 * kBand, 2) k_residual_comp(const In *__res
             const int sa = (ya + h - dyi - ring_origin) % W::RING, sb = (sa + kHalf) % W::RING;
             const bool core_row = dyi >= h - kCore && dyi <= h + kCore;
             for (int p = 0; p < np; p++) {
-                const float *ta = Tp + (p * W::RING + sa) * W::WCS, *tb = Tp + (p * W::RING + sb) * W::WCS;
+                // skew(cx + m) = wsk + m + m / 8: the window's offsets are immediates
+                const float *ta = Tp + (p * W::RING + sa) * W::WCS + wsk, *tb = Tp + (p * W::RING + sb) * W::WCS + wsk;
                 float2 wp[W::NW];
 #pragma unroll
-                for (int m = 0; m < W::NW; m++)
-                    wp[m] = make_float2(ta[skew<float, false>(cx + m)], tb[skew<float, false>(cx + m)]);
-                float ca[W::LLP], cb[W::LLP];
-                load_coeffs<float, LL>(cf + ((ty * LL + dyi) * np + p) * W::LLP, ca);
-                load_coeffs<float, LL>(cf + (((ty + kHalf) * LL + dyi) * np + p) * W::LLP, cb);
+                for (int m = 0; m < W::NW; m++) wp[m] = make_float2(ta[m + (m >> 3)], tb[m + (m >> 3)]);
+                float2 cp[W::LLP];  // (row a, row b) coefficient pairs
+                const float4 *cq = reinterpret_cast<const float4 *>(cf + ((ty * LL + dyi) * np + p) * 2 * W::LLP);
+#pragma unroll
+                for (int k = 0; k < W::LLP / 2; k++) {
+                    const float4 v = cq[k];
+                    cp[2 * k] = make_float2(v.x, v.y);
+                    cp[2 * k + 1] = make_float2(v.z, v.w);
+                }
                 if (core_row && p == 0) {
 #pragma unroll
                     for (int dxi = 0; dxi < LL; dxi++) {
-                        const float2 cc = make_float2(ca[dxi], cb[dxi]);
+                        const float2 cc = cp[dxi];
                         if (dxi >= h - kCore && dxi <= h + kCore) {
 #pragma unroll
                             for (int r = 0; r < kRX; r++) {
@@ -453,7 +584,7 @@ __global__ void __launch_bounds__(16 * kBand, 2) k_residual_comp(const In *__res
                 } else {
 #pragma unroll
                     for (int dxi = 0; dxi < LL; dxi++) {
-                        const float2 cc = make_float2(ca[dxi], cb[dxi]);
+                        const float2 cc = cp[dxi];
 #pragma unroll
                         for (int r = 0; r < kRX; r++) wing[r] = __ffma2_rn(cc, wp[r + (LL - 1) - dxi], wing[r]);
                     }
@@ -467,17 +598,31 @@ __global__ void __launch_bounds__(16 * kBand, 2) k_residual_comp(const In *__res
         for (int r = 0; r < kRX; r++) {
             const int x = x0 + cx + r;
             if (x >= nx) continue;
-            const double ra = (double)hi[r].x + ((double)lo[r].x - (double)wing[r].x);
-            const double rb = (double)hi[r].y + ((double)lo[r].y - (double)wing[r].y);
-            if (ya < yc1) resid[(size_t)ya * g.pitch + x] = (In)ra;
-            if (yb2 < yc1) resid[(size_t)yb2 * g.pitch + x] = (In)rb;
+            // R = hi + lo - wing.  FP32 output: (hi - wing) is within a few rounding units of R
+            // (lo is of the order u |hi|), so the two FP32 adds cost about one extra rounding
+            // of R; on this part an FP64 add runs at 1/64 of the FP32 rate.
+            float fa, fb;
+            if constexpr (std::is_same<In, float>::value) {
+                const float2 t = __fadd2_rn(__fadd2_rn(hi[r], neg2(wing[r])), lo[r]);
+                fa = t.x;
+                fb = t.y;
+                if (ya < yc1) resid[(size_t)ya * g.pitch + x] = fa;
+                if (yb2 < yc1) resid[(size_t)yb2 * g.pitch + x] = fb;
+            } else {
+                const double ra = (double)hi[r].x + ((double)lo[r].x - (double)wing[r].x);
+                const double rb = (double)hi[r].y + ((double)lo[r].y - (double)wing[r].y);
+                if (ya < yc1) resid[(size_t)ya * g.pitch + x] = (In)ra;
+                if (yb2 < yc1) resid[(size_t)yb2 * g.pitch + x] = (In)rb;
+                fa = (float)ra;
+                fb = (float)rb;
+            }
             if (mom_part) {
-                const float fa = (good >> (2 * r)) & 1u ? (float)ra : 0.f;
-                const float fb = (good >> (2 * r + 1)) & 1u ? (float)rb : 0.f;
+                fa = (good >> (2 * r)) & 1u ? fa : 0.f;
+                fb = (good >> (2 * r + 1)) & 1u ? fb : 0.f;
 #pragma unroll
                 for (int p = 0; p <= kMaxDB; p++) {
                     if (p > g.db) break;
-                    const float xv = xps[p * W::WC + cx + r + h];
+                    const float xv = xo[p * Ly::OC + wsk + r];
                     ma[p] = fmaf(fa, xv, ma[p]);
                     mb[p] = fmaf(fb, xv, mb[p]);
                 }
@@ -493,25 +638,29 @@ __global__ void __launch_bounds__(16 * kBand, 2) k_residual_comp(const In *__res
                     mb[p] += __shfl_xor_sync(0xffffffffu, mb[p], o);
                 }
             }
-            if (lane == 0) {
-                const double yha = ny > 1 ? (2.0 * ya - (ny - 1)) / (double)(ny - 1) : 0.0;
-                const double yhb = ny > 1 ? (2.0 * yb2 - (ny - 1)) / (double)(ny - 1) : 0.0;
-                for (int j = 0; j < g.nb; j++) {
-                    int pr, qs;
-                    mono_pq(j, pr, qs);
-                    double wa = 1.0, wb = 1.0;
-                    for (int q = 0; q < qs; q++) wa *= yha, wb *= yhb;
-                    float va = 0.f, vb = 0.f;
+            // lane j < nP(DB) adds moment j of the two rows (FP32 weights yh^q) to its FP64 sum
+            if (lane < g.nb) {
+                const float yha = ny > 1 ? (float)(2 * ya - (ny - 1)) * yscale : 0.f;
+                const float yhb = ny > 1 ? (float)(2 * yb2 - (ny - 1)) * yscale : 0.f;
+                int pr, qs;
+                mono_pq(lane, pr, qs);
+                float wa = 1.f, wb = 1.f;
+                for (int q = 0; q < qs; q++) wa *= yha, wb *= yhb;
+                float va = 0.f, vb = 0.f;
 #pragma unroll
-                    for (int p = 0; p <= kMaxDB; p++)
-                        if (p == pr) va = ma[p], vb = mb[p];
-                    macc[ty][j] += wa * (double)va + wb * (double)vb;
-                }
+                for (int p = 0; p <= kMaxDB; p++)
+                    if (p == pr) va = ma[p], vb = mb[p];
+                macc[ty][lane] += (double)fmaf(wa, va, wb * vb);
             }
         }
         __syncthreads();
-        if (yb + kBand < yc1)
-            stage_rows<float, In, LL, false>(tmpl, mask, true, g, xps, x0, yb + kBand + h, kBand, ring_origin, Tp);
+        if (yb + kBand < yc1) {
+            async_coeffs<float, LL, true>(g, cfold, yb + kBand, cf, byp);
+            async_sci<float, In, LL, false>(sci, g, x0, yb + kBand, yc1, ss);
+            stage_rows<float, In, LL, false, kRowBatch>(tmpl, mask, true, g, xps, x0, yb + kBand + h, kBand,
+                                                        ring_origin, Tp, sk);
+            cp_async_wait();
+        }
     }
     if (mom_part) {
         __syncthreads();
@@ -556,12 +705,12 @@ cudaError_t run(const Geometry &g, const void *sci, const void *tmpl, const uint
         k_fold<R><<<(unsigned)((nt + 255) / 256), 256, 0, st>>>(coeffs, g, (R *)cfold);
     }
     const int np = g.dk + 1;
-    const size_t sm = stream_smem<R, LL>(np, g.db);
+    const size_t sm = Layout<R, In, LL>::bytes(np, g.db);
     const int strips = (g.nx + Tile<R>::kCols - 1) / Tile<R>::kCols;
     if constexpr (std::is_same<R, float>::value) {
         if (residual) {
             auto kc = k_residual_comp<In, LL>;
-            const size_t smc = stream_smem<float, LL, false>(np, g.db);
+            const size_t smc = Layout<float, In, LL, false>::bytes(np, g.db);
             cudaError_t e = cudaFuncSetAttribute(kc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smc);
             if (e == cudaSuccess)
                 e = cudaFuncSetAttribute(kc, cudaFuncAttributePreferredSharedMemoryCarveout,
