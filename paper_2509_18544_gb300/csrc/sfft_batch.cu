@@ -144,6 +144,14 @@ namespace {
 
 constexpr int kRec = 8;
 
+// ny rows of `width` bytes, `pitch` bytes apart on both sides: one contiguous copy when the
+// rows touch (a 2-D copy of narrow rows, such as a mask's, runs far below the link's rate)
+cudaError_t copy_frame(void *dst, const void *src, size_t pitch, size_t width, int ny, cudaMemcpyKind kind,
+                       cudaStream_t s) {
+    if (pitch == width) return cudaMemcpyAsync(dst, src, width * (size_t)ny, kind, s);
+    return cudaMemcpy2DAsync(dst, pitch, src, pitch, width, ny, kind, s);
+}
+
 // queue the whole batch: fork from `origin` into the lanes, run each lane's pairs, join
 cudaError_t queue_batch(sfft_batch_t b, sfft_status *st) {
     cudaError_t e = cudaEventRecord(b->ev_fork, b->origin);
@@ -156,14 +164,14 @@ cudaError_t queue_batch(sfft_batch_t b, sfft_status *st) {
             const size_t elt = b->base.dtype == SFFT_F64 ? 8 : 4;
             const size_t pitch = q.pitch ? q.pitch : q.nx;
             if (q.sci_host) {  // this pair's inputs, on its own lane
-                e = cudaMemcpy2DAsync(const_cast<void *>(q.sci), pitch * elt, q.sci_host, pitch * elt, q.nx * elt, q.ny,
-                                      cudaMemcpyHostToDevice, b->ls[l]);
+                e = copy_frame(const_cast<void *>(q.sci), q.sci_host, pitch * elt, q.nx * elt, q.ny,
+                               cudaMemcpyHostToDevice, b->ls[l]);
                 if (e == cudaSuccess && q.tmpl_host)
-                    e = cudaMemcpy2DAsync(const_cast<void *>(q.tmpl), pitch * elt, q.tmpl_host, pitch * elt,
-                                          q.nx * elt, q.ny, cudaMemcpyHostToDevice, b->ls[l]);
+                    e = copy_frame(const_cast<void *>(q.tmpl), q.tmpl_host, pitch * elt, q.nx * elt, q.ny,
+                                   cudaMemcpyHostToDevice, b->ls[l]);
                 if (e == cudaSuccess && q.mask && q.mask_host)
-                    e = cudaMemcpy2DAsync(const_cast<uint8_t *>(q.mask), pitch, q.mask_host, pitch, q.nx, q.ny,
-                                          cudaMemcpyHostToDevice, b->ls[l]);
+                    e = copy_frame(const_cast<uint8_t *>(q.mask), q.mask_host, pitch, q.nx, q.ny, cudaMemcpyHostToDevice,
+                                   b->ls[l]);
                 if (e != cudaSuccess) break;
             }
             sfft_status s = sfft_fit(p, q.sci, q.tmpl, q.mask, q.x0, q.coeffs, nullptr);
@@ -176,8 +184,7 @@ cudaError_t queue_batch(sfft_batch_t b, sfft_status *st) {
             if (q.coeffs_host)
                 e = cudaMemcpyAsync(q.coeffs_host, q.coeffs, sizeof(double) * p->g.n, cudaMemcpyDeviceToHost, b->ls[l]);
             if (e == cudaSuccess && q.diff_host)
-                e = cudaMemcpy2DAsync(q.diff_host, pitch * elt, q.diff, pitch * elt, q.nx * elt, q.ny,
-                                      cudaMemcpyDeviceToHost, b->ls[l]);
+                e = copy_frame(q.diff_host, q.diff, pitch * elt, q.nx * elt, q.ny, cudaMemcpyDeviceToHost, b->ls[l]);
             if (e != cudaSuccess) break;
             // the pair's outcome: status word, solver flags and norms into its record
             double *r = b->rec + (size_t)pi * kRec;

@@ -166,3 +166,37 @@ def test_batch_with_host_buffers_copies_in_and_out_on_the_lanes():
     for c, (th, D) in zip(cuts, refs):
         assert torch.equal(c["host"]["coeffs"], th.cpu())
         assert torch.equal(c["host"]["diff"][:, :c["nx"]], D[:, :c["nx"]].cpu())
+
+
+def test_batch_with_contiguous_host_frames():
+    """Whole frames (pitch == nx) with pinned host buffers: the copies in and out are single
+    contiguous transfers; the host results equal single-pair device runs bit for bit."""
+    n = oracle.n_unknowns(L, DK, DB)
+    pairs, refs, keep = [], [], []
+    for k, (ny, nx) in enumerate([(160, 192), (224, 128), (128, 256)]):
+        S, T, M = synth.roman_pair(ny, nx, seed=300 + k, n_stars=60)
+        c = dict(S=torch.from_numpy(S).to(DEV), T=torch.from_numpy(T).to(DEV), M=torch.from_numpy(M).to(DEV))
+        d = sfft.make_desc(ny, nx, L, DK, DB)
+        with sfft.sfft_plan(d) as p:
+            th = torch.empty(n, dtype=torch.float64, device=DEV)
+            D = torch.empty((ny, nx), dtype=torch.float32, device=DEV)
+            sfft.sfft_fit(p, c["S"], c["T"], c["M"], None, th)
+            sfft.sfft_subtract(p, c["S"], c["T"], th, D)
+            torch.cuda.synchronize()
+        refs.append((th, D))
+        host = dict(sci=torch.from_numpy(S).pin_memory(), tmpl=torch.from_numpy(T).pin_memory(),
+                    mask=torch.from_numpy(M).pin_memory(),
+                    coeffs=torch.full((n,), float("nan"), dtype=torch.float64).pin_memory(),
+                    diff=torch.full((ny, nx), float("nan"), dtype=torch.float32).pin_memory())
+        dev = [torch.zeros_like(c[a]) for a in ("S", "T", "M")]
+        th2 = torch.empty(n, dtype=torch.float64, device=DEV)
+        D2 = torch.empty((ny, nx), dtype=torch.float32, device=DEV)
+        keep.append((host, dev, th2, D2))
+        pairs.append(sfft.make_pair(dev[0], dev[1], dev[2], th2, D2, ny, nx, host=host))
+    with sfft.sfft_batch_create(sfft.make_desc(128, 128, L, DK, DB), pairs, lanes=3, flags=sfft.BATCH_GRAPH) as b:
+        sfft.sfft_batch_run(b)
+        infos = sfft.sfft_batch_info(b)
+    for (host, _, _, _), (th, D), info in zip(keep, refs, infos):
+        assert info.status == 0
+        assert torch.equal(host["coeffs"], th.cpu())
+        assert torch.equal(host["diff"], D.cpu())
