@@ -10,6 +10,8 @@
 //
 // These spectra feed the lag correlations of the normal matrix of the delta-basis fit
 // (SFFT subtraction step, Sec. "Pipeline steps", step 6).
+#include <algorithm>
+
 #include "sfft_internal.cuh"
 
 namespace sfft {
@@ -95,37 +97,50 @@ __device__ __forceinline__ void fft256(cpx<R> (&v)[16], int t, cpx<R> *e, const 
 }
 
 constexpr int kRowsPerCta = 16;
+constexpr int kMaxRowsPP = 4;  // rows transformed per pass
 // exchange buffer per FFT: 16 x 17 (padded transpose) + 1, so that buffers of consecutive
 // FFTs start two banks apart instead of on the same bank
 constexpr int kEx = 16 * 17 + 1;
 
-// Spectra of every image of a row segment, two rows per pass.  Layout of the output:
+// The weights factor: w_i = xh^p yh^q with yh constant along a row, so the row-segment
+// spectrum of any image is yh^q times the spectrum of its x-weighted base image.  The
+// kernel transforms only the base images
+//   b = p            A side: xh^p T_m on the segment's own columns (p <= DK)
+//   b = DK+1+p       B side: xh^p T_m on the window
+//   b = 2(DK+1)+p    xh^p m on the window (p <= DB)
+//   b = nbase-1      S_m on the window
+// two to a complex FFT, and writes every output image from its base spectrum times yh^q.
+__host__ __device__ __forceinline__ int n_base(int dk, int db) { return 2 * (dk + 1) + (db + 1) + 1; }
+
+// Spectra of every image of a row segment, rows_pp rows per pass.  Layout of the output:
 // spec[s][y][k][img] (a contiguous block of nkf * nimg_pad values per row segment).
 template <class R, class In, int MAXT, int MINB>
 __global__ void __launch_bounds__(MAXT, MINB) k_segment_fft(const In *__restrict__ sci, const In *__restrict__ tmpl,
-                                                    const uint8_t *__restrict__ mask, Geometry g,
+                                                    const uint8_t *__restrict__ mask, Geometry g, int rows_pp,
                                                     const cpx<R> *__restrict__ tw_g, const R *__restrict__ xpow_g,
                                                     const R *__restrict__ ypow_g, cpx<R> *__restrict__ spec) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int nk = g.nk, nb = g.nb, G = g.G, U = g.U, nx = g.nx, ny = g.ny, NI = g.nimg_pad, nkf = g.nkf;
     const int maxdeg = g.dk > g.db ? g.dk : g.db;
+    const int nbase = n_base(g.dk, g.db), nbfft = (nbase + 1) / 2;
     const int s = blockIdx.x;
     const int x0 = s * U;
     const int tid = threadIdx.x, nthr = blockDim.x;
-    const int per_row = g.nfft * 16;
+    const int per_row = nbfft * 16;
 
     cpx<R> *tw = reinterpret_cast<cpx<R> *>(smem_raw);  // [P] twiddle, high part
     cpx<R> *twl = tw + kP;                              // [P] remainder
-    cpx<R> *ex = twl + kP;                              // [2][nfft][kEx]
-    R *xpow = reinterpret_cast<R *>(ex + 2 * g.nfft * kEx);  // [maxdeg+1][P + 1] (row P is all ones)
+    cpx<R> *ex = twl + kP;                              // [rows_pp][nbfft][kEx]
+    R *xpow = reinterpret_cast<R *>(ex + (size_t)rows_pp * nbfft * kEx);  // [maxdeg+1][P]
     R *ones = xpow + (maxdeg + 1) * kP;                 // [P] ones (S_m has no coordinate weight)
-    R *tv = ones + kP;                                  // [2][P] T_m on the window
-    R *sv = tv + 2 * kP;                                // [2][P] S_m
-    R *mv = sv + 2 * kP;                                // [2][P] m
-    int *ik = reinterpret_cast<int *>(mv + 2 * kP);     // [nimg_pad] kind
-    int *ip = ik + NI;                                  // [nimg_pad] p
-    int *iq = ip + NI;                                  // [nimg_pad] q
-    int *wcol = iq + NI;                                // [P] frame column of each window column
+    R *tv = ones + kP;                                  // [rows_pp][P] T_m on the window
+    R *sv = tv + rows_pp * kP;                          // [rows_pp][P] S_m
+    R *mv = sv + rows_pp * kP;                          // [rows_pp][P] m
+    int *bk = reinterpret_cast<int *>(mv + rows_pp * kP);  // [2 nbfft] base kind
+    int *bp = bk + 2 * nbfft;                           // [2 nbfft] base x power
+    int *ob = bp + 2 * nbfft;                           // [nimg_pad] base of each output image (-1: zero)
+    int *oq = ob + NI;                                  // [nimg_pad] y power of each output image
+    int *wcol = oq + NI;                                // [P] frame column of each window column
 
     for (int i = tid; i < kP; i += nthr) {
         tw[i] = tw_g[i];
@@ -137,27 +152,35 @@ __global__ void __launch_bounds__(MAXT, MINB) k_segment_fft(const In *__restrict
         ones[i] = (R)1;
         wcol[i] = xw;
     }
-    for (int i = tid; i < NI; i += nthr) {
-        // kinds: 0 = A (W_i on own columns), 1 = B W_i, 2 = Psi_r, 3 = S_m, 4 = zero pad
-        int kind, mi = 0;
-        if (i < nk) { kind = 0; mi = i; }
-        else if (i < 2 * nk) { kind = 1; mi = i - nk; }
-        else if (i < 2 * nk + nb) { kind = 2; mi = i - 2 * nk; }
-        else if (i == 2 * nk + nb) { kind = 3; }
+    for (int b = tid; b < 2 * nbfft; b += nthr) {
+        // kinds: 0 = A (own columns), 1 = B (window), 2 = m (window), 3 = S_m, 4 = zero pad
+        const int na = g.dk + 1;
+        int kind, p = 0;
+        if (b < na) { kind = 0; p = b; }
+        else if (b < 2 * na) { kind = 1; p = b - na; }
+        else if (b < 2 * na + g.db + 1) { kind = 2; p = b - 2 * na; }
+        else if (b == nbase - 1) { kind = 3; }
         else { kind = 4; }
-        int p = 0, q = 0;
-        mono_pq(mi, p, q);
-        ik[i] = kind;
-        ip[i] = p;
-        iq[i] = q;
+        bk[b] = kind;
+        bp[b] = p;
+    }
+    for (int i = tid; i < NI; i += nthr) {
+        const int na = g.dk + 1;
+        int base = -1, p = 0, q = 0;
+        if (i < nk) { mono_pq(i, p, q); base = p; }
+        else if (i < 2 * nk) { mono_pq(i - nk, p, q); base = na + p; }
+        else if (i < 2 * nk + nb) { mono_pq(i - 2 * nk, p, q); base = 2 * na + p; }
+        else if (i == 2 * nk + nb) { base = nbase - 1; q = 0; }
+        ob[i] = base;
+        oq[i] = q;
     }
 
     const int ybeg = blockIdx.y * kRowsPerCta, yend = min(ny, ybeg + kRowsPerCta);
-    // window positions loaded per thread per pass (2 rows x P positions): position
+    // window positions loaded per thread per pass (rows_pp rows x P positions): position
     // q = tid + c nthr is row q / P, window column q % P; its wrapped frame column is fixed
     // for the whole kernel, so it is computed once
     constexpr int kMaxPf = 4;
-    const int npos = 2 * kP;
+    const int npos = rows_pp * kP;
     auto load_pos = [&](int c, int ybase, R &t_out, R &s_out, R &m_out) {
         const int q = tid + c * nthr;
         const int y = ybase + (q >> 8);
@@ -173,57 +196,47 @@ __global__ void __launch_bounds__(MAXT, MINB) k_segment_fft(const In *__restrict
         }
     };
     __syncthreads();  // wcol
-    // prologue: window of the first pass straight to shared memory
+    // prologue: window of the first pass straight to shared memory (the host gives every
+    // launch at least npos / kMaxPf threads)
 #pragma unroll
     for (int c = 0; c < kMaxPf; c++) {
         const int q = tid + c * nthr;
         if (q < npos) load_pos(c, ybeg, tv[q], sv[q], mv[q]);
     }
-    for (int q = tid + kMaxPf * nthr; q < npos; q += nthr) {  // only with fewer than 128 threads
-        const int r = q >> 8, y = ybeg + r;
-        const size_t u = (size_t)y * g.pitch + wrapi(x0 - G + (q & (kP - 1)), nx);
-        const bool use = y < yend && !(mask && mask[u]);
-        tv[q] = use ? (R)tmpl[u] : (R)0;
-        sv[q] = use ? (R)sci[u] : (R)0;
-        mv[q] = use ? (R)1 : (R)0;
-    }
     __syncthreads();
 
     const int r_fft = tid / per_row, rem = tid - r_fft * per_row;
     const int f = rem >> 4, t = rem & 15;
-    for (int y0 = ybeg; y0 < yend; y0 += 2) {
+    for (int y0 = ybeg; y0 < yend; y0 += rows_pp) {
         // prefetch the next pass's window into registers
         R pft[kMaxPf], pfs[kMaxPf], pfm[kMaxPf];
-        const bool more = y0 + 2 < yend;
+        const bool more = y0 + rows_pp < yend;
 #pragma unroll
         for (int c = 0; c < kMaxPf; c++) {
             int q = tid + c * nthr;
-            if (more && q < npos) load_pos(c, y0 + 2, pft[c], pfs[c], pfm[c]);
+            if (more && q < npos) load_pos(c, y0 + rows_pp, pft[c], pfs[c], pfm[c]);
         }
         // FFT lanes of this warp: each half-warp is one FFT of a row that exists
         auto half_active = [&](int base) {
             int rr = base / per_row;
-            return base < 2 * per_row && y0 + rr < yend;
+            return base < rows_pp * per_row && y0 + rr < yend;
         };
         const int wbase = tid & ~31;
         const unsigned msk = (half_active(wbase) ? 0x0000ffffu : 0u) | (half_active(wbase + 16) ? 0xffff0000u : 0u);
-        if (r_fft < 2 && y0 + r_fft < yend) {
-            const int y = y0 + r_fft;
+        if (r_fft < rows_pp && y0 + r_fft < yend) {
             const R *tvr = tv + r_fft * kP, *svr = sv + r_fft * kP, *mvr = mv + r_fft * kP;
-            // per image of this lane's pair: source row, coordinate-power row, y weight, offset
-            // of the pixel inside the window and the number of valid positions (branch-free
+            // per base image of this lane's pair: source row, coordinate-power row, offset of
+            // the pixel inside the window and the number of valid positions (branch-free
             // construction of z = x_{2f} + i x_{2f+1} below)
             const R *src[2], *xpr[2];
-            R yq[2];
             int off[2], lim[2];
 #pragma unroll
             for (int c = 0; c < 2; c++) {
-                const int im = 2 * f + c, kind = ik[im];
+                const int b = 2 * f + c, kind = bk[b];
                 src[c] = kind == 2 ? mvr : (kind == 3 ? svr : tvr);
-                xpr[c] = kind == 3 ? ones : xpow + ip[im] * kP;
-                yq[c] = kind == 3 ? (R)1 : (kind == 4 ? (R)0 : ypow_g[(size_t)iq[im] * ny + y]);
+                xpr[c] = kind == 3 ? ones : xpow + bp[b] * kP;
                 off[c] = kind == 0 ? G : 0;
-                lim[c] = kind == 0 ? min(U, nx - x0) : kP;
+                lim[c] = kind == 0 ? min(U, nx - x0) : (kind == 4 ? 0 : kP);
             }
             cpx<R> v[16];
 #pragma unroll
@@ -233,46 +246,53 @@ __global__ void __launch_bounds__(MAXT, MINB) k_segment_fft(const In *__restrict
 #pragma unroll
                 for (int c = 0; c < 2; c++) {
                     const int q = n < lim[c] ? n + off[c] : 0;
-                    R r = xpr[c][q] * yq[c] * src[c][q];
+                    R r = xpr[c][q] * src[c][q];
                     val[c] = n < lim[c] ? r : (R)0;
                 }
                 v[jj] = {val[0], val[1]};
             }
-            cpx<R> *e = ex + (r_fft * g.nfft + f) * kEx;
+            cpx<R> *e = ex + (r_fft * nbfft + f) * kEx;
             fft256(v, t, e, tw, twl, msk);
 #pragma unroll
             for (int k2 = 0; k2 < 16; k2++) e[t + 16 * k2] = v[k2];  // natural order Z[k]
         }
         __syncthreads();
-        // unpack the packed real pairs; each row segment is one contiguous block
+        // unpack the packed real pairs, scale by yh^q; each row segment is one contiguous block
         const int per_out = nkf * NI;
-        const int nrow = min(2, yend - y0);
+        const int nrow = min(rows_pp, yend - y0);
         if (nthr % NI == 0) {
             // every thread keeps one image and walks the bins (consecutive threads write
             // consecutive values), so no index is divided per value
             const int img = tid % NI, kstep = nthr / NI;
-            const bool odd = img & 1;
+            const int b = ob[img], q = oq[img];
+            const bool odd = b & 1;
             for (int rr = 0; rr < nrow; rr++) {
-                const cpx<R> *e = ex + (rr * g.nfft + (img >> 1)) * kEx;
-                cpx<R> *o = spec + ((size_t)s * ny + (y0 + rr)) * per_out + img;
+                const int y = y0 + rr;
+                const R yq = b < 0 ? (R)0 : (q == 0 ? (R)1 : ypow_g[(size_t)q * ny + y]);
+                const cpx<R> *e = ex + (rr * nbfft + (b < 0 ? 0 : b >> 1)) * kEx;
+                cpx<R> *o = spec + ((size_t)s * ny + y) * per_out + img;
+                const R hy = (R)0.5 * yq;
                 for (int k = tid / NI; k < nkf; k += kstep) {
                     const cpx<R> zk = e[k], zc = e[(kP - k) & (kP - 1)];
-                    o[(size_t)k * NI] = odd ? cpx<R>{(R)0.5 * (zk.im + zc.im), (R)0.5 * (zc.re - zk.re)}
-                                            : cpx<R>{(R)0.5 * (zk.re + zc.re), (R)0.5 * (zk.im - zc.im)};
+                    o[(size_t)k * NI] = odd ? cpx<R>{hy * (zk.im + zc.im), hy * (zc.re - zk.re)}
+                                            : cpx<R>{hy * (zk.re + zc.re), hy * (zk.im - zc.im)};
                 }
             }
         } else {
             for (int idx = tid; idx < nrow * per_out; idx += nthr) {
                 const int rr = idx / per_out, r2 = idx - rr * per_out;
                 const int k = r2 / NI, img = r2 - k * NI;
-                const cpx<R> *e = ex + (rr * g.nfft + (img >> 1)) * kEx;
+                const int b = ob[img], q = oq[img], y = y0 + rr;
+                const R yq = b < 0 ? (R)0 : (q == 0 ? (R)1 : ypow_g[(size_t)q * ny + y]);
+                const R hy = (R)0.5 * yq;
+                const cpx<R> *e = ex + (rr * nbfft + (b < 0 ? 0 : b >> 1)) * kEx;
                 cpx<R> zk = e[k], zc = e[(kP - k) & (kP - 1)];
                 cpx<R> out;
-                if ((img & 1) == 0)
-                    out = {(R)0.5 * (zk.re + zc.re), (R)0.5 * (zk.im - zc.im)};
+                if ((b & 1) == 0)
+                    out = {hy * (zk.re + zc.re), hy * (zk.im - zc.im)};
                 else
-                    out = {(R)0.5 * (zk.im + zc.im), (R)0.5 * (zc.re - zk.re)};
-                spec[((size_t)s * ny + (y0 + rr)) * per_out + r2] = out;
+                    out = {hy * (zk.im + zc.im), hy * (zc.re - zk.re)};
+                spec[((size_t)s * ny + y) * per_out + r2] = out;
             }
         }
         // the next pass's window (its FFT readers are past the barrier above)
@@ -334,29 +354,42 @@ __global__ void __launch_bounds__(128) k_segment_fft_single(const In *__restrict
     }
 }
 
+// rows per pass and threads: every base FFT of rows_pp rows (16 lanes each), at least
+// 256 threads so that kMaxPf positions per thread cover the rows_pp x P window
+struct SegLaunch {
+    int rows_pp, threads;
+};
+SegLaunch seg_launch(const Geometry &g) {
+    const int nbfft = (n_base(g.dk, g.db) + 1) / 2;
+    SegLaunch l;
+    l.rows_pp = std::max(1, std::min(kMaxRowsPP, 384 / (nbfft * 16)));
+    l.threads = std::max(256, (l.rows_pp * nbfft * 16 + 31) / 32 * 32);
+    return l;
+}
+
 template <class R>
-size_t segfft_smem(const Geometry &g) {
+size_t segfft_smem(const Geometry &g, int rows_pp) {
     const int maxdeg = g.dk > g.db ? g.dk : g.db;
-    return sizeof(cpx<R>) * (2 * kP + (size_t)2 * g.nfft * kEx) +
-           sizeof(R) * ((size_t)(maxdeg + 2) * kP + 6 * kP) + sizeof(int) * (3 * g.nimg_pad + kP);
+    const int nbfft = (n_base(g.dk, g.db) + 1) / 2;
+    return sizeof(cpx<R>) * (2 * kP + (size_t)rows_pp * nbfft * kEx) +
+           sizeof(R) * ((size_t)(maxdeg + 2) * kP + 3 * (size_t)rows_pp * kP) +
+           sizeof(int) * (4 * nbfft + 2 * g.nimg_pad + kP);
 }
 
 template <class R, class In>
 cudaError_t run(const Geometry &g, const void *sci, const void *tmpl, const uint8_t *mask, const void *tw,
                 const void *xpow, const void *ypow, void *spec, cudaStream_t st) {
-    size_t sm = segfft_smem<R>(g);
-    int threads = ((2 * g.nfft * 16 + 31) / 32) * 32;
-    if (threads < 128) threads = 128;
-    // up to 384 threads: register budget for two CTAs per SM; larger bases: one
-    auto kern = threads <= 384 ? k_segment_fft<R, In, 384, 2> : k_segment_fft<R, In, 512, 1>;
+    const SegLaunch l = seg_launch(g);
+    size_t sm = segfft_smem<R>(g, l.rows_pp);
+    auto kern = k_segment_fft<R, In, 384, 2>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return e;
     dim3 grid(g.nseg, (g.ny + kRowsPerCta - 1) / kRowsPerCta);
     note_launch();
-    kern<<<grid, threads, sm, st>>>((const In *)sci, (const In *)tmpl, mask, g, (const cpx<R> *)tw,
-                                    (const R *)xpow, (const R *)ypow, (cpx<R> *)spec);
+    kern<<<grid, l.threads, sm, st>>>((const In *)sci, (const In *)tmpl, mask, g, l.rows_pp, (const cpx<R> *)tw,
+                                      (const R *)xpow, (const R *)ypow, (cpx<R> *)spec);
     return cudaGetLastError();
 }
 
@@ -384,7 +417,7 @@ cudaError_t launch_segment_fft_single(const Geometry &g, int dtype, int precisio
 cudaError_t launch_segment_fft(const Geometry &g, int dtype, int precision, const void *sci, const void *tmpl,
                                const uint8_t *mask, const void *tw_fft, const void *xpow, const void *ypow,
                                void *spec, cudaStream_t st) {
-    if (g.P != kP || g.nfft > 16) return cudaErrorInvalidValue;
+    if (g.P != kP || n_base(g.dk, g.db) > 48) return cudaErrorInvalidValue;
     if (precision == SFFT_PREC_FP64) {
         return dtype == SFFT_F64 ? run<double, double>(g, sci, tmpl, mask, tw_fft, xpow, ypow, spec, st)
                                  : run<double, float>(g, sci, tmpl, mask, tw_fft, xpow, ypow, spec, st);
