@@ -186,10 +186,12 @@ __global__ void __launch_bounds__(MAXT, MINB) k_segment_fft(const In *__restrict
         const int y = ybase + (q >> 8);
         if (y < yend) {
             const size_t u = (size_t)y * g.pitch + wcol[q & (kP - 1)];
-            const bool bad = mask && mask[u];
-            // selects, not products: a masked pixel never enters, whatever value it holds
-            t_out = bad ? (R)0 : (R)tmpl[u];
-            s_out = bad ? (R)0 : (R)sci[u];
+            // all three loads issue together (none waits for the mask byte); then selects,
+            // not products: a masked pixel never enters, whatever value it holds
+            const In tr = tmpl[u], sr = sci[u];
+            const bool bad = mask ? mask[u] != 0 : false;
+            t_out = bad ? (R)0 : (R)tr;
+            s_out = bad ? (R)0 : (R)sr;
             m_out = bad ? (R)0 : (R)1;
         } else {
             t_out = s_out = m_out = (R)0;
