@@ -142,6 +142,7 @@ cudaError_t launch_segment_fft(const Geometry &g, int dtype, int precision, cons
                                const void *tmpl, const uint8_t *mask, const void *tw_fft, const void *xpow,
                                const void *ypow, void *spec, cudaStream_t st);
 // background moments (mask and masked science times monomials) -> mom_part
+int moments_ctas(const Geometry &g);  // CTAs (partial sums) of the moments kernel
 cudaError_t launch_moments(const Geometry &g, int dtype, int precision, const void *sci,
                            const uint8_t *mask, const void *ypow, double *mom_part, cudaStream_t st);
 // K1 for one image (the refinement residual) written into image slot `slot` of spec

@@ -25,103 +25,146 @@ __device__ __forceinline__ R coordv(int i, int n) {
 }
 
 constexpr int kMaxDB = 4;
+constexpr int kMaxMomRows = 128;  // rows of one moments CTA (the plan's mom_rows is at most this)
 
 // Column sums over a band of rows, folded into FP64 products with x powers, reduced per CTA.
-template <class R, class In>
-__global__ void __launch_bounds__(256) k_moments(const In *__restrict__ sci, const uint8_t *__restrict__ mask,
+// Each thread sums kMomCols adjacent columns; DB is a template parameter so that every loop
+// over the powers unrolls without guards.
+constexpr int kMomCols = 2;
+constexpr int kMomRowBatch = 8;
+template <class R, class In, int DB>
+__global__ void __launch_bounds__(256, 2) k_moments(const In *__restrict__ sci, const uint8_t *__restrict__ mask,
                                                 const R *__restrict__ ypow, Geometry g, double *__restrict__ part) {
+    constexpr int NB2 = 2 * DB + 1, NB1 = DB + 1;
     __shared__ double red[8][64];
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    // yh^b of the chunk's rows, b <= 2 DB (FP64 powers rounded once: the shared table)
+    __shared__ R yw[NB2][kMaxMomRows];
+    const int x0 = (blockIdx.x * blockDim.x + threadIdx.x) * kMomCols;
     const int ya = blockIdx.y * g.mom_rows, yb = min(g.ny, ya + g.mom_rows);
-    const int db2 = 2 * g.db;
-    // hi/lo column sums: cm[b] = sum m yh^b (b <= 2 db), cs[b] = sum m S yh^b (b <= db)
-    R cmh[2 * kMaxDB + 1], cml[2 * kMaxDB + 1], csh[kMaxDB + 1], csl[kMaxDB + 1];
-    R cma[2 * kMaxDB + 1], csa[kMaxDB + 1];
+    for (int e = threadIdx.x; e < NB2 * kMaxMomRows; e += blockDim.x) {
+        const int b = e / kMaxMomRows, r = e % kMaxMomRows;
+        yw[b][r] = ya + r < yb ? ypow[(size_t)b * g.ny + ya + r] : (R)0;
+    }
+    __syncthreads();
+    // hi/lo column sums: cm[b] = sum m yh^b (b <= 2 DB), cs[b] = sum m S yh^b (b <= DB)
+    R cmh[kMomCols][NB2], cml[kMomCols][NB2], csh[kMomCols][NB1], csl[kMomCols][NB1];
 #pragma unroll
-    for (int b = 0; b <= 2 * kMaxDB; b++) cmh[b] = cml[b] = cma[b] = (R)0;
+    for (int c = 0; c < kMomCols; c++) {
 #pragma unroll
-    for (int b = 0; b <= kMaxDB; b++) csh[b] = csl[b] = csa[b] = (R)0;
-    if (x < g.nx) {
-        int cnt = 0;
-        for (int y = ya; y < yb; y++) {
-            const size_t u = (size_t)y * g.pitch + x;
-            const bool bad = mask && mask[u];
-            const R m = bad ? (R)0 : (R)1;
-            const R sm = bad ? (R)0 : (R)sci[u];  // a masked pixel never enters, whatever it holds
+        for (int b = 0; b < NB2; b++) cmh[c][b] = cml[c][b] = (R)0;
 #pragma unroll
-            for (int b = 0; b <= 2 * kMaxDB; b++) {
-                if (b <= db2) {
-                    R w = ypow[(size_t)b * g.ny + y];  // FP64 power rounded once (shared table)
-                    cma[b] += m * w;
-                    if (b <= g.db) csa[b] += sm * w;
+        for (int b = 0; b < NB1; b++) csh[c][b] = csl[c][b] = (R)0;
+    }
+    bool colok[kMomCols];
+#pragma unroll
+    for (int c = 0; c < kMomCols; c++) colok[c] = x0 + c < g.nx;
+    if (colok[0]) {
+        // kMomRowBatch rows at a time: every load of the batch issues before the first is used
+        // (no load waits for a mask byte), then the sums run in row order and fold into hi + lo
+        for (int y0 = ya; y0 < yb; y0 += kMomRowBatch) {
+            const int nr = min(kMomRowBatch, yb - y0);
+            R mv[kMomRowBatch][kMomCols], sv[kMomRowBatch][kMomCols];
+#pragma unroll
+            for (int i = 0; i < kMomRowBatch; i++) {
+#pragma unroll
+                for (int c = 0; c < kMomCols; c++) {
+                    mv[i][c] = sv[i][c] = (R)0;
+                    if (i < nr && colok[c]) {
+                        const size_t u = (size_t)(y0 + i) * g.pitch + x0 + c;
+                        const In sr = sci[u];
+                        const bool bad = mask ? mask[u] != 0 : false;
+                        mv[i][c] = bad ? (R)0 : (R)1;
+                        sv[i][c] = bad ? (R)0 : (R)sr;  // a masked pixel never enters, whatever it holds
+                    }
                 }
             }
-            if (++cnt == 16 || y == yb - 1) {
-                cnt = 0;
+            R cma[kMomCols][NB2], csa[kMomCols][NB1];
 #pragma unroll
-                for (int b = 0; b <= 2 * kMaxDB; b++) {
+            for (int c = 0; c < kMomCols; c++) {
+#pragma unroll
+                for (int b = 0; b < NB2; b++) cma[c][b] = (R)0;
+#pragma unroll
+                for (int b = 0; b < NB1; b++) csa[c][b] = (R)0;
+            }
+#pragma unroll
+            for (int i = 0; i < kMomRowBatch; i++) {
+                // rows past the chunk hold m = S = 0 and weight 0: they add exact zeros
+#pragma unroll
+                for (int b = 0; b < NB2; b++) {
+                    const R w = yw[b][y0 - ya + i < kMaxMomRows ? y0 - ya + i : 0];
+#pragma unroll
+                    for (int c = 0; c < kMomCols; c++) {
+                        cma[c][b] += mv[i][c] * w;
+                        if (b < NB1) csa[c][b] += sv[i][c] * w;
+                    }
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < kMomCols; c++) {
+#pragma unroll
+                for (int b = 0; b < NB2; b++) {
                     if constexpr (sizeof(R) == 4) {
                         float s, e;
-                        two_sum(cmh[b], cma[b], s, e);
-                        cmh[b] = s;
-                        cml[b] += e;
+                        two_sum(cmh[c][b], cma[c][b], s, e);
+                        cmh[c][b] = s;
+                        cml[c][b] += e;
                     } else {
-                        cmh[b] += cma[b];
+                        cmh[c][b] += cma[c][b];
                     }
-                    cma[b] = (R)0;
                 }
 #pragma unroll
-                for (int b = 0; b <= kMaxDB; b++) {
+                for (int b = 0; b < NB1; b++) {
                     if constexpr (sizeof(R) == 4) {
                         float s, e;
-                        two_sum(csh[b], csa[b], s, e);
-                        csh[b] = s;
-                        csl[b] += e;
+                        two_sum(csh[c][b], csa[c][b], s, e);
+                        csh[c][b] = s;
+                        csl[c][b] += e;
                     } else {
-                        csh[b] += csa[b];
+                        csh[c][b] += csa[c][b];
                     }
-                    csa[b] = (R)0;
                 }
             }
         }
     }
-    const double xh = x < g.nx ? coordv<double>(x, g.nx) : 0.0;
+    double xh[kMomCols];
+#pragma unroll
+    for (int c = 0; c < kMomCols; c++) xh[c] = colok[c] ? coordv<double>(x0 + c, g.nx) : 0.0;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int nmask = npoly(db2);
-    for (int j = 0; j < g.nmom; j++) {
+    constexpr int nmask = (2 * DB + 1) * (2 * DB + 2) / 2;
+    constexpr int nmom = nmask + (DB + 1) * (DB + 2) / 2;
+#pragma unroll
+    for (int j = 0; j < nmom; j++) {
         int a, b;
         double v = 0.0;
-        if (x < g.nx) {
+        if (j < nmask) mono_pq(j, a, b);
+        else mono_pq(j - nmask, a, b);
+#pragma unroll
+        for (int c = 0; c < kMomCols; c++) {
+            if (!colok[c]) continue;
+            double cs = 0.0;
             if (j < nmask) {
-                mono_pq(j, a, b);
-                double cs = 0.0;
 #pragma unroll
-                for (int bb = 0; bb <= 2 * kMaxDB; bb++)
-                    if (bb == b) cs = (double)cmh[bb] + (double)cml[bb];
-                double xa = 1.0;
-                for (int e = 0; e < a; e++) xa *= xh;
-                v = xa * cs;
+                for (int bb = 0; bb < NB2; bb++)
+                    if (bb == b) cs = (double)cmh[c][bb] + (double)cml[c][bb];
             } else {
-                mono_pq(j - nmask, a, b);
-                double cs = 0.0;
 #pragma unroll
-                for (int bb = 0; bb <= kMaxDB; bb++)
-                    if (bb == b) cs = (double)csh[bb] + (double)csl[bb];
-                double xa = 1.0;
-                for (int e = 0; e < a; e++) xa *= xh;
-                v = xa * cs;
+                for (int bb = 0; bb < NB1; bb++)
+                    if (bb == b) cs = (double)csh[c][bb] + (double)csl[c][bb];
             }
+            double xa = 1.0;
+            for (int e = 0; e < a; e++) xa *= xh[c];
+            v += xa * cs;
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
         if (lane == 0) red[warp][j & 63] = v;
-        if ((j & 63) == 63 || j == g.nmom - 1) {
+        if ((j & 63) == 63 || j == nmom - 1) {
             __syncthreads();
             int jbase = j & ~63;
             for (int jj = threadIdx.x; jj <= (j & 63); jj += blockDim.x) {
                 double s = 0.0;
                 for (int w = 0; w < (int)(blockDim.x >> 5); w++) s += red[w][jj];
-                part[((size_t)blockIdx.y * gridDim.x + blockIdx.x) * g.nmom + jbase + jj] = s;
+                part[((size_t)blockIdx.y * gridDim.x + blockIdx.x) * nmom + jbase + jj] = s;
             }
             __syncthreads();
         }
@@ -285,22 +328,40 @@ __global__ void k_assemble(const double *__restrict__ lagww, const double *__res
 
 }  // namespace
 
-cudaError_t launch_moments(const Geometry &g, int dtype, int precision, const void *sci, const uint8_t *mask,
-                           const void *ypow, double *mom_part, cudaStream_t st) {
-    if (g.db > kMaxDB) return cudaErrorInvalidValue;
-    dim3 grid((g.nx + 255) / 256, (g.ny + g.mom_rows - 1) / g.mom_rows);
-    if (precision == SFFT_PREC_FP64) {
-        if (dtype == SFFT_F64)
-            { note_launch(); k_moments<double, double><<<grid, 256, 0, st>>>((const double *)sci, mask, (const double *)ypow, g, mom_part); }
-        else
-            { note_launch(); k_moments<double, float><<<grid, 256, 0, st>>>((const float *)sci, mask, (const double *)ypow, g, mom_part); }
-    } else {
-        if (dtype == SFFT_F64)
-            { note_launch(); k_moments<float, double><<<grid, 256, 0, st>>>((const double *)sci, mask, (const float *)ypow, g, mom_part); }
-        else
-            { note_launch(); k_moments<float, float><<<grid, 256, 0, st>>>((const float *)sci, mask, (const float *)ypow, g, mom_part); }
+int moments_ctas(const Geometry &g) {
+    return ((g.nx + 256 * kMomCols - 1) / (256 * kMomCols)) * ((g.ny + g.mom_rows - 1) / g.mom_rows);
+}
+
+namespace {
+
+template <class R, class In>
+cudaError_t launch_moments_t(const Geometry &g, const void *sci, const uint8_t *mask, const void *ypow,
+                             double *mom_part, cudaStream_t st) {
+    dim3 grid((g.nx + 256 * kMomCols - 1) / (256 * kMomCols), (g.ny + g.mom_rows - 1) / g.mom_rows);
+    const In *s = (const In *)sci;
+    const R *yp = (const R *)ypow;
+    note_launch();
+    switch (g.db) {
+        case 0: k_moments<R, In, 0><<<grid, 256, 0, st>>>(s, mask, yp, g, mom_part); break;
+        case 1: k_moments<R, In, 1><<<grid, 256, 0, st>>>(s, mask, yp, g, mom_part); break;
+        case 2: k_moments<R, In, 2><<<grid, 256, 0, st>>>(s, mask, yp, g, mom_part); break;
+        case 3: k_moments<R, In, 3><<<grid, 256, 0, st>>>(s, mask, yp, g, mom_part); break;
+        case 4: k_moments<R, In, 4><<<grid, 256, 0, st>>>(s, mask, yp, g, mom_part); break;
+        default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_moments(const Geometry &g, int dtype, int precision, const void *sci, const uint8_t *mask,
+                           const void *ypow, double *mom_part, cudaStream_t st) {
+    if (g.db > kMaxDB || g.mom_rows > kMaxMomRows) return cudaErrorInvalidValue;
+    if (precision == SFFT_PREC_FP64)
+        return dtype == SFFT_F64 ? launch_moments_t<double, double>(g, sci, mask, ypow, mom_part, st)
+                                 : launch_moments_t<double, float>(g, sci, mask, ypow, mom_part, st);
+    return dtype == SFFT_F64 ? launch_moments_t<float, double>(g, sci, mask, ypow, mom_part, st)
+                             : launch_moments_t<float, float>(g, sci, mask, ypow, mom_part, st);
 }
 
 cudaError_t launch_lag_tables(const Geometry &g, const double *ypart, double *ysum, const double *tw_x,

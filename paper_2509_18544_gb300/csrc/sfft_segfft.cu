@@ -218,6 +218,17 @@ __global__ void __launch_bounds__(MAXT, MINB) k_segment_fft(const In *__restrict
             int q = tid + c * nthr;
             if (more && q < npos) load_pos(c, y0 + rows_pp, pft[c], pfs[c], pfm[c]);
         }
+        // yh^q of this thread's unpacked image for the pass's rows, loaded before the FFTs
+        R yqv[kMaxRowsPP];
+        {
+            const int img = tid % NI, b = ob[img], q = oq[img];
+#pragma unroll
+            for (int rr = 0; rr < kMaxRowsPP; rr++) {
+                const int y = y0 + rr;
+                yqv[rr] = (b < 0 || rr >= rows_pp || y >= yend) ? (R)0
+                                                              : (q == 0 ? (R)1 : ypow_g[(size_t)q * ny + y]);
+            }
+        }
         // FFT lanes of this warp: each half-warp is one FFT of a row that exists
         auto half_active = [&](int base) {
             int rr = base / per_row;
@@ -266,14 +277,15 @@ __global__ void __launch_bounds__(MAXT, MINB) k_segment_fft(const In *__restrict
             // every thread keeps one image and walks the bins (consecutive threads write
             // consecutive values), so no index is divided per value
             const int img = tid % NI, kstep = nthr / NI;
-            const int b = ob[img], q = oq[img];
+            const int b = ob[img];
             const bool odd = b & 1;
-            for (int rr = 0; rr < nrow; rr++) {
+#pragma unroll
+            for (int rr = 0; rr < kMaxRowsPP; rr++) {
+                if (rr >= nrow) break;
                 const int y = y0 + rr;
-                const R yq = b < 0 ? (R)0 : (q == 0 ? (R)1 : ypow_g[(size_t)q * ny + y]);
                 const cpx<R> *e = ex + (rr * nbfft + (b < 0 ? 0 : b >> 1)) * kEx;
                 cpx<R> *o = spec + ((size_t)s * ny + y) * per_out + img;
-                const R hy = (R)0.5 * yq;
+                const R hy = (R)0.5 * yqv[rr];
                 for (int k = tid / NI; k < nkf; k += kstep) {
                     const cpx<R> zk = e[k], zc = e[(kP - k) & (kP - 1)];
                     o[(size_t)k * NI] = odd ? cpx<R>{hy * (zk.im + zc.im), hy * (zc.re - zk.re)}
