@@ -134,6 +134,7 @@ struct sfft_batch_s {
     std::vector<sfft_plan_t> plans;                // owned
     cudaEvent_t ev_fork = nullptr;
     std::vector<cudaEvent_t> ev_join;
+    std::vector<cudaEvent_t> ev_in;  // per lane: its first pair's host inputs are on the device
     double *rec = nullptr;                         // per pair: [status, flag0, flag1, scal0, scal1, scal2, -, -]
     cudaGraph_t graph_h = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -155,8 +156,10 @@ cudaError_t copy_frame(void *dst, const void *src, size_t pitch, size_t width, i
 // queue the whole batch: fork from `origin` into the lanes, run each lane's pairs, join
 cudaError_t queue_batch(sfft_batch_t b, sfft_status *st) {
     cudaError_t e = cudaEventRecord(b->ev_fork, b->origin);
+    int prev_in = -1;  // last lane whose first pair copied host inputs
     for (int l = 0; l < b->lanes && e == cudaSuccess; l++) {
         e = cudaStreamWaitEvent(b->ls[l], b->ev_fork, 0);
+        bool first = true;
         for (int pi : b->lane_pairs[l]) {
             if (e != cudaSuccess) break;
             const sfft_pair &q = b->pairs[pi];
@@ -164,7 +167,11 @@ cudaError_t queue_batch(sfft_batch_t b, sfft_status *st) {
             const size_t elt = b->base.dtype == SFFT_F64 ? 8 : 4;
             const size_t pitch = q.pitch ? q.pitch : q.nx;
             if (q.sci_host) {  // this pair's inputs, on its own lane
-                e = copy_frame(const_cast<void *>(q.sci), q.sci_host, pitch * elt, q.nx * elt, q.ny,
+                // the lanes' first input copies go one after another, so that the first lane
+                // starts computing after one pair's transfer instead of after all of them
+                if (first && prev_in >= 0) e = cudaStreamWaitEvent(b->ls[l], b->ev_in[prev_in], 0);
+                if (e == cudaSuccess)
+                    e = copy_frame(const_cast<void *>(q.sci), q.sci_host, pitch * elt, q.nx * elt, q.ny,
                                cudaMemcpyHostToDevice, b->ls[l]);
                 if (e == cudaSuccess && q.tmpl_host)
                     e = copy_frame(const_cast<void *>(q.tmpl), q.tmpl_host, pitch * elt, q.nx * elt, q.ny,
@@ -172,8 +179,13 @@ cudaError_t queue_batch(sfft_batch_t b, sfft_status *st) {
                 if (e == cudaSuccess && q.mask && q.mask_host)
                     e = copy_frame(const_cast<uint8_t *>(q.mask), q.mask_host, pitch, q.nx, q.ny, cudaMemcpyHostToDevice,
                                    b->ls[l]);
+                if (e == cudaSuccess && first) {
+                    e = cudaEventRecord(b->ev_in[l], b->ls[l]);
+                    prev_in = l;
+                }
                 if (e != cudaSuccess) break;
             }
+            first = false;
             sfft_status s = sfft_fit(p, q.sci, q.tmpl, q.mask, q.x0, q.coeffs, nullptr);
             if (s == SFFT_OK) s = sfft_subtract(p, q.sci, q.tmpl, q.coeffs, q.diff);
             if (s != SFFT_OK) {
@@ -212,6 +224,8 @@ void free_batch(sfft_batch_t b) {
     if (b->origin) cudaStreamDestroy(b->origin);
     if (b->ev_fork) cudaEventDestroy(b->ev_fork);
     for (cudaEvent_t ev : b->ev_join)
+        if (ev) cudaEventDestroy(ev);
+    for (cudaEvent_t ev : b->ev_in)
         if (ev) cudaEventDestroy(ev);
     if (b->rec) cudaFree(b->rec);
     delete b;
@@ -417,9 +431,11 @@ sfft_status sfft_batch_create(sfft_batch_t *out, const sfft_desc *base, const sf
     cudaError_t e = cudaStreamCreateWithFlags(&b->origin, cudaStreamNonBlocking);
     b->ls.assign(b->lanes, nullptr);
     b->ev_join.assign(b->lanes, nullptr);
+    b->ev_in.assign(b->lanes, nullptr);
     for (int l = 0; l < b->lanes && e == cudaSuccess; l++) {
         e = cudaStreamCreateWithFlags(&b->ls[l], cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_join[l], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_in[l], cudaEventDisableTiming);
     }
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaMalloc(&b->rec, sizeof(double) * kRec * npairs);
