@@ -282,6 +282,14 @@ sfft_status sfft_cnn_train(sfft_cnn_t cnn, const float *stamps, const float *tar
 /* Warm starts for sfft_fit: x0[b n_stride + j] = output j of sample b (j < n_out), 0 for
  * the remaining n_stride - n_out unknowns (the background). */
 sfft_status sfft_cnn_warm_start(sfft_cnn_t cnn, const float *stamps, int32_t batch, int32_t n_stride, double *x0);
+/* Parameters to and from a file (a trained network kept between runs): an 8-byte tag
+ * "SFFTCNN1", int32 n_out, int32 0, int64 param_count, then param_count floats, all in the
+ * host's byte order (little-endian on x86-64 and AArch64).  Load reads the whole file, checks
+ * tag, n_out and count against this network and returns SFFT_ERR_INVALID_ARG on a mismatch,
+ * a short or unreadable file; on success it replaces the parameters and resets the Adam
+ * state like sfft_cnn_set_params.  Both synchronise the network's stream. */
+sfft_status sfft_cnn_save(sfft_cnn_t cnn, const char *path);
+sfft_status sfft_cnn_load(sfft_cnn_t cnn, const char *path);
 const char *sfft_cnn_last_error(sfft_cnn_t cnn);
 
 /* Stage timing (instrumentation; the paper profiles its pipeline stage by stage, Sec. "GPU

@@ -439,6 +439,51 @@ sfft_status sfft_cnn_get_params(sfft_cnn_t c, float *params) {
     return SFFT_OK;
 }
 
+static const char kCnnTag[8] = {'S', 'F', 'F', 'T', 'C', 'N', 'N', '1'};
+
+sfft_status sfft_cnn_save(sfft_cnn_t c, const char *path) {
+    if (!c || !path) return cnn_err(c, SFFT_ERR_INVALID_ARG, "null argument");
+    const int64_t P = (int64_t)c->lay.total;
+    std::vector<float> h((size_t)P);
+    sfft_status s = sfft_cnn_get_params(c, h.data());
+    if (s != SFFT_OK) return s;
+    FILE *f = fopen(path, "wb");
+    if (!f) return cnn_err(c, SFFT_ERR_INVALID_ARG, "save: cannot open the file for writing");
+    const int32_t hdr[2] = {c->n_out, 0};
+    bool ok = fwrite(kCnnTag, 1, 8, f) == 8 && fwrite(hdr, sizeof hdr, 1, f) == 1 && fwrite(&P, sizeof P, 1, f) == 1 &&
+              fwrite(h.data(), sizeof(float), (size_t)P, f) == (size_t)P;
+    ok = (fclose(f) == 0) && ok;
+    if (!ok) return cnn_err(c, SFFT_ERR_INVALID_ARG, "save: write failed");
+    return SFFT_OK;
+}
+
+sfft_status sfft_cnn_load(sfft_cnn_t c, const char *path) {
+    if (!c || !path) return cnn_err(c, SFFT_ERR_INVALID_ARG, "null argument");
+    FILE *f = fopen(path, "rb");
+    if (!f) return cnn_err(c, SFFT_ERR_INVALID_ARG, "load: cannot open the file");
+    char tag[8];
+    int32_t hdr[2];
+    int64_t P = 0;
+    const int64_t want = (int64_t)c->lay.total;
+    bool ok = fread(tag, 1, 8, f) == 8 && memcmp(tag, kCnnTag, 8) == 0 && fread(hdr, sizeof hdr, 1, f) == 1 &&
+              fread(&P, sizeof P, 1, f) == 1;
+    if (!ok) {
+        fclose(f);
+        return cnn_err(c, SFFT_ERR_INVALID_ARG, "load: not a network file");
+    }
+    if (hdr[0] != c->n_out || P != want) {
+        fclose(f);
+        return cnn_err(c, SFFT_ERR_INVALID_ARG, "load: the file's output width or parameter count differs");
+    }
+    std::vector<float> h((size_t)P);
+    ok = fread(h.data(), sizeof(float), (size_t)P, f) == (size_t)P;
+    char extra;
+    ok = ok && fread(&extra, 1, 1, f) == 0;  // nothing after the parameters
+    fclose(f);
+    if (!ok) return cnn_err(c, SFFT_ERR_INVALID_ARG, "load: short or oversized file");
+    return sfft_cnn_set_params(c, h.data());
+}
+
 sfft_status sfft_cnn_forward(sfft_cnn_t c, const float *stamps, int32_t batch, float *out) {
     sfft_status s = check_batch(c, batch);
     if (s != SFFT_OK) return s;

@@ -27,7 +27,7 @@ EXPORTED = ("sfft_plan", "sfft_destroy", "sfft_n_unknowns", "sfft_workspace_size
             "sfft_status_string", "sfft_last_error",
             "sfft_cnn_create", "sfft_cnn_destroy", "sfft_cnn_param_count", "sfft_cnn_set_params",
             "sfft_cnn_get_params", "sfft_cnn_forward", "sfft_cnn_gradients", "sfft_cnn_train_step",
-            "sfft_cnn_train", "sfft_cnn_warm_start", "sfft_cnn_last_error")
+            "sfft_cnn_train", "sfft_cnn_warm_start", "sfft_cnn_save", "sfft_cnn_load", "sfft_cnn_last_error")
 NSTAGES = 8
 STAGES = ("segment_fft", "moments", "ycorr", "lag_tables", "assemble", "solve", "subtract", "refine")
 
@@ -127,6 +127,8 @@ def load_library(path: str = LIB_PATH):
         lib.sfft_cnn_train.argtypes = [P, P, P, I32, I32, I32, ctypes.c_float, ctypes.c_uint64,
                                        ctypes.POINTER(ctypes.c_float)]
         lib.sfft_cnn_warm_start.argtypes = [P, P, I32, I32, P]
+        lib.sfft_cnn_save.argtypes = [P, ctypes.c_char_p]
+        lib.sfft_cnn_load.argtypes = [P, ctypes.c_char_p]
         lib.sfft_cnn_last_error.argtypes = [P]
         lib.sfft_cnn_last_error.restype = ctypes.c_char_p
         for name in EXPORTED:
@@ -428,6 +430,16 @@ def sfft_cnn_set_params(cnn: Cnn, params):
 
 def sfft_cnn_get_params(cnn: Cnn, params):
     _check_cnn(load_library().sfft_cnn_get_params(cnn.handle, _ptr(params)), cnn.handle)
+
+
+def sfft_cnn_save(cnn: Cnn, path: str):
+    """Write the network's parameters to a file (see sfft_cnn_save in include/sfft.h)."""
+    _check_cnn(load_library().sfft_cnn_save(cnn.handle, os.fsencode(path)), cnn.handle)
+
+
+def sfft_cnn_load(cnn: Cnn, path: str):
+    """Replace the parameters with a file written by sfft_cnn_save for the same output width."""
+    _check_cnn(load_library().sfft_cnn_load(cnn.handle, os.fsencode(path)), cnn.handle)
 
 
 def sfft_cnn_forward(cnn: Cnn, stamps, batch: int, out):

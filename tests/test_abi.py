@@ -68,3 +68,9 @@ def test_null_arguments_rejected_without_gpu(lib):
     assert lib.sfft_fit(None, None, None, None, None, None, None) == sfft.ERR_INVALID_ARG
     assert lib.sfft_subtract(None, None, None, None, None) == sfft.ERR_INVALID_ARG
     lib.sfft_destroy(None)
+
+
+def test_cnn_file_calls_reject_null_arguments_without_gpu(lib):
+    assert lib.sfft_cnn_save(None, b"/nonexistent") == sfft.ERR_INVALID_ARG
+    assert lib.sfft_cnn_load(None, b"/nonexistent") == sfft.ERR_INVALID_ARG
+    lib.sfft_cnn_destroy(None)

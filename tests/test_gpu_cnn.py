@@ -163,3 +163,37 @@ def test_trained_network_gains_the_pcg_solve():
     assert info["cold"].start_residual == 1.0
     assert info["cnn"].start_residual < 0.25
     assert info["cnn"].iterations <= info["cold"].iterations
+
+
+def test_save_and_load_round_trip(tmp_path):
+    """A saved network loads into a fresh one with the same outputs; a file for another
+    output width, a truncated file or a foreign file is rejected."""
+    n_out, batch = 37, 3
+    p, x, _ = _case(n_out, batch, seed=8)
+    path = str(tmp_path / "net.bin")
+    xs = torch.from_numpy(x).to(DEV)
+    with _net(n_out, batch, p) as a:
+        sfft.sfft_cnn_save(a, path)
+        out_a = torch.empty((batch, n_out), dtype=torch.float32, device=DEV)
+        sfft.sfft_cnn_forward(a, xs, batch, out_a)
+    with sfft.sfft_cnn_create(n_out, batch) as b:
+        sfft.sfft_cnn_load(b, path)
+        got = torch.empty(C.param_count(n_out), dtype=torch.float32, device=DEV)
+        sfft.sfft_cnn_get_params(b, got)
+        out_b = torch.empty((batch, n_out), dtype=torch.float32, device=DEV)
+        sfft.sfft_cnn_forward(b, xs, batch, out_b)
+        torch.cuda.synchronize()
+        assert torch.equal(got.cpu(), torch.from_numpy(p))
+        assert torch.equal(out_a, out_b)
+    with sfft.sfft_cnn_create(n_out + 1, batch) as c:
+        with pytest.raises(sfft.SfftError):
+            sfft.sfft_cnn_load(c, path)
+    raw = open(path, "rb").read()
+    short = str(tmp_path / "short.bin")
+    open(short, "wb").write(raw[:-4])
+    foreign = str(tmp_path / "foreign.bin")
+    open(foreign, "wb").write(b"NOTANNET" + raw[8:])
+    with sfft.sfft_cnn_create(n_out, batch) as d:
+        for bad in (short, foreign, str(tmp_path / "missing.bin")):
+            with pytest.raises(sfft.SfftError):
+                sfft.sfft_cnn_load(d, bad)
