@@ -194,12 +194,25 @@ __global__ void k_ysum(const double2 *__restrict__ ypart, Geometry g, bool pairs
     size_t total = (size_t)g.nkf * g.nent;
     if (idx >= total) return;
     double2 s = make_double2(0.0, 0.0);
-    for (int sg = 0; sg < g.nseg * g.ysplit; sg++) {
-        if (pairs) {
-            float4 v = reinterpret_cast<const float4 *>(ypart)[(size_t)sg * total + idx];
-            s.x += (double)v.x + (double)v.z;
-            s.y += (double)v.y + (double)v.w;
-        } else {
+    const int nsg = g.nseg * g.ysplit;
+    if (pairs) {
+        // (hi, lo) FP32 partials summed as a double-float: the high parts by error-free
+        // two-sums, the low parts and the errors in FP32 (their rounding is ~u^2 of the sum);
+        // one conversion to FP64 at the end (FP64 adds run at 1/64 of the FP32 rate)
+        float hx = 0.f, lx = 0.f, hy = 0.f, ly = 0.f;
+        for (int sg = 0; sg < nsg; sg++) {
+            const float4 v = reinterpret_cast<const float4 *>(ypart)[(size_t)sg * total + idx];
+            float t, e;
+            two_sum(hx, v.x, t, e);
+            hx = t;
+            lx += e + v.z;
+            two_sum(hy, v.y, t, e);
+            hy = t;
+            ly += e + v.w;
+        }
+        s = make_double2((double)hx + (double)lx, (double)hy + (double)ly);
+    } else {
+        for (int sg = 0; sg < nsg; sg++) {
             double2 v = ypart[(size_t)sg * total + idx];
             s.x += v.x;
             s.y += v.y;
@@ -219,12 +232,19 @@ __global__ void __launch_bounds__(256) k_ysum_ws(const float4 *__restrict__ wspa
     const size_t per = (size_t)g.nkf * g.nk * L;
     if (idx >= per) return;  // whole warps leave together
     const int nsy = g.nseg * g.ychunks_ws;
-    double sx = 0.0, syv = 0.0;
+    // each lane sums its partials as a double-float (see k_ysum), then one FP64 value per lane
+    float hx = 0.f, lx = 0.f, hy = 0.f, ly = 0.f;
     for (int sy = lane; sy < nsy; sy += 32) {
         const float4 v = wspart[(size_t)sy * per + idx];
-        sx += (double)v.x + (double)v.z;
-        syv += (double)v.y + (double)v.w;
+        float t, e;
+        two_sum(hx, v.x, t, e);
+        hx = t;
+        lx += e + v.z;
+        two_sum(hy, v.y, t, e);
+        hy = t;
+        ly += e + v.w;
     }
+    double sx = (double)hx + (double)lx, syv = (double)hy + (double)ly;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         sx += __shfl_xor_sync(0xffffffffu, sx, o);
@@ -242,10 +262,12 @@ __global__ void k_lagx(const double2 *__restrict__ ysum, const double2 *__restri
     const int L = g.L, h = g.h, Lw = 2 * L - 1, G = g.G;
     const int nww = g.npair * Lw * Lw;
     const int nrest = g.nk * (g.nb + 1) * L * L;
-    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    // one warp per output: the lanes take interleaved bins, a fixed shuffle tree adds them
+    int t = (int)(((size_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
     if (ws_only) {
-        // thread -> (i, dyi, dxi) of the W_i x S_m table, mapped into the full numbering
-        if (t >= g.nk * L * L) return;
+        // warp -> (i, dyi, dxi) of the W_i x S_m table, mapped into the full numbering
+        if (t >= g.nk * L * L) return;  // whole warps leave together
         int i = t / (L * L), l = t - i * L * L;
         t = nww + ((i * (g.nb + 1) + g.nb) * L * L) + l;
     }
@@ -272,13 +294,15 @@ __global__ void k_lagx(const double2 *__restrict__ ysum, const double2 *__restri
     const int m = G + dx;
     const int W = 2 * G + 1;
     double acc = 0.0;
-    for (int k = 0; k < g.nkf; k++) {
+    for (int k = lane; k < g.nkf; k += 32) {
         double2 y = ysum[(size_t)k * g.nent + ent];
         double2 w = tw_x[(size_t)k * W + m];
         acc = fma(y.x, w.x, acc);
         acc = fma(-y.y, w.y, acc);
     }
-    *out = acc;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) *out = acc;
 }
 
 __global__ void k_assemble(const double *__restrict__ lagww, const double *__restrict__ lagwg,
@@ -377,7 +401,7 @@ cudaError_t launch_lag_tables(const Geometry &g, const double *ypart, double *ys
     }
     int nout = ws_only ? g.nk * g.L * g.L : g.npair * (2 * g.L - 1) * (2 * g.L - 1) + g.nk * (g.nb + 1) * g.L * g.L;
     note_launch();
-    k_lagx<<<(nout + 127) / 128, 128, 0, st>>>((const double2 *)ysum, (const double2 *)tw_x, g, ws_only, lagww,
+    k_lagx<<<(unsigned)(((size_t)nout * 32 + 255) / 256), 256, 0, st>>>((const double2 *)ysum, (const double2 *)tw_x, g, ws_only, lagww,
                                                lagwg, lagws);
     if (mom_part) {  // the refinement of the FP32 path reduces its moments elsewhere
         note_launch();
