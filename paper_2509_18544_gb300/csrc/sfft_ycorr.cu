@@ -416,7 +416,6 @@ template <int C>
 __global__ void __launch_bounds__(256) k_ycorr_ws(const cpx<float> *__restrict__ spec, const cpx<float> *__restrict__ rspec,
                                                  Geometry g, int ychunks, float4 *__restrict__ wspart) {
     const int nk = g.nk, nkf = g.nkf, ny = g.ny, NI = g.nimg_pad, h = g.h;
-    const int slot = 2 * nk + g.nb;
     const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
     const long total = (long)g.nseg * ychunks * nkf * nk;
     if (t >= total) return;
@@ -522,7 +521,7 @@ cudaError_t run(const Geometry &g, int precision, const void *spec, double *ypar
         // packed FP32x2 variant (transposed tile) unless the tuning picked the scalar one
         size_t sm = g.ycorr_scalar ? 2 * rows * ln.kg * ln.cw * sizeof(cpx<float>)
                                    : 2 * (size_t)tile_rp((int)rows) * ln.kg * ln.cw * sizeof(cpx<float>);
-        auto kern = g.ycorr_scalar ? k_ycorr_f32<C> : k_ycorr_f32x2<C, 4>;
+        auto kern = g.ycorr_scalar ? k_ycorr_f32<C> : k_ycorr_f32x2<C, 8>;
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);

@@ -19,6 +19,10 @@ Tolerances:
     |N_gpu - N_ref|_ij <= tol sqrt(N_ii N_jj) with tol = 5e-7 for the FP32 path (random
     rounding of the FP32 segment FFTs, ~ u sqrt(log2 P) per spectral value, averaged by the
     lag sums; the systematic twiddle bias is removed by split twiddles), 1e-12 for FP64.
+    The kernel x background block gets 2e-6: the background images m xh^p yh^q are smooth,
+    so their spectra sit in a few large low-frequency bins whose FP32 rounding does not
+    average out over the lag sums, and the more so the higher the degree (measured 2.8e-7
+    at DB = 2, 7.8e-7 at DB = 4, with the coefficients still within 3e-7).
 """
 import numpy as np
 import pytest
@@ -90,6 +94,7 @@ CASES = [
     (40, 500, 1, 0, 0, True, np.float32),     # L = 1, 3 segments
     (96, 244, 7, 3, 1, True, np.float32),     # nx == U for L = 7: exactly one segment
     (66, 300, 15, 1, 0, False, np.float32),   # largest supported L
+    (128, 200, 5, 1, 4, True, np.float32),    # largest background degree, odd nP(DK)
 ]
 
 
@@ -106,8 +111,14 @@ def test_normal_equations_match_oracle(ny, nx, L, dk, db, masked, dtype):
     N_ref, b_ref = oracle.normal_equations(S, T, M, L, dk, db)
     N, b = gpu_normal(S, T, M, L, dk, db)
     e_n, e_b = scaled_err(N, N_ref), rhs_err(b, b_ref, N_ref) / np.sqrt(np.sum((S.astype(np.float64) * (1 - (M if M is not None else 0))) ** 2))
-    print("N scaled err %.3e  b err %.3e" % (e_n, e_b))
-    assert e_n <= 5e-7
+    nker = L * L * (dk + 1) * (dk + 2) // 2
+    d = np.sqrt(np.abs(np.diag(N_ref)))
+    E = np.abs(N - N_ref) / np.outer(d, d)
+    e_kk, e_kb, e_bb = E[:nker, :nker].max(), E[:nker, nker:].max(), E[nker:, nker:].max()
+    print("N scaled err %.3e (kernel x kernel %.3e, kernel x background %.3e, background %.3e)  b err %.3e" % (
+        e_n, e_kk, e_kb, e_bb, e_b))
+    assert e_kk <= 5e-7 and e_bb <= 5e-7
+    assert e_kb <= 2e-6
     assert e_b <= 5e-7
     assert np.array_equal(N, N.T)
 
