@@ -305,7 +305,7 @@ def run_ours(args, world, rank, local):
     # DRAM bytes of one launch (dram__bytes_read.sum + dram__bytes_write.sum) from an ncu capture of
     # this kernel, unchanged since, on a 2048^2 pair: 439 MB, scaled to the frame by its pixel count
     # (the spectra it reads grow in proportion)
-    traffic = 439.4e6 * (NY * NX) / (2048.0 * 2048.0)
+    traffic = 439.0e6 * (NY * NX) / (2048.0 * 2048.0)
     roofline = {"bound": "alu", "kernel": "k_ycorr_f32x2 (y-direction lag correlation)",
                 "achieved": round(achieved_tflops, 3), "peak": round(fp32_peak, 2), "unit": "TFLOP/s",
                 "frac": round(achieved_tflops / fp32_peak, 4), "traffic": round(traffic),
