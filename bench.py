@@ -42,7 +42,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--pairs", type=int, default=4, help="pairs per step per rank")
+    ap.add_argument("--pairs", type=int, default=8, help="pairs per step per rank")
+    ap.add_argument("--lanes", type=int, default=8, help="streams of the batched form (at most --pairs)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--train-samples", type=int, default=2048, help="warm-start network training fits")
     ap.add_argument("--frame", type=int, default=NY, help="frame side (smaller frames are for profiling runs)")
@@ -243,7 +244,7 @@ def run_ours(args, world, rank, local):
         sfft.sfft_tuning_set(sfft.make_desc(NY, NX, L, DK, DB, solver=sfft.SOLVE_PCG), tn)
     t0 = time.perf_counter()
     batch = sfft.sfft_batch_create(sfft.make_desc(NY, NX, L, DK, DB, solver=sfft.SOLVE_PCG), bpairs,
-                                   lanes=min(args.pairs, 4), flags=sfft.BATCH_GRAPH | sfft.BATCH_AUTOTUNE,
+                                   lanes=min(args.pairs, args.lanes), flags=sfft.BATCH_GRAPH | sfft.BATCH_AUTOTUNE,
                                    stream=stream)
     create_s = time.perf_counter() - t0
     tuning, _ = sfft.sfft_tuning_get(sfft.make_desc(NY, NX, L, DK, DB, solver=sfft.SOLVE_PCG))
@@ -276,7 +277,7 @@ def run_ours(args, world, rank, local):
     e2e_pairs = [sfft.make_pair(dS, dT, dM, th, D, NY, NX, x0=x0[k], host=host[k])
                  for k, ((dS, dT, dM), th, D) in enumerate(zip(e2e_in, e2e_th, e2e_D))]
     e2e_batch = sfft.sfft_batch_create(sfft.make_desc(NY, NX, L, DK, DB, solver=sfft.SOLVE_PCG), e2e_pairs,
-                                       lanes=min(args.pairs, 4), flags=sfft.BATCH_GRAPH, stream=stream)
+                                       lanes=min(args.pairs, args.lanes), flags=sfft.BATCH_GRAPH, stream=stream)
 
     def e2e_step():
         sfft.sfft_cnn_warm_start(cnn, stamps, args.pairs, n, x0)
@@ -325,7 +326,7 @@ def run_ours(args, world, rank, local):
                    "pairs_per_step_per_rank": args.pairs,
                    "mode": "batched+learned: CNN warm starts, %d-lane CUDA-graph batch, autotuned, cluster PCG "
                            "(FP32 Cholesky preconditioner, FP64 residuals), FP32 spectra, one compensated "
-                           "refinement pass" % min(args.pairs, 4),
+                           "refinement pass" % min(args.pairs, args.lanes),
                    "l2": "inputs larger than L2 (150 MB frames + 1.5 GB spectra per pair); no flush",
                    "parallelism": "replicas: independent pairs per GPU" if world > 1 else "1 GPU"},
         "plain": {"value": round(plain_value, 3), "ms_per_step": round(plain_ms / args.steps, 3),
