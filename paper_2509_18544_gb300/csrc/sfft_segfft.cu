@@ -96,7 +96,7 @@ __device__ __forceinline__ void fft256(cpx<R> (&v)[16], int t, cpx<R> *e, const 
     __syncwarp(msk);
 }
 
-constexpr int kRowsPerCta = 16;
+constexpr int kRowsPerCta = 32;
 constexpr int kMaxRowsPP = 4;  // rows transformed per pass
 // exchange buffer per FFT: 16 x 17 (padded transpose) + 1, so that buffers of consecutive
 // FFTs start two banks apart instead of on the same bank
