@@ -82,8 +82,7 @@ bool make_geometry(const sfft_desc &d, Geometry &g, char *err, size_t errlen) {
     g.nkf = g.P / 2 + 1;
     g.nimg = 2 * g.nk + g.nb + 1;
     g.nimg_pad = (g.nimg + 1) & ~1;
-    g.nfft = g.nimg_pad / 2;
-    if (g.nfft > 16) return snprintf(err, errlen, "dk=%d, db=%d give %d images per segment (max 32)", d.dk, d.db, g.nimg), false;
+    if (g.nimg_pad > 32) return snprintf(err, errlen, "dk=%d, db=%d give %d images per segment (max 32)", d.dk, d.db, g.nimg), false;
     g.npair = g.nk * (g.nk + 1) / 2;
     g.nent = g.npair * (2 * d.L - 1) + g.nk * (g.nb + 1) * d.L;
     g.C = d.L;

@@ -46,7 +46,7 @@ struct Geometry {
     int ny, nx, pitch, L, h, dk, db;
     int nk, nb, nker, n;       // monomials of kernel / background, unknowns
     int P, U, G, nseg, nkf;    // segment FFT length, useful length, halo, segments, half-spectrum bins
-    int nimg, nimg_pad, nfft;  // real images per segment row (A then B), padded to even, complex FFTs
+    int nimg, nimg_pad;        // spectra per segment row (A then B images), padded to even
     int npair, nent;           // W-W pairs (i <= j), (pair, dy) entries per frequency
     int C, items_per_k, kg;    // y-correlation: dy chunk, work items per frequency, frequencies per CTA
     int kg_ws;                 // frequencies per CTA when only the W x S_m items run (refinement)
