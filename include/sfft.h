@@ -76,7 +76,11 @@ typedef struct {
                               residual (coefficients within ~1e-6 of the FP64 answer);
                               SFFT_PREC_FP32: the same kernels without refinement (faster,
                               ~1e-6 .. 4e-5); SFFT_PREC_FP64: FP64 throughout */
-    int32_t solver;        /* SFFT_SOLVE_CHOLESKY (FP64 Cholesky + one refinement step) */
+    int32_t solver;        /* SFFT_SOLVE_CHOLESKY (FP64 Cholesky + one refinement step) or
+                              SFFT_SOLVE_PCG (PCG in one thread-block cluster: FP32 Cholesky
+                              preconditioner of the Jacobi-scaled N, FP64 residuals, warm start
+                              from x0; falls back to the FP64 Cholesky on the device when it
+                              does not converge or a pivot fails) */
     int32_t max_iter;      /* PCG iteration cap (0 = default) */
     double tol;            /* PCG relative-residual tolerance (0 = default 1e-12) */
     size_t workspace_cap;  /* bytes the plan may allocate; 0 = no cap */
