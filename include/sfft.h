@@ -90,7 +90,12 @@ typedef struct {
                               A pass forms the residual image of the fit on the masked frames,
                               correlates it with the basis through the same segment spectra,
                               and corrects theta with the existing factorisation. */
-    int32_t reserved[6];   /* zero */
+    int32_t spin_limit;    /* iteration limit of every bounded device-side wait (the grid
+                              barrier of the cooperative FP64 Cholesky): each iteration sleeps
+                              ~64 ns, and on expiry the kernel records SFFT_ERR_TIMEOUT in the
+                              plan's status word and returns instead of waiting on; 0 = default
+                              2^24 (about a second), > 0 = that many iterations */
+    int32_t reserved[5];   /* zero */
 } sfft_desc;
 
 typedef struct {
@@ -101,7 +106,14 @@ typedef struct {
     double rel_residual;   /* ||b - N theta||_2 / ||b||_2 after the last step */
     double start_residual; /* ||b - N x||_2 / ||b||_2 at PCG's starting point (after the warm
                               start's projection); 1 for Cholesky and for a fallback */
-    double reserved[2];
+    int32_t pcg_status;    /* SFFT_SOLVE_PCG only: SFFT_OK when PCG met the tolerance,
+                              SFFT_ERR_NO_CONVERGENCE when it stopped at max_iter,
+                              SFFT_ERR_NOT_SPD when its FP32 preconditioner met a non-positive
+                              pivot or a search direction lost positive curvature; in the two
+                              error cases the FP64 Cholesky fallback produced the coefficients
+                              and `status` is that solve's outcome.  SFFT_OK for Cholesky. */
+    int32_t reserved_i;
+    double reserved[1];
 } sfft_fit_info;
 
 /* Create a plan for one frame geometry and basis.  Validates the descriptor, chooses the
@@ -232,14 +244,19 @@ sfft_status sfft_tuning_load(const char *path);
  * sci, tmpl, coeffs (n doubles) and diff are device pointers as for sfft_subtract, with
  * pitch = desc->pitch (0 = nx), queued on `stream`.  The scratch -- the coordinate-power
  * table and the folded kernel coefficients, (max(dk,db)+1) nx + ny (L^2 (dk+1) + db + 1)
- * values of 4 bytes (8 for SFFT_PREC_FP64) -- lives in one fixed 16 MiB device array that
- * every GPU which loads the library holds until the process exits; a frame that needs more
- * is rejected with SFFT_ERR_INVALID_ARG (message in sfft_last_error(NULL)).  The first call
+ * values of 4 bytes (8 for SFFT_PREC_FP64) -- lives in one fixed 16 MiB device array.  The
+ * array is created on a device when the library's kernels are first loaded there (with
+ * CUDA's lazy module loading that can be during the first call of this entry point, or of
+ * any other libsfft call) and stays until the process exits; a frame that needs more is
+ * rejected with SFFT_ERR_INVALID_ARG (message in sfft_last_error(NULL)).  The first call
  * on each device looks up that array's device address (cudaGetSymbolAddress, once per
- * device, with the device current); make that first call before any stream capture.  All
- * calls share the array and each call overwrites everything it reads, so nothing carries
- * over from the previous call, but calls that overlap on the GPU (different streams,
- * or different host threads on one device) race on it and must be serialised. */
+ * device, with the device current) and keeps it; make that first call (a warm-up call is
+ * enough) before any stream capture or latency-critical use.  The kept address belongs to
+ * the device's primary context: after cudaDeviceReset it is stale, so do not use this
+ * entry point on a device that this process has reset.  All calls share the array and
+ * each call overwrites everything it reads, so nothing carries over from the previous
+ * call, but calls that overlap on the GPU (different streams, or different host threads
+ * on one device) race on it and must be serialised. */
 sfft_status sfft_subtract_noalloc(const sfft_desc *desc, const void *sci, const void *tmpl,
                                   const double *coeffs, void *diff, sfft_stream_t stream);
 

@@ -59,6 +59,7 @@ def _load():
         P = ctypes.c_void_p
         I = ctypes.c_int
         lib.oracle_lag_tables.argtypes = [I, I, P, P, P, I, I, I, P, P, P, P, P]
+        lib.oracle_lag_tables_band.argtypes = [I, I, P, P, P, I, I, I, I, I, P, P, P, P, P]
         lib.oracle_normal.argtypes = [I, I, P, P, P, I, I, I, P, P]
         lib.oracle_brute_normal.argtypes = [I, I, P, P, P, I, I, I, P, P]
         lib.oracle_normal_entries.argtypes = [I, I, P, P, P, I, I, I, I, P, P, P]
@@ -70,7 +71,7 @@ def _load():
         lib.oracle_n_unknowns.argtypes = [I, I, I]
         lib.oracle_npoly.argtypes = [I]
         lib.oracle_mono_pq.argtypes = [I, P, P]
-        for name in ("oracle_lag_tables", "oracle_normal", "oracle_brute_normal",
+        for name in ("oracle_lag_tables", "oracle_lag_tables_band", "oracle_normal", "oracle_brute_normal",
                      "oracle_normal_entries", "oracle_assemble", "oracle_cholesky_solve",
                      "oracle_fit", "oracle_subtract", "oracle_subtract_pixels",
                      "oracle_n_unknowns", "oracle_npoly", "oracle_num_threads"):
@@ -134,6 +135,22 @@ def lag_tables(S, T, mask, L, dk, db):
     rc = lib.oracle_lag_tables(ny, nx, _ptr(S), _ptr(T), _ptr(m), L, dk, db,
                                *[_ptr(out[k]) for k in ("Cww", "Cwg", "Cws", "Ggg", "Ggs")])
     _check(rc, "oracle_lag_tables")
+    return out
+
+
+def lag_tables_band(S, T, mask, L, dk, db, y0, y1):
+    """The lag tables of ``lag_tables`` with the sums restricted to rows y0 <= y < y1 of the
+    first factor; tables of bands that cover every row add up to the full tables."""
+    lib = _load()
+    S, T = _f64(S), _f64(T)
+    ny, nx = S.shape
+    m = _mask(mask, S.shape)
+    nk, nb, Lw = npoly(dk), npoly(db), 2 * L - 1
+    out = dict(Cww=np.zeros((nk * (nk + 1) // 2, Lw, Lw)), Cwg=np.zeros((nk, nb, L, L)),
+               Cws=np.zeros((nk, L, L)), Ggg=np.zeros((nb, nb)), Ggs=np.zeros(nb))
+    rc = lib.oracle_lag_tables_band(ny, nx, _ptr(S), _ptr(T), _ptr(m), L, dk, db, int(y0), int(y1),
+                                    *[_ptr(out[k]) for k in ("Cww", "Cwg", "Cws", "Ggg", "Ggs")])
+    _check(rc, "oracle_lag_tables_band")
     return out
 
 

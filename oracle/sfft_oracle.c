@@ -203,6 +203,103 @@ int oracle_lag_tables(int ny, int nx, const double *S, const double *T, const ui
     return OR_OK;
 }
 
+/*
+ * The same lag tables restricted to the rows y0 <= y < y1 of the first factor:
+ *   C^band_AB(D) = sum_{y0 <= y < y1} sum_x A(y, x) B((y + dy) mod ny, (x + dx) mod nx).
+ * The tables of bands that cover [0, ny) add up to the full tables (the sums of step 2,
+ * split by rows).  Only the rows a band reads are formed: y0 - (L-1) .. y1 + (L-1) - 1,
+ * taken modulo ny.  Used to time the oracle on one full frame in slices.
+ */
+int oracle_lag_tables_band(int ny, int nx, const double *S, const double *T, const uint8_t *mask, int L,
+                           int dk, int db, int y0, int y1, double *Cww, double *Cwg, double *Cws,
+                           double *Ggg, double *Ggs) {
+    int rc = check_args(ny, nx, L, dk, db);
+    if (rc) return rc;
+    if (y0 < 0 || y1 > ny || y0 >= y1) return OR_ERR_ARG;
+    int nk = oracle_npoly(dk), nb = oracle_npoly(db), h = (L - 1) / 2;
+    int Lw = 2 * L - 1, nww = Lw * Lw, ns = L * L, G = L - 1;
+    int npair = nk * (nk + 1) / 2;
+    int nrow = (y1 - y0) + 2 * G; /* local row r is frame row (y0 - G + r) mod ny */
+    size_t np = (size_t)nrow * nx;
+    int nimg = nk + nb + 1;
+    double *img = (double *)malloc(sizeof(double) * np * (size_t)nimg);
+    if (!img) return OR_ERR_OOM;
+#pragma omp parallel for schedule(static)
+    for (int r = 0; r < nrow; r++) {
+        int y = wrap(y0 - G + r, ny);
+        for (int x = 0; x < nx; x++) {
+            size_t u = (size_t)y * nx + x, v = (size_t)r * nx + x;
+            double m = (mask && mask[u]) ? 0.0 : 1.0;
+            double tm = m != 0.0 ? T[u] : 0.0, sm = m != 0.0 ? S[u] : 0.0;
+            for (int i = 0; i < nk; i++) img[(size_t)i * np + v] = mono_at(i, y, x, ny, nx) * tm;
+            for (int q = 0; q < nb; q++) img[(size_t)(nk + q) * np + v] = mono_at(q, y, x, ny, nx) * m;
+            img[(size_t)(nk + nb) * np + v] = sm;
+        }
+    }
+    const double *W = img, *Gb = img + (size_t)nk * np, *Sm = img + (size_t)(nk + nb) * np;
+    const int nband = y1 - y0;
+    long n_ww = (long)npair * nww, n_wg = (long)nk * nb * ns, n_ws = (long)nk * ns;
+    long n_gg = (long)nb * nb, n_gs = nb;
+    long total = n_ww + n_wg + n_ws + n_gg + n_gs;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (long e = 0; e < total; e++) {
+        const double *A, *B;
+        int dx = 0, dy = 0;
+        double *out;
+        if (e < n_ww) {
+            int pr = (int)(e / nww), l = (int)(e % nww), i = 0, j = 0;
+            for (int a = 0, c = 0; a < nk; a++)
+                for (int b2 = a; b2 < nk; b2++, c++)
+                    if (c == pr) { i = a; j = b2; }
+            dy = l / Lw - (L - 1);
+            dx = l % Lw - (L - 1);
+            A = W + (size_t)i * np;
+            B = W + (size_t)j * np;
+            out = Cww + e;
+        } else if (e < n_ww + n_wg) {
+            long f = e - n_ww;
+            int i = (int)(f / ((long)nb * ns)), q = (int)((f / ns) % nb), l = (int)(f % ns);
+            dy = l / L - h;
+            dx = l % L - h;
+            A = W + (size_t)i * np;
+            B = Gb + (size_t)q * np;
+            out = Cwg + f;
+        } else if (e < n_ww + n_wg + n_ws) {
+            long f = e - n_ww - n_wg;
+            int i = (int)(f / ns), l = (int)(f % ns);
+            dy = l / L - h;
+            dx = l % L - h;
+            A = W + (size_t)i * np;
+            B = Sm;
+            out = Cws + f;
+        } else if (e < n_ww + n_wg + n_ws + n_gg) {
+            long f = e - n_ww - n_wg - n_ws;
+            A = Gb + (size_t)(f / nb) * np;
+            B = Gb + (size_t)(f % nb) * np;
+            out = Ggg + f;
+        } else {
+            long f = e - n_ww - n_wg - n_ws - n_gg;
+            A = Gb + (size_t)f * np;
+            B = Sm;
+            out = Ggs + f;
+        }
+        nsum_t acc = {0.0, 0.0};
+        for (int yy = 0; yy < nband; yy++) {
+            const double *a = A + (size_t)(G + yy) * nx;
+            const double *b = B + (size_t)(G + yy + dy) * nx;
+            for (int x = 0; x < nx; x++) {
+                int xb = x + dx;
+                if (xb >= nx) xb -= nx;
+                else if (xb < 0) xb += nx;
+                nsum_add(&acc, a[x] * b[xb]);
+            }
+        }
+        *out = nsum_val(&acc);
+    }
+    free(img);
+    return OR_OK;
+}
+
 /* ---------------------------------------------------------- step 3: assembly */
 
 int oracle_assemble(int L, int dk, int db, const double *Cww, const double *Cwg, const double *Cws,

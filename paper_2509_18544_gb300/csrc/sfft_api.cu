@@ -122,6 +122,8 @@ bool make_geometry(const sfft_desc &d, Geometry &g, char *err, size_t errlen) {
     g.mom_ctas = moments_ctas(g);
     g.nmom = npoly(2 * d.db) + npoly(d.db);
     g.pmax = d.dk > 2 * d.db ? d.dk : 2 * d.db;
+    if (d.spin_limit < 0) return snprintf(err, errlen, "spin_limit must be >= 0"), false;
+    g.spin_limit = d.spin_limit > 0 ? (long long)d.spin_limit : (1ll << 24);
     return true;
 }
 
@@ -512,11 +514,11 @@ sfft_status sfft_normal(sfft_plan_t plan, const void *sci, const void *tmpl, con
 }
 
 static sfft_status read_status(sfft_plan_t p, sfft_fit_info *info) {
-    int st_h = 0, fl[2] = {0, 0};
+    int st_h = 0, fl[3] = {0, 0, 0};
     double scal[3] = {0.0, 0.0, 0.0};
     cudaError_t e = cudaMemcpyAsync(&st_h, p->ws.status, sizeof(int), cudaMemcpyDeviceToHost, p->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(scal, p->ws.scal, 3 * sizeof(double), cudaMemcpyDeviceToHost, p->stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(fl, p->ws.flags, 2 * sizeof(int), cudaMemcpyDeviceToHost, p->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(fl, p->ws.flags, 3 * sizeof(int), cudaMemcpyDeviceToHost, p->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
     if (e != cudaSuccess) return cuda_fail(p, e, "status read-back");
     if (info) {
@@ -528,6 +530,7 @@ static sfft_status read_status(sfft_plan_t p, sfft_fit_info *info) {
         info->fallback = fast && !fl[0] ? 1 : 0;
         info->rel_residual = scal[1] > 0 ? sqrt(scal[0] / scal[1]) : 0.0;
         info->start_residual = fast && fl[0] && scal[1] > 0 ? sqrt(scal[2] / scal[1]) : 1.0;
+        info->pcg_status = fast && !fl[0] ? (fl[2] ? fl[2] : (int)SFFT_ERR_NOT_SPD) : 0;
     }
     if (st_h != 0) {
         set_err(p, "device status: %s", sfft_status_string((sfft_status)st_h));
@@ -551,7 +554,7 @@ sfft_status sfft_fit(sfft_plan_t plan, const void *sci, const void *tmpl, const 
     {
         StageTimer t(plan, ST_SOLVE);
         const bool fast = plan->desc.solver == SFFT_SOLVE_PCG;
-        e = cudaMemsetAsync(w.flags, 0, 2 * sizeof(int), plan->stream);
+        e = cudaMemsetAsync(w.flags, 0, 3 * sizeof(int), plan->stream);
         if (e == cudaSuccess && fast && pcg_cluster_size(plan->g) > 0) {
             const int max_iter = plan->desc.max_iter > 0 ? plan->desc.max_iter : 50;
             const double tol = plan->desc.tol > 0.0 ? plan->desc.tol : 1e-12;

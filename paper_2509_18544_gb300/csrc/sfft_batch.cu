@@ -135,7 +135,7 @@ struct sfft_batch_s {
     cudaEvent_t ev_fork = nullptr;
     std::vector<cudaEvent_t> ev_join;
     std::vector<cudaEvent_t> ev_in;  // per lane: its first pair's host inputs are on the device
-    double *rec = nullptr;                         // per pair: [status, flag0, flag1, scal0, scal1, scal2, -, -]
+    double *rec = nullptr;                         // per pair: [status, flag0 flag1, flag2, scal0, scal1, scal2, -, -]
     cudaGraph_t graph_h = nullptr;
     cudaGraphExec_t exec = nullptr;
     uint64_t launches_per_run = 0;
@@ -202,7 +202,7 @@ cudaError_t queue_batch(sfft_batch_t b, sfft_status *st) {
             double *r = b->rec + (size_t)pi * kRec;
             e = cudaMemcpyAsync(r, p->ws.status, sizeof(int), cudaMemcpyDeviceToDevice, b->ls[l]);
             if (e == cudaSuccess)
-                e = cudaMemcpyAsync(r + 1, p->ws.flags, 2 * sizeof(int), cudaMemcpyDeviceToDevice, b->ls[l]);
+                e = cudaMemcpyAsync(r + 1, p->ws.flags, 3 * sizeof(int), cudaMemcpyDeviceToDevice, b->ls[l]);
             if (e == cudaSuccess)
                 e = cudaMemcpyAsync(r + 3, p->ws.scal, 3 * sizeof(double), cudaMemcpyDeviceToDevice, b->ls[l]);
             if (e == cudaSuccess) e = cudaMemsetAsync(p->ws.status, 0, sizeof(int), b->ls[l]);
@@ -562,7 +562,7 @@ sfft_status sfft_batch_info(sfft_batch_t b, sfft_fit_info *infos) {
     sfft_status worst = SFFT_OK;
     for (int i = 0; i < np; i++) {
         const double *r = rec.data() + (size_t)i * kRec;
-        int st, fl[2];
+        int st, fl[3];
         memcpy(&st, r, sizeof st);
         memcpy(fl, r + 1, sizeof fl);
         sfft_fit_info &f = infos[i];
@@ -573,6 +573,7 @@ sfft_status sfft_batch_info(sfft_batch_t b, sfft_fit_info *infos) {
         f.fallback = fast && !fl[0] ? 1 : 0;
         f.rel_residual = r[4] > 0 ? sqrt(r[3] / r[4]) : 0.0;
         f.start_residual = fast && fl[0] && r[4] > 0 ? sqrt(r[5] / r[4]) : 1.0;
+        f.pcg_status = fast && !fl[0] ? (fl[2] ? fl[2] : (int)SFFT_ERR_NOT_SPD) : 0;
         if (st != 0 && worst == SFFT_OK) worst = (sfft_status)st;
     }
     return worst;

@@ -62,6 +62,7 @@ struct Geometry {
     int ycorr_scalar;          // 1: scalar FP32 y-correlation kernel instead of packed FP32x2
     int sub_per_sm;            // subtract / residual CTAs per SM the grid is sized for
     int pcg_cluster;           // PCG cluster size asked for (0: the largest available)
+    long long spin_limit;      // iterations of a bounded device-side wait before it gives up
 };
 
 bool make_geometry(const sfft_desc &d, Geometry &g, char *err, size_t errlen);
@@ -94,7 +95,7 @@ struct Workspace {
     float *dinvf = nullptr;      // [n] FP32 reciprocal diagonal
     double *dscale = nullptr;    // [n] Jacobi scaling diag(N)^{-1/2} of the fast solver
     float *Lg = nullptr;         // packed FP32 factor tiles of the fast solver
-    int *flags = nullptr;        // fast solver: [0] converged, [1] iterations
+    int *flags = nullptr;        // fast solver: [0] converged, [1] iterations, [2] outcome if not converged
     void *cfold = nullptr;       // subtract: folded kernel coefficients [ny][L][dk+1][L] (R)
     int *status = nullptr;       // device status word(s)
     unsigned *bar = nullptr;     // grid-barrier words of the cooperative solver [count, generation]

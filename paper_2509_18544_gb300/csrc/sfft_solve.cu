@@ -22,7 +22,6 @@ namespace {
 
 constexpr int NB = 32;
 constexpr int CT = 256;
-constexpr long long kSpinLimit = 1ll << 24;  // x ~64 ns sleep: a few seconds at most
 
 __device__ __forceinline__ double ldg_cg(const double *p) { return __ldcg(p); }
 
@@ -36,6 +35,7 @@ struct SolveArgs {
     double *scal;   // [0] ||r||^2 after refinement, [1] ||b||^2
     unsigned *bar;  // [0] arrival count, [1] generation
     int *status;
+    long long spin_limit;  // barrier wait iterations (~64 ns sleep each) before SFFT_ERR_TIMEOUT
     int n;
     int factor;     // 1: factor N, solve and refine; 0: x += N^{-1} b with the factor in R
     double *dinv;   // [n] reciprocals of the diagonal of L (computed once by the factorisation)
@@ -43,7 +43,7 @@ struct SolveArgs {
     float *dinvf;   // [n] FP32 reciprocals
 };
 
-__device__ bool grid_barrier(unsigned *bar, int *status) {
+__device__ bool grid_barrier(unsigned *bar, int *status, long long spin_limit) {
     __syncthreads();
     if (threadIdx.x == 0) {
         volatile unsigned *vgen = bar + 1;
@@ -57,7 +57,7 @@ __device__ bool grid_barrier(unsigned *bar, int *status) {
         } else {
             long long it = 0;
             while (*vgen == g) {
-                if (++it > kSpinLimit) {
+                if (++it > spin_limit) {
                     atomicCAS(status, 0, (int)SFFT_ERR_TIMEOUT);
                     break;
                 }
@@ -191,14 +191,14 @@ __global__ void __launch_bounds__(CT) k_cholesky_factor(SolveArgs A, const int *
     const int n = A.n, nblk = (n + NB - 1) / NB;
     for (size_t e = (size_t)blockIdx.x * CT + threadIdx.x; e < (size_t)n * n; e += (size_t)gridDim.x * CT)
         A.R[e] = A.N[e];
-    if (!grid_barrier(A.bar, A.status)) return;
+    if (!grid_barrier(A.bar, A.status, A.spin_limit)) return;
     for (int kb = 0; kb < nblk; kb++) {
         if (blockIdx.x == 0) potrf_tile(A.R, A.dinv, A.Rf, A.dinvf, n, kb, A.status, s0);
-        if (!grid_barrier(A.bar, A.status)) return;
+        if (!grid_barrier(A.bar, A.status, A.spin_limit)) return;
         const int rest = nblk - kb - 1;
         if (rest == 0) break;
         for (int t = blockIdx.x; t < rest; t += gridDim.x) trsm_tile(A.R, A.Rf, A.dinv, n, kb, kb + 1 + t, s0, s1);
-        if (!grid_barrier(A.bar, A.status)) return;
+        if (!grid_barrier(A.bar, A.status, A.spin_limit)) return;
         const int ntiles = rest * (rest + 1) / 2;
         for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
             int a = (int)((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);
@@ -206,7 +206,7 @@ __global__ void __launch_bounds__(CT) k_cholesky_factor(SolveArgs A, const int *
             while (a * (a + 1) / 2 > t) a--;
             syrk_tile(A.R, n, kb, kb + 1 + a, kb + 1 + (t - a * (a + 1) / 2), s0, s1);
         }
-        if (!grid_barrier(A.bar, A.status)) return;
+        if (!grid_barrier(A.bar, A.status, A.spin_limit)) return;
     }
 }
 
@@ -343,7 +343,7 @@ cudaError_t launch_cholesky_solve(const Geometry &g, const double *N, const doub
         if (!coop || per_sm < 1) return cudaErrorCooperativeLaunchTooLarge;
         g_coop_grid = sms;  // one CTA per SM: co-resident by construction
     }
-    SolveArgs A{N, b, R, x, r, z, scal, bar, status, n, 1, dinv, Rf, dinvf};
+    SolveArgs A{N, b, R, x, r, z, scal, bar, status, g.spin_limit, n, 1, dinv, Rf, dinvf};
     void *params[] = {&A, (void *)&skip};
     // As the fallback of PCG (skip != NULL) the factor usually returns at once, but a
     // cooperative launch starts only when all its CTAs can be resident: one CTA per SM would

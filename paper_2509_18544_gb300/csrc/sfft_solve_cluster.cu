@@ -43,7 +43,7 @@ struct FastArgs {
     double *r, *p, *q, *z, *d;  // [n] FP64 work vectors, d = diag(N)^{-1/2}
     float *Lg;         // packed FP32 factor tiles in global memory [ntiles][TT]
     double *scal;      // [0] final ||r||^2, [1] ||b||^2, [2] ||r||^2 at the starting point
-    int *flags;        // [0] converged, [1] iterations
+    int *flags;        // [0] converged, [1] iterations, [2] outcome when not converged (sfft_status)
     int n, nblk, ntiles;
     int nker, nb;      // kernel and background unknowns (n = nker + nb)
     int max_iter;
@@ -271,7 +271,10 @@ __global__ void __launch_bounds__(CTH) k_pcg_cluster(FastArgs A) {
         for (int rk = 0; rk < CL; rk++) any_bad |= *cl.map_shared_rank(&bad, rk);
         cl.sync();  // nobody leaves while another CTA may still read its flag
         if (any_bad) {
-            if (rank == 0 && tid == 0) A.flags[0] = 0;
+            if (rank == 0 && tid == 0) {
+                A.flags[0] = 0;
+                A.flags[2] = (int)SFFT_ERR_NOT_SPD;
+            }
             return;
         }
     }
@@ -448,6 +451,8 @@ __global__ void __launch_bounds__(CTH) k_pcg_cluster(FastArgs A) {
     if (rank == 0 && tid == 0) {
         A.flags[0] = conv ? 1 : 0;
         A.flags[1] = it;
+        // why PCG stopped short: the iteration cap, or a breakdown (p^T N p <= 0, NaN)
+        A.flags[2] = conv ? 0 : (it >= A.max_iter ? (int)SFFT_ERR_NO_CONVERGENCE : (int)SFFT_ERR_NOT_SPD);
         A.scal[0] = rr;
         A.scal[1] = bb;
         A.scal[2] = rr0;

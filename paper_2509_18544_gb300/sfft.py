@@ -43,13 +43,15 @@ class sfft_desc(ctypes.Structure):
                 ("L", ctypes.c_int32), ("dk", ctypes.c_int32), ("db", ctypes.c_int32),
                 ("dtype", ctypes.c_int32), ("precision", ctypes.c_int32), ("solver", ctypes.c_int32),
                 ("max_iter", ctypes.c_int32), ("tol", ctypes.c_double), ("workspace_cap", ctypes.c_size_t),
-                ("seg", ctypes.c_int32), ("refine", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6)]
+                ("seg", ctypes.c_int32), ("refine", ctypes.c_int32), ("spin_limit", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 5)]
 
 
 class sfft_fit_info(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("n", ctypes.c_int32), ("iterations", ctypes.c_int32),
                 ("fallback", ctypes.c_int32), ("rel_residual", ctypes.c_double),
-                ("start_residual", ctypes.c_double), ("reserved", ctypes.c_double * 2)]
+                ("start_residual", ctypes.c_double), ("pcg_status", ctypes.c_int32),
+                ("reserved_i", ctypes.c_int32), ("reserved", ctypes.c_double * 1)]
 
 
 class sfft_pair(ctypes.Structure):
@@ -192,11 +194,12 @@ class Plan:
 
 
 def make_desc(ny, nx, L, dk, db, dtype=F32, precision=PREC_SPLIT, solver=SOLVE_CHOLESKY, pitch=0,
-              max_iter=0, tol=0.0, workspace_cap=0, seg=0, refine=0) -> sfft_desc:
+              max_iter=0, tol=0.0, workspace_cap=0, seg=0, refine=0, spin_limit=0) -> sfft_desc:
     d = sfft_desc()
     d.ny, d.nx, d.pitch, d.L, d.dk, d.db = ny, nx, pitch, L, dk, db
     d.dtype, d.precision, d.solver = dtype, precision, solver
     d.max_iter, d.tol, d.workspace_cap, d.seg, d.refine = max_iter, tol, workspace_cap, seg, refine
+    d.spin_limit = spin_limit
     return d
 
 

@@ -1,5 +1,6 @@
 """The benchmark's reference arm (the FP64 oracle on the host's cores) prints one JSON line
-with the contract's keys; it needs no GPU, so the CPU suite runs it."""
+with the contract's keys; it needs no GPU, so the CPU suite runs it (on a 256^2 frame; the
+default is the full 4088^2 pair, cut into one slice per timed step)."""
 import json
 import os
 import subprocess
@@ -10,7 +11,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 def test_reference_arm_prints_one_contract_line():
     r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
-                        "--warmup", "1"], cwd=ROOT, capture_output=True, text=True, timeout=600)
+                        "--warmup", "1", "--frame", "256"], cwd=ROOT, capture_output=True, text=True, timeout=600)
     assert r.returncode == 0, r.stderr[-2000:]
     lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
     assert len(lines) == 1
@@ -21,7 +22,8 @@ def test_reference_arm_prints_one_contract_line():
         assert key in d, key
     assert d["steps"] == 1 and d["warmup"] == 1 and d["n_gpus"] == 1
     assert d["value"] > 0 and d["higher_is_better"] is True
-    assert d["config"]["workload"].startswith("Roman-like 4088x4088")
+    assert d["config"]["workload"].startswith("Roman-like 256x256")
+    assert d["config"]["pairs_per_step"] == 1.0
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}

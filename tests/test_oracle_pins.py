@@ -289,3 +289,27 @@ def test_masked_pixels_never_enter_the_fit_whatever_they_hold():
     ea = oracle.normal_entries(Sz, Tz, M, 5, 1, 1, rows, rows[::-1])
     eb = oracle.normal_entries(Sn, Tn, M, 5, 1, 1, rows, rows[::-1])
     assert np.array_equal(ea, eb)
+
+
+def test_band_lag_tables_are_row_restricted_sums():
+    """The band routine (used to time the oracle on a full frame in slices): each band's
+    table equals the lag sum restricted to the band's rows, written here with numpy rolls,
+    and the bands of a partition of the rows add up to the full tables."""
+    ny, nx, L, dk, db = 23, 19, 5, 1, 1
+    S, T, m = _frames(ny, nx, seed=17)
+    good = 1.0 - m
+    wk = [w * T * good for w in _monomials_by_definition(ny, nx, dk)]
+    bands = [(0, 4), (4, 13), (13, 23)]
+    tabs = [oracle.lag_tables_band(S, T, m, L, dk, db, y0, y1) for y0, y1 in bands]
+    full = oracle.lag_tables(S, T, m, L, dk, db)
+    for k in full:
+        tot = sum(t[k] for t in tabs)
+        assert np.allclose(tot, full[k], rtol=1e-12, atol=1e-10 * np.abs(full[k]).max())
+    # one entry by definition: C_{W_0,W_1}(dx=2, dy=-3) over rows 4..12 only
+    y0, y1 = bands[1]
+    prod = wk[0] * np.roll(wk[1], shift=(3, -2), axis=(0, 1))  # B((u + d) mod N) at u
+    want = prod[y0:y1].sum()
+    got = tabs[1]["Cww"][1, -3 + L - 1, 2 + L - 1]
+    assert got == pytest.approx(want, rel=1e-12)
+    with pytest.raises(oracle.OracleError):
+        oracle.lag_tables_band(S, T, m, L, dk, db, 5, 5)
