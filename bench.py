@@ -51,16 +51,32 @@ def parse():
     ap.add_argument("--train-epochs", type=int, default=40)
     ap.add_argument("--pcg-cluster", type=int, default=0, choices=[0, 8, 16],
                     help="PCG cluster size for the batched form (0: the tuner's / largest available)")
-    ap.add_argument("--workload", default="roman4088", choices=["roman4088", "sxt48", "learned256"],
+    ap.add_argument("--workload", default="roman4088",
+                    choices=["roman4088", "sxt48", "learned256", "stress4088", "library"],
                     help="roman4088: the headline line; sxt48: 8 x 6 science/template pairs of uneven "
                          "cutout sizes, batched vs sequential; learned256: 256 batched 2048^2 pairs "
-                         "with and without the network's warm starts")
+                         "with and without the network's warm starts; stress4088: the precision-stress "
+                         "shape (L=15, DK=3, DB=2, 1e5 flux range) in SPLIT and FP64; library: the "
+                         "cuFFT + cuSOLVER comparison build on the headline pairs")
     return ap.parse_args()
 
 
 def pair_seeds(rank: int, pairs: int):
     """Seeds of this rank's pairs: ranks draw disjoint pairs (weak scaling, no shared data)."""
     return [1000 + 100 * rank + i for i in range(pairs)]
+
+
+def pair_field(seed: int):
+    """PSF fields of the pair drawn with this seed: round Moffats whose FWHM runs linearly
+    1.8 -> 2.4 px across the frame, along a direction drawn per pair and per image (the pair
+    with seed 1000 keeps x for the template and y for the science image), so that the
+    warm-start network sees a different input for every pair."""
+    import numpy as np
+    from paper_2509_18544_gb300 import synth
+    if seed == 1000:
+        return synth.roman_field()
+    th = np.random.Generator(np.random.PCG64(seed + 77)).uniform(0.0, 2.0 * np.pi, 2)
+    return synth.linear_field(th[0], th[1])
 
 
 def max_over_ranks(v: float, world: int, device=None) -> float:
@@ -164,7 +180,8 @@ def run_ours(args, world, rank, local):
 
     NY = NX = args.frame
     workload = WORKLOAD if args.frame == 4088 else WORKLOAD.replace("4088x4088", "%dx%d" % (NY, NX))
-    pairs = [synth.roman_pair(NY, NX, seed=sd) for sd in pair_seeds(rank, args.pairs)]
+    seeds = pair_seeds(rank, args.pairs)
+    pairs = [synth.roman_pair(NY, NX, seed=sd, field=pair_field(sd)) for sd in seeds]
     dev_pairs = [tuple(torch.from_numpy(a).to(dev) for a in p) for p in pairs]
     stream = torch.cuda.current_stream(dev)
     n = L * L * (DK + 1) * (DK + 2) // 2 + (DB + 1) * (DB + 2) // 2
@@ -230,8 +247,8 @@ def run_ours(args, world, rank, local):
                                 stream=stream)
     train_s = time.perf_counter() - t0
     del tr_stamps, tr_targets
-    # every pair of this workload is drawn with the same PSF fields
-    stamps = torch.from_numpy(np.repeat(synth.psf_stamps(synth.roman_field())[None], args.pairs, 0)).to(dev)
+    # each pair's own PSF fields
+    stamps = torch.from_numpy(np.stack([synth.psf_stamps(pair_field(sd)) for sd in seeds])).to(dev)
     x0 = torch.zeros((args.pairs, n), dtype=torch.float64, device=dev)
     bcoeffs = [torch.empty(n, dtype=torch.float64, device=dev) for _ in pairs]
     bdiffs = [torch.empty((NY, NX), dtype=torch.float32, device=dev) for _ in pairs]
@@ -508,6 +525,152 @@ def run_sxt48(args):
         p.close()
 
 
+def library_fit_subtract(S, T, M, L, dk, db):
+    """The same fit and subtraction built on library routines, as a comparison baseline only:
+    full-frame 2-D FFTs (cuFFT through torch.fft, FP32), every lag table from a full inverse
+    FFT of its cross-spectrum, the normal matrix assembled and solved in FP64 (cuSOLVER
+    Cholesky through torch.linalg), the difference image by FFT convolution.  Returns
+    (theta, D)."""
+    import torch
+    dev = S.device
+    ny, nx = S.shape
+    h, G = (L - 1) // 2, L - 1
+    good = (M == 0).to(torch.float32) if M is not None else torch.ones_like(S)
+    Tm, Sm = torch.where(good > 0, T, torch.zeros_like(T)), torch.where(good > 0, S, torch.zeros_like(S))
+    xh = torch.linspace(-1.0, 1.0, nx, device=dev, dtype=torch.float64).to(torch.float32)
+    yh = torch.linspace(-1.0, 1.0, ny, device=dev, dtype=torch.float64).to(torch.float32)
+
+    def monos(d):
+        return [(deg - q, q) for deg in range(d + 1) for q in range(deg + 1)]
+
+    mk, mb = monos(dk), monos(db)
+    wmon = lambda p, q: yh[:, None] ** q * xh[None, :] ** p
+    W = torch.stack([wmon(p, q) * Tm for p, q in mk])
+    Psi = torch.stack([wmon(p, q) * good for p, q in mb])
+    FW, FP, FS = torch.fft.rfft2(W), torch.fft.rfft2(Psi), torch.fft.rfft2(Sm)
+    nk, nb = len(mk), len(mb)
+    dys = torch.arange(-G, G + 1, device=dev)
+
+    def lags(FA, FB, r):
+        c = torch.fft.irfft2(torch.conj(FA) * FB, s=(ny, nx))  # C(d) = sum_u A(u) B(u + d)
+        iy = (torch.arange(-r, r + 1, device=dev) % ny)[:, None]
+        ix = (torch.arange(-r, r + 1, device=dev) % nx)[None, :]
+        return c[iy, ix].to(torch.float64)
+
+    ns, nker = L * L, nk * L * L
+    n = nker + nb
+    N = torch.empty((n, n), dtype=torch.float64, device=dev)
+    bvec = torch.empty(n, dtype=torch.float64, device=dev)
+    l = torch.arange(ns, device=dev)
+    dyl, dxl = l // L - h, l % L - h
+    ddy = (dyl[:, None] - dyl[None, :]) + G
+    ddx = (dxl[:, None] - dxl[None, :]) + G
+    for i in range(nk):
+        for j in range(i, nk):
+            C = lags(FW[i], FW[j], G)
+            blk = C[ddy, ddx]  # <Phi_i,d, Phi_j,d'> = C_ij(d - d')
+            N[i * ns:(i + 1) * ns, j * ns:(j + 1) * ns] = blk
+            N[j * ns:(j + 1) * ns, i * ns:(i + 1) * ns] = blk.T
+        for r in range(nb):
+            v = lags(FW[i], FP[r], h).reshape(-1)
+            N[i * ns:(i + 1) * ns, nker + r] = v
+            N[nker + r, i * ns:(i + 1) * ns] = v
+        bvec[i * ns:(i + 1) * ns] = lags(FW[i], FS, h).reshape(-1)
+    P64 = Psi.to(torch.float64)
+    N[nker:, nker:] = torch.einsum("ayx,byx->ab", P64, P64)
+    bvec[nker:] = torch.einsum("ayx,yx->a", P64, Sm.to(torch.float64))
+    theta = torch.cholesky_solve(bvec[:, None], torch.linalg.cholesky(N))[:, 0]
+    # D = S - sum_pq (kernel_pq * (w_pq T)) - background, the kernels as cyclic images
+    model = torch.zeros((ny, nx // 2 + 1), dtype=torch.complex64, device=dev)
+    for i, (p, q) in enumerate(mk):
+        kimg = torch.zeros((ny, nx), dtype=torch.float32, device=dev)
+        kimg[dyl % ny, dxl % nx] = theta[i * ns:(i + 1) * ns].to(torch.float32)
+        model += torch.fft.rfft2(wmon(p, q) * T) * torch.fft.rfft2(kimg)
+    D = S - torch.fft.irfft2(model, s=(ny, nx))
+    for r, (p, q) in enumerate(mb):
+        D -= theta[nker + r].to(torch.float32) * wmon(p, q)
+    return theta, D
+
+
+def run_library(args):
+    """Comparison baseline: `library_fit_subtract` (cuFFT + cuSOLVER) on the headline pairs,
+    timed like the plain form, with its agreement with libsfft's coefficients."""
+    import torch
+    from paper_2509_18544_gb300 import build as sfft_build
+    from paper_2509_18544_gb300 import sfft, synth
+    sfft_build.build()
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    npairs = min(args.pairs, 4)
+    seeds = pair_seeds(0, npairs)
+    data = [tuple(torch.from_numpy(a).to(dev) for a in synth.roman_pair(NY, NX, seed=sd, field=pair_field(sd)))
+            for sd in seeds]
+    with torch.no_grad():
+        for S, T, M in data[:1]:
+            library_fit_subtract(S, T, M, L, DK, DB)
+        ms = _timed_once(lambda: [library_fit_subtract(S, T, M, L, DK, DB) for S, T, M in data], stream, 1)
+        th_lib = [library_fit_subtract(S, T, M, L, DK, DB)[0] for S, T, M in data]
+    n = L * L * (DK + 1) * (DK + 2) // 2 + (DB + 1) * (DB + 2) // 2
+    with sfft.sfft_plan(sfft.make_desc(NY, NX, L, DK, DB), stream=stream) as plan:
+        th = torch.empty(n, dtype=torch.float64, device=dev)
+        D = torch.empty_like(data[0][0])
+
+        def ours():
+            for S, T, M in data:
+                sfft.sfft_fit(plan, S, T, M, None, th, want_info=False)
+                sfft.sfft_subtract(plan, S, T, th, D)
+
+        ours()
+        ours_ms = _timed_once(ours, stream, 3)
+        errs = []
+        for (S, T, M), tl in zip(data, th_lib):
+            sfft.sfft_fit(plan, S, T, M, None, th, want_info=True)
+            errs.append(float(torch.linalg.norm(tl - th) / torch.linalg.norm(th)))
+    print(json.dumps({"metric": "4088^2 difference images/s, library comparison build", "unit": UNIT,
+                      "value": round(npairs / (ms / 1e3), 3), "ms_per_pair": round(ms / npairs, 2),
+                      "workload": "%d headline pairs (4088^2, L=11, DK=2, DB=2, masked)" % npairs,
+                      "library": "cuFFT 2-D FFTs (FP32) + full inverse per cross-spectrum, cuSOLVER Cholesky (FP64), "
+                                 "FFT convolution for the difference image, through torch",
+                      "libsfft_plain_ms_per_pair": round(ours_ms / npairs, 2),
+                      "libsfft_over_library": round(ms / ours_ms, 2),
+                      "library_coeff_rel_diff_vs_libsfft": errs}), flush=True)
+
+
+def run_stress(args):
+    """The precision-stress shape: a 4088^2 pair with fluxes log-uniform over 1e2..1e7 e-,
+    L = 15, DK = 3, DB = 2 (2256 unknowns); fit + subtract in SPLIT precision (FP32 spectra,
+    one compensated refinement) and in FP64 throughout, with their coefficient agreement.
+    (Agreement with the FP64 CPU oracle is the parity test's job.)"""
+    import torch
+    from paper_2509_18544_gb300 import build as sfft_build
+    from paper_2509_18544_gb300 import sfft, synth
+    sfft_build.build()
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    Ls, dks, dbs = 15, 3, 2
+    S, T, M = (torch.from_numpy(a).to(dev) for a in synth.roman_pair(NY, NX, seed=3000, flux_mode="dynamic"))
+    out = {}
+    for name, prec in (("split", sfft.PREC_SPLIT), ("fp64", sfft.PREC_FP64)):
+        with sfft.sfft_plan(sfft.make_desc(NY, NX, Ls, dks, dbs, precision=prec), stream=stream) as plan:
+            th = torch.empty(plan.n, dtype=torch.float64, device=dev)
+            D = torch.empty_like(S)
+
+            def step():
+                sfft.sfft_fit(plan, S, T, M, None, th, want_info=False)
+                sfft.sfft_subtract(plan, S, T, th, D)
+
+            step()
+            ms = _timed_once(step, stream, max(1, min(args.steps, 5)) if prec == sfft.PREC_SPLIT else 1)
+            sfft.sfft_fit(plan, S, T, M, None, th, want_info=True)
+            out[name] = (ms, th.clone())
+    rel = float(torch.linalg.norm(out["split"][1] - out["fp64"][1]) / torch.linalg.norm(out["fp64"][1]))
+    print(json.dumps({"metric": "precision-stress 4088^2 difference images/s (SPLIT)", "unit": UNIT,
+                      "value": round(1e3 / out["split"][0], 3),
+                      "workload": "stress4088: 4088^2 pair, fluxes 1e2..1e7 e-, L=15 DK=3 DB=2 (2256 unknowns)",
+                      "split_ms": round(out["split"][0], 2), "fp64_ms": round(out["fp64"][0], 2),
+                      "split_vs_fp64_gpu_coeff_rel": rel}), flush=True)
+
+
 def run_learned256(args):
     """The warm-start network trained on `--train-samples` fits, driving PCG over a batch of
     256 2048^2 pairs (16 distinct seeded pairs, each used 16 times), against the same batch
@@ -597,6 +760,12 @@ def main():
         return
     if args.workload == "learned256":
         run_learned256(args)
+        return
+    if args.workload == "library":
+        run_library(args)
+        return
+    if args.workload == "stress4088":
+        run_stress(args)
         return
     run_ours(args, world, rank, local)
 

@@ -210,13 +210,18 @@ sfft_status sfft_batch(const sfft_desc *base, int32_t n_sci, int32_t n_tmpl, con
  * refine); without an entry built-in heuristics apply.  Zero fields mean "heuristic". */
 typedef struct {
     int32_t ycorr_bins;       /* frequencies per y-correlation CTA (1 .. the thread/smem limit) */
-    int32_t ycorr_split;      /* y-correlation row chunks */
+    int32_t ycorr_split;      /* y-correlation row chunks (direct) or CTAs per frequency (y-FFT) */
     int32_t ycorr_scalar;     /* 1: scalar FP32 y-correlation kernel, 0: packed FP32x2 */
     int32_t subtract_ctas;    /* subtract / residual CTAs per SM the grid is sized for (1 .. 4) */
     int32_t pcg_cluster;      /* CTAs in the PCG solver's cluster: 8 or 16 (0 = the largest the
                                  device allows); a smaller cluster is easier to place among the
                                  other lanes of a batch */
-    int32_t reserved[3];
+    int32_t ycorr_direct;     /* 0: y-block FFT route (K1 writes the x-weighted base spectra; the
+                                 y correlation takes 128-point DFTs of 128-row blocks and inverts
+                                 the summed cross-spectra at the lags; ycorr_split = CTAs per
+                                 frequency); 1: direct correlation over the rows (K1 writes every
+                                 image's spectrum; ycorr_bins, ycorr_split, ycorr_scalar apply) */
+    int32_t reserved[2];
 } sfft_tuning;
 /* The cached entry for desc (zeros and *cached = 0 when there is none). */
 sfft_status sfft_tuning_get(const sfft_desc *desc, sfft_tuning *t, int32_t *cached);
@@ -259,6 +264,22 @@ sfft_status sfft_tuning_load(const char *path);
  * on one device) race on it and must be serialised. */
 sfft_status sfft_subtract_noalloc(const sfft_desc *desc, const void *sci, const void *tmpl,
                                   const double *coeffs, void *diff, sfft_stream_t stream);
+
+/* ---------------------------------------------------------------------------------
+ * Cross-convolution (Sec. "Pipeline steps", step 5: before the subtraction the science
+ * image is convolved with the template's PSF and the template with the science image's,
+ * so that both carry the same PSF).
+ *   sci_out(u)  = sum_d psf_tmpl(d) sci((u - d) mod N),
+ *   tmpl_out(u) = sum_d psf_sci(d)  tmpl((u - d) mod N),
+ * d = (a - r, b - r) for stamp element [a][b] of the K x K row-major float32 stamps
+ * (K = 2r + 1 odd, 1 <= K <= 31, centred on the middle element), cyclic on the ny x nx
+ * frame.  Images and outputs are device arrays of `dtype` (SFFT_F32 or SFFT_F64) with a row
+ * pitch of `pitch` elements (0 = nx); the arithmetic is FP32.  Either half is skipped when
+ * its image, stamp or output is NULL (both NULL: SFFT_ERR_INVALID_ARG); an output may not
+ * alias an input.  Queued on `stream`; no allocation. */
+sfft_status sfft_cross_convolve(int32_t ny, int32_t nx, int32_t pitch, int32_t dtype, int32_t K, const void *sci,
+                                const void *tmpl, const float *psf_sci, const float *psf_tmpl, void *sci_out,
+                                void *tmpl_out, sfft_stream_t stream);
 
 /* ---------------------------------------------------------------------------------
  * Warm-start network (the learned warm start of the PCG solve).  A small CNN maps the

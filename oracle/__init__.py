@@ -69,12 +69,13 @@ def _load():
         lib.oracle_subtract.argtypes = [I, I, P, P, I, I, I, P, P]
         lib.oracle_subtract_pixels.argtypes = [I, I, P, P, I, I, I, P, I, P, P]
         lib.oracle_n_unknowns.argtypes = [I, I, I]
+        lib.oracle_convolve.argtypes = [I, I, P, I, P, P]
         lib.oracle_npoly.argtypes = [I]
         lib.oracle_mono_pq.argtypes = [I, P, P]
         for name in ("oracle_lag_tables", "oracle_lag_tables_band", "oracle_normal", "oracle_brute_normal",
                      "oracle_normal_entries", "oracle_assemble", "oracle_cholesky_solve",
                      "oracle_fit", "oracle_subtract", "oracle_subtract_pixels",
-                     "oracle_n_unknowns", "oracle_npoly", "oracle_num_threads"):
+                     "oracle_n_unknowns", "oracle_npoly", "oracle_num_threads", "oracle_convolve"):
             getattr(lib, name).restype = ctypes.c_int
         _lib = lib
         return lib
@@ -243,4 +244,18 @@ def subtract_pixels(S, T, theta, L, dk, db, flat_idx):
     out = np.zeros(len(idx))
     _check(lib.oracle_subtract_pixels(ny, nx, _ptr(S), _ptr(T), L, dk, db, _ptr(theta), len(idx),
                                       _ptr(idx), _ptr(out)), "oracle_subtract_pixels")
+    return out
+
+
+def convolve(X, P):
+    """Cyclic convolution of the image X with the odd-sized square stamp P (centred on its
+    middle element), by direct FP64 sums: the cross-convolution of the pipeline."""
+    lib = _load()
+    X, P = _f64(X), _f64(P)
+    ny, nx = X.shape
+    K = P.shape[0]
+    if P.shape != (K, K):
+        raise ValueError("stamp must be square")
+    out = np.zeros((ny, nx))
+    _check(lib.oracle_convolve(ny, nx, _ptr(X), K, _ptr(P), _ptr(out)), "oracle_convolve")
     return out

@@ -529,6 +529,26 @@ int oracle_subtract_pixels(int ny, int nx, const double *S, const double *T, int
     return OR_OK;
 }
 
+/* ------------------------------------------ cross-convolution (pipeline step 5) */
+
+/* out(u) = sum_d P(d) X((u - d) mod N), d = (a - r, b - r) for the K x K stamp P[a][b]
+ * (K = 2r + 1, row-major): the cyclic convolution of the image with the stamp, centred on
+ * the stamp's middle element, by direct FP64 sums. */
+int oracle_convolve(int ny, int nx, const double *X, int K, const double *P, double *out) {
+    if (ny < 1 || nx < 1 || K < 1 || (K % 2) == 0) return OR_ERR_ARG;
+    int r = (K - 1) / 2;
+#pragma omp parallel for schedule(static)
+    for (int y = 0; y < ny; y++)
+        for (int x = 0; x < nx; x++) {
+            nsum_t acc = {0.0, 0.0};
+            for (int a = 0; a < K; a++)
+                for (int b = 0; b < K; b++)
+                    nsum_add(&acc, P[a * K + b] * X[(size_t)wrap(y - (a - r), ny) * nx + wrap(x - (b - r), nx)]);
+            out[(size_t)y * nx + x] = nsum_val(&acc);
+        }
+    return OR_OK;
+}
+
 int oracle_num_threads(void) {
 #ifdef _OPENMP
     return omp_get_max_threads();

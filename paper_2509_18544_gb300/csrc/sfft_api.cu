@@ -39,6 +39,9 @@ size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 namespace sfft {
 
 void set_global_error(const char *msg) { set_err(nullptr, "%s", msg); }
+void default_y2split(Geometry &g);
+void finish_geometry(Geometry &g);
+int device_sm_count();
 
 int default_ysplit(const Geometry &g) {
     // row chunks so the grid covers several waves of 2 CTAs on each of 152 SMs
@@ -124,7 +127,69 @@ bool make_geometry(const sfft_desc &d, Geometry &g, char *err, size_t errlen) {
     g.pmax = d.dk > 2 * d.db ? d.dk : 2 * d.db;
     if (d.spin_limit < 0) return snprintf(err, errlen, "spin_limit must be >= 0"), false;
     g.spin_limit = d.spin_limit > 0 ? (long long)d.spin_limit : (1ll << 24);
+    // y-block FFT route (the default): blocks of Py = 128 rows, Uy = Py - 2G of them new
+    g.nbase = 2 * (d.dk + 1) + (d.db + 1) + 1;
+    g.Py = 128;
+    g.Uy = g.Py - 2 * g.G;
+    g.nyb = (d.ny + g.Uy - 1) / g.Uy;
+    g.npair_all = g.npair + g.nk * (g.nb + 1);
+    g.yfft = 1;
+    {
+        // pairs per CTA: at most 64 (16 per thread, 4 threads per ky in the FP32 layout) and
+        // what the shared-memory budget leaves; groups balanced
+        int ypg = g.npair_all < 64 ? g.npair_all : 64;
+        for (;;) {
+            g.ypg = ypg;
+            if (ypg == 1 || yfft_smem_bytes(g, d.precision, false) <= (size_t)220 * 1024) break;
+            ypg--;
+        }
+        g.npg = (g.npair_all + ypg - 1) / ypg;
+        g.ypg = (g.npair_all + g.npg - 1) / g.npg;
+        if (yfft_smem_bytes(g, d.precision, false) > (size_t)220 * 1024 ||
+            yfft_smem_bytes(g, d.precision, true) > (size_t)220 * 1024)
+            g.yfft = 0;  // this basis is too large for the y-FFT kernels: the direct route runs it
+    }
+    default_y2split(g);
+    finish_geometry(g);
     return true;
+}
+
+// CTAs per frequency of the y-FFT kernels: the main pass runs one 512-thread CTA per SM, so
+// its split is the one (at least 8 units per CTA) whose last wave is fullest; the
+// refinement pass (256 threads, several CTAs per SM) takes about four CTAs per SM
+void default_y2split(Geometry &g) {
+    const int sms = device_sm_count();
+    const int units = g.nseg * g.nyb;
+    int best = 1;
+    double best_eff = -1.0;
+    for (int sp = 1; sp <= 16; sp++) {
+        if (sp > 1 && units / sp < 8) break;
+        const long ctas = (long)g.nkf * sp * g.npg;
+        const long waves = (ctas + sms - 1) / sms;
+        const double eff = (double)ctas / (double)(waves * sms);
+        if (eff > best_eff + 1e-9) best_eff = eff, best = sp;
+    }
+    g.y2split = best;
+    int ws = (4 * sms + g.nkf - 1) / g.nkf;
+    if (ws > units) ws = units;
+    g.y2split_ws = ws < 1 ? 1 : (ws > 16 ? 16 : ws);
+}
+
+// fields that follow from the route: values per spectrum record
+void finish_geometry(Geometry &g) { g.nrec = g.yfft ? (g.nbase + 1) & ~1 : g.nimg_pad; }
+
+int device_sm_count() {
+    static std::atomic<int> cached{0};
+    int v = cached.load();
+    if (v > 0) return v;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        sms < 1) {
+        cudaGetLastError();
+        return 152;  // no device visible (host-only calls): the GB300's count
+    }
+    cached.store(sms);
+    return sms;
 }
 
 struct Carve {
@@ -144,15 +209,25 @@ static size_t carve(const Geometry &g, int precision, int dtype, void *base, Wor
     const size_t cpx_sz = precision == SFFT_PREC_FP64 ? 16 : 8;
     Workspace tmp;
     Workspace &o = w ? *w : tmp;
-    o.spec = c.take<char>(base, (size_t)g.nseg * g.nkf * g.ny * g.nimg_pad * cpx_sz);
+    o.spec = c.take<char>(base, (size_t)g.nseg * g.nkf * g.ny * g.nrec * cpx_sz);
     {
-        // the y-correlation partials, or (refinement) the W x S_m partials: 16 bytes per value
-        size_t main_v = (size_t)g.nseg * g.ysplit * g.nkf * g.nent;
-        size_t ws_v = (size_t)g.nseg * g.ychunks_ws * g.nkf * g.nk * g.L;
+        // K2 partial sums, 16 bytes per complex value: y-FFT route [split][nkf][pairs][Py];
+        // direct route [segment][chunk][nkf][entry], or (refinement) the W x S_m partials
+        size_t main_v, ws_v;
+        if (g.yfft) {
+            main_v = (size_t)g.y2split * g.nkf * g.npair_all * g.Py;
+            const size_t ws_fft = (size_t)g.y2split_ws * g.nkf * g.nk * g.Py;
+            const size_t ws_dir = (size_t)g.nseg * g.ychunks_ws * g.nkf * g.nk * g.L;
+            ws_v = ws_fft > ws_dir ? ws_fft : ws_dir;
+        } else {
+            main_v = (size_t)g.nseg * g.ysplit * g.nkf * g.nent;
+            ws_v = (size_t)g.nseg * g.ychunks_ws * g.nkf * g.nk * g.L;
+        }
         o.ypart = c.take<double>(base, 2 * (main_v > ws_v ? main_v : ws_v));
     }
     o.resid = g.refine ? c.take<char>(base, (size_t)g.ny * g.pitch * (dtype_size)) : nullptr;
-    o.rspec = g.refine && precision != SFFT_PREC_FP64 ? c.take<char>(base, (size_t)g.nseg * g.ny * g.nkf * cpx_sz) : nullptr;
+    o.rspec = g.refine && (precision != SFFT_PREC_FP64 || g.yfft)
+                  ? c.take<char>(base, (size_t)g.nseg * g.ny * g.nkf * cpx_sz) : nullptr;
     o.ysum = c.take<double>(base, (size_t)g.nkf * g.nent * 2);
     o.lagww = c.take<double>(base, (size_t)g.npair * (2 * g.L - 1) * (2 * g.L - 1));
     o.lagwg = c.take<double>(base, (size_t)g.nk * g.nb * g.L * g.L);
@@ -186,6 +261,8 @@ static size_t carve(const Geometry &g, int precision, int dtype, void *base, Wor
     o.xpow = c.take<char>(base, (size_t)(g.pmax + 1) * g.nx * (cpx_sz / 2));
     o.ypow = c.take<char>(base, (size_t)(g.pmax + 1) * g.ny * (cpx_sz / 2));
     o.tw_x = c.take<double>(base, (size_t)g.nkf * (2 * g.G + 1) * 2);
+    o.tw_y = c.take<char>(base, (size_t)2 * g.Py * cpx_sz);
+    o.tw_yi = c.take<char>(base, (size_t)g.Py * 16);
     return align_up(c.off, 256);
 }
 
@@ -356,6 +433,35 @@ sfft_status sfft_plan(sfft_plan_t *plan, const sfft_desc *desc, sfft_stream_t st
             if (e == cudaSuccess) e = cudaMemcpyAsync(p->ws.ypow, yp32.data(), yp32.size() * 4, cudaMemcpyHostToDevice, p->stream);
         }
     }
+    // y-block FFT twiddles: forward exp(-2 pi i m / Py) (FP32: high part and remainder) and the
+    // inverse exp(+2 pi i m / Py) (FP32: double-float (cos hi, sin hi, cos lo, sin lo))
+    std::vector<double> twy64((size_t)g.Py * 4, 0.0), twyi64((size_t)g.Py * 2);
+    std::vector<float> twy32((size_t)g.Py * 4, 0.0f), twyi32((size_t)g.Py * 4);
+    for (int m = 0; m < g.Py; m++) {
+        const double c = cos(two_pi * m / g.Py), sn = sin(two_pi * m / g.Py);
+        twy64[2 * m] = c;
+        twy64[2 * m + 1] = -sn;
+        const float ch = (float)c, sh = (float)-sn;
+        twy32[2 * m] = ch;
+        twy32[2 * m + 1] = sh;
+        twy32[2 * (g.Py + m)] = (float)(c - (double)ch);
+        twy32[2 * (g.Py + m) + 1] = (float)(-sn - (double)sh);
+        twyi64[2 * m] = c;
+        twyi64[2 * m + 1] = sn;
+        const float ih = (float)c, jh = (float)sn;
+        twyi32[4 * m] = ih;
+        twyi32[4 * m + 1] = jh;
+        twyi32[4 * m + 2] = (float)(c - (double)ih);
+        twyi32[4 * m + 3] = (float)(sn - (double)jh);
+    }
+    if (e == cudaSuccess) {
+        const bool f64 = desc->precision == SFFT_PREC_FP64;
+        e = f64 ? cudaMemcpyAsync(p->ws.tw_y, twy64.data(), twy64.size() * 8, cudaMemcpyHostToDevice, p->stream)
+                : cudaMemcpyAsync(p->ws.tw_y, twy32.data(), twy32.size() * 4, cudaMemcpyHostToDevice, p->stream);
+        if (e == cudaSuccess)
+            e = f64 ? cudaMemcpyAsync(p->ws.tw_yi, twyi64.data(), twyi64.size() * 8, cudaMemcpyHostToDevice, p->stream)
+                    : cudaMemcpyAsync(p->ws.tw_yi, twyi32.data(), twyi32.size() * 4, cudaMemcpyHostToDevice, p->stream);
+    }
     if (e == cudaSuccess) e = cudaMemsetAsync(p->ws.status, 0, 16 * sizeof(int), p->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);  // host staging vectors die here
     if (e != cudaSuccess) {
@@ -453,13 +559,16 @@ static sfft_status queue_normal(sfft_plan_t p, const void *sci, const void *tmpl
     if (e != cudaSuccess) return cuda_fail(p, e, "moments launch");
     {
         StageTimer t(p, ST_YCORR);
-        e = launch_ycorr(g, p->desc.precision, w.spec, w.ypart, false, nullptr, st);
+        e = g.yfft ? launch_ycorr_fft(g, p->desc.precision, w.spec, nullptr, w.ypow, w.tw_y, w.ypart, false, st)
+                   : launch_ycorr(g, p->desc.precision, w.spec, w.ypart, false, nullptr, nullptr, st);
     }
     if (e != cudaSuccess) return cuda_fail(p, e, "y-correlation launch");
     {
         StageTimer t(p, ST_LAGS);
-        e = launch_lag_tables(g, w.ypart, w.ysum, w.tw_x, w.lagww, w.lagwg, w.lagws, w.mom_part, w.mom, false,
-                              p->desc.precision != SFFT_PREC_FP64, st);
+        if (g.yfft) e = launch_yinv(g, p->desc.precision, w.ypart, w.tw_yi, w.ysum, false, st);
+        if (e == cudaSuccess)
+            e = launch_lag_tables(g, w.ypart, w.ysum, w.tw_x, w.lagww, w.lagwg, w.lagws, w.mom_part, w.mom, false,
+                                  p->desc.precision != SFFT_PREC_FP64, g.yfft != 0, st);
     }
     if (e != cudaSuccess) return cuda_fail(p, e, "lag-table launch");
     {
@@ -471,9 +580,9 @@ static sfft_status queue_normal(sfft_plan_t p, const void *sci, const void *tmpl
 }
 
 // One residual refinement pass: R = S_m - sum a (w T_m)(u - d) - m sum b w (the residual of
-// the fit on the masked frames), c = [Phi Psi]^T R through the same segment spectra (R is
-// transformed into the S_m slot; the W_i spectra of the main pass are still in place), then
-// theta += N^{-1} c with the existing Cholesky factor.
+// the fit on the masked frames), c = [Phi Psi]^T R through the same segment spectra (R gets
+// its own row-segment spectra; the base spectra of the main pass are still in place), then
+// theta += N^{-1} c with the existing factor.
 static cudaError_t queue_refine(sfft_plan_t p, const void *sci, const void *tmpl, const uint8_t *mask,
                                 double *coeffs) {
     const Geometry &g = p->g;
@@ -488,10 +597,16 @@ static cudaError_t queue_refine(sfft_plan_t p, const void *sci, const void *tmpl
                                                         w.spec, w.rspec, st);
     if (e == cudaSuccess && !fp32)
         e = launch_moments(g, p->desc.dtype, p->desc.precision, w.resid, mask, w.ypow, w.mom_part, st);
-    if (e == cudaSuccess) e = launch_ycorr(g, p->desc.precision, w.spec, w.ypart, true, w.rspec, st);
+    // W_i x R: the direct row correlation on the FP32 paths (either spectrum layout), the
+    // y-FFT kernels for FP64 spectra on the y-FFT route
+    const bool ws_fft = g.yfft && !fp32;
+    if (e == cudaSuccess)
+        e = ws_fft ? launch_ycorr_fft(g, p->desc.precision, w.spec, w.rspec, w.ypow, w.tw_y, w.ypart, true, st)
+                   : launch_ycorr(g, p->desc.precision, w.spec, w.ypart, true, w.rspec, w.ypow, st);
+    if (e == cudaSuccess && ws_fft) e = launch_yinv(g, p->desc.precision, w.ypart, w.tw_yi, w.ysum, true, st);
     if (e == cudaSuccess)
         e = launch_lag_tables(g, w.ypart, w.ysum, w.tw_x, w.lagww, w.lagwg, w.lagws, fp32 ? nullptr : w.mom_part,
-                              w.mom, true, fp32, st);
+                              w.mom, true, fp32, ws_fft, st);
     if (e == cudaSuccess) e = launch_refine_rhs(g, w.lagws, w.mom, w.q, st);
     // correction x += N^{-1} c: with the cluster factor when the fast solver converged, else
     // with the FP32 copy of the FP64 Cholesky factor (each launch checks the flag)

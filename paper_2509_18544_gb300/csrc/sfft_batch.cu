@@ -30,6 +30,7 @@
 
 namespace sfft {
 void set_global_error(const char *msg);
+void finish_geometry(Geometry &g);
 }
 
 using namespace sfft;
@@ -60,10 +61,17 @@ bool apply_tuning(const sfft_tuning &t, Geometry &g, char *err, size_t errlen) {
     if (t.ycorr_bins < 0 || t.ycorr_bins > g.kg_max)
         return snprintf(err, errlen, "ycorr_bins %d outside [0, %d]", t.ycorr_bins, g.kg_max), false;
     if (t.ycorr_bins > 0) g.kg = t.ycorr_bins;
-    const int max_ys = std::max(1, g.ny / (2 * g.ytile));
+    if (t.ycorr_direct != 0 && t.ycorr_direct != 1) return snprintf(err, errlen, "ycorr_direct must be 0 or 1"), false;
+    if (t.ycorr_direct) g.yfft = 0;
+    const int max_ys = g.yfft ? 64 : std::max(1, g.ny / (2 * g.ytile));
     if (t.ycorr_split < 0 || t.ycorr_split > max_ys)
         return snprintf(err, errlen, "ycorr_split %d outside [0, %d]", t.ycorr_split, max_ys), false;
-    g.ysplit = t.ycorr_split > 0 ? t.ycorr_split : default_ysplit(g);
+    if (g.yfft) {
+        if (t.ycorr_split > 0) g.y2split = t.ycorr_split;
+    } else {
+        g.ysplit = t.ycorr_split > 0 ? t.ycorr_split : default_ysplit(g);
+    }
+    finish_geometry(g);
     if (t.ycorr_scalar != 0 && t.ycorr_scalar != 1) return snprintf(err, errlen, "ycorr_scalar must be 0 or 1"), false;
     g.ycorr_scalar = t.ycorr_scalar;
     if (t.subtract_ctas < 0 || t.subtract_ctas > 4)
@@ -264,13 +272,14 @@ sfft_status sfft_tuning_save(const char *path) {
     if (!f) return errf("sfft_tuning_save: cannot open %s", path), SFFT_ERR_INVALID_ARG;
     std::lock_guard<std::mutex> lk(g_tune_mu);
     fprintf(f, "# ny nx pitch L dk db dtype precision solver refine : ycorr_bins ycorr_split ycorr_scalar subtract_ctas "
-               "pcg_cluster\n");
+               "pcg_cluster ycorr_direct\n");
     for (auto &kv : g_tune) {
         const Key &k = kv.first;
         const sfft_tuning &t = kv.second;
-        fprintf(f, "%d %d %d %d %d %d %d %d %d %d : %d %d %d %d %d\n", std::get<0>(k), std::get<1>(k), std::get<2>(k),
+        fprintf(f, "%d %d %d %d %d %d %d %d %d %d : %d %d %d %d %d %d\n", std::get<0>(k), std::get<1>(k), std::get<2>(k),
                 std::get<3>(k), std::get<4>(k), std::get<5>(k), std::get<6>(k), std::get<7>(k), std::get<8>(k),
-                std::get<9>(k), t.ycorr_bins, t.ycorr_split, t.ycorr_scalar, t.subtract_ctas, t.pcg_cluster);
+                std::get<9>(k), t.ycorr_bins, t.ycorr_split, t.ycorr_scalar, t.subtract_ctas, t.pcg_cluster,
+                t.ycorr_direct);
     }
     const bool ok = fclose(f) == 0;
     return ok ? SFFT_OK : (errf("sfft_tuning_save: write failed"), SFFT_ERR_INVALID_ARG);
@@ -290,11 +299,11 @@ sfft_status sfft_tuning_load(const char *path) {
         memset(&d, 0, sizeof d);
         sfft_tuning t;
         memset(&t, 0, sizeof t);
-        int n = sscanf(line, "%d %d %d %d %d %d %d %d %d %d : %d %d %d %d %d", &d.ny, &d.nx, &d.pitch, &d.L, &d.dk,
+        int n = sscanf(line, "%d %d %d %d %d %d %d %d %d %d : %d %d %d %d %d %d", &d.ny, &d.nx, &d.pitch, &d.L, &d.dk,
                        &d.db, &d.dtype, &d.precision, &d.solver, &d.refine, &t.ycorr_bins, &t.ycorr_split,
-                       &t.ycorr_scalar, &t.subtract_ctas, &t.pcg_cluster);
-        if (n != 15) {
-            errf("sfft_tuning_load: %s:%d: expected 15 fields", path, lineno);
+                       &t.ycorr_scalar, &t.subtract_ctas, &t.pcg_cluster, &t.ycorr_direct);
+        if (n != 16) {
+            errf("sfft_tuning_load: %s:%d: expected 16 fields", path, lineno);
             result = SFFT_ERR_INVALID_ARG;
             break;
         }
@@ -343,13 +352,16 @@ sfft_status sfft_autotune(const sfft_desc *desc, const void *sci, const void *tm
     memset(&cur, 0, sizeof cur);
     double cur_ms = eval(cur);
     sfft_status result = cur_ms < 0 ? SFFT_ERR_CUDA : SFFT_OK;
-    // coordinate descent over the y-correlation kernel and shape, then the subtract grid
+    // coordinate descent: the y-correlation route and kernel (the y-FFT route, measured above,
+    // against the direct route's kernels and frequencies per CTA), then its split, then the
+    // subtract grid
     std::vector<std::vector<sfft_tuning>> rounds;
     {
         std::vector<sfft_tuning> r;
         for (int scalar = 0; scalar <= 1; scalar++)
             for (int kg : {g0.kg_max, std::max(1, g0.kg_max / 2), std::max(1, (3 * g0.kg_max) / 4)}) {
                 sfft_tuning t = cur;
+                t.ycorr_direct = 1;
                 t.ycorr_scalar = scalar;
                 t.ycorr_bins = kg;
                 r.push_back(t);
@@ -359,12 +371,17 @@ sfft_status sfft_autotune(const sfft_desc *desc, const void *sci, const void *tm
     for (int rd = 0; rd < 3 && result == SFFT_OK; rd++) {
         std::vector<sfft_tuning> cand;
         if (rd == 0) {
-            cand = rounds[0];
+            if (g0.yfft) cand = rounds[0];  // (a basis too large for the y-FFT kernels is direct already)
+            else
+                for (const sfft_tuning &t : rounds[0])
+                    if (t.ycorr_scalar == 1 || t.ycorr_bins != g0.kg_max) cand.push_back(t);
         } else if (rd == 1) {
             Geometry g = g0;
             apply_tuning(cur, g, err, sizeof err);
-            const int ys = g.ysplit, max_ys = std::max(1, g.ny / (2 * g.ytile));
+            const int ys = g.yfft ? g.y2split : g.ysplit;
+            const int max_ys = g.yfft ? 64 : std::max(1, g.ny / (2 * g.ytile));
             for (int v : {std::max(1, ys / 2), std::min(max_ys, 2 * ys), std::min(max_ys, ys + ys / 2)}) {
+                if (v == ys) continue;
                 sfft_tuning t = cur;
                 t.ycorr_split = v;
                 cand.push_back(t);

@@ -63,6 +63,15 @@ struct Geometry {
     int sub_per_sm;            // subtract / residual CTAs per SM the grid is sized for
     int pcg_cluster;           // PCG cluster size asked for (0: the largest available)
     long long spin_limit;      // iterations of a bounded device-side wait before it gives up
+    // y-direction correlation route: 1 = y-block FFTs of the base spectra (K1 writes the
+    // nbase x-weighted base images per record), 0 = direct correlation over the rows (K1
+    // writes the nimg yh^q-scaled images per record)
+    int yfft;
+    int nbase, nrec;           // base images per segment row; complex values per spectrum record
+    int Py, Uy, nyb;           // y-block FFT length, rows per block, blocks per segment
+    int npair_all;             // correlation pairs: npair W-W, then nk (nb + 1) W-(Psi|S)
+    int ypg, npg;              // pairs per y-FFT CTA, pair groups
+    int y2split, y2split_ws;   // y-FFT CTAs per frequency (main pass, refinement pass)
 };
 
 bool make_geometry(const sfft_desc &d, Geometry &g, char *err, size_t errlen);
@@ -75,10 +84,10 @@ int default_ysplit(const Geometry &g);
 struct Workspace {
     void *base = nullptr;
     size_t bytes = 0;
-    void *spec = nullptr;        // [nseg][ny][nkf][nimg_pad] complex (R)
-    double *ypart = nullptr;     // [nseg][ysplit][nkf][nent] complex FP64 (re, im interleaved)
+    void *spec = nullptr;        // [nseg][ny][nkf][nrec] complex (R)
+    double *ypart = nullptr;     // K2 partial sums, 16 bytes per complex value (see the K2 launchers)
     void *resid = nullptr;       // [ny][nx] residual image of the refinement pass (input dtype)
-    void *rspec = nullptr;       // FP32 path: [nseg][ny][nkf] complex spectrum of the residual (compact)
+    void *rspec = nullptr;       // [nseg][ny][nkf] complex spectrum of the residual (compact; FP32 path, or y-FFT route)
     double *ysum = nullptr;      // [nkf][nent] complex FP64
     double *lagww = nullptr;     // [npair][2L-1][2L-1]
     double *lagwg = nullptr;     // [nk][nb][L][L]
@@ -103,6 +112,8 @@ struct Workspace {
     void *xpow = nullptr;        // [pmax+1][nx] (R): xh^p, FP64 powers rounded once
     void *ypow = nullptr;        // [pmax+1][ny] (R): yh^q
     double *tw_x = nullptr;      // [nkf][2G+1] complex FP64: w_k exp(+2 pi i k m / P) / P
+    void *tw_y = nullptr;        // [2][Py] complex (R): exp(-2 pi i m / Py), high part then remainder
+    void *tw_yi = nullptr;       // [Py] exp(+2 pi i m / Py): FP32 (cos hi, sin hi, cos lo, sin lo) or FP64
 };
 
 size_t workspace_bytes(const Geometry &g, int precision, int dtype);
@@ -149,14 +160,25 @@ cudaError_t launch_moments(const Geometry &g, int dtype, int precision, const vo
 // K1 for one image (the refinement residual) written into image slot `slot` of spec
 cudaError_t launch_segment_fft_single(const Geometry &g, int dtype, int precision, const void *img,
                                       const void *tw_fft, int slot, void *spec, void *rspec, cudaStream_t st);
+// K2, y-block FFT route: cross-spectra of the image pairs summed over (segment, block) units,
+// one share per CTA -> part [split][nkf][pairs][Py] (16 bytes per value); ws: W_i x R only
+size_t yfft_smem_bytes(const Geometry &g, int precision, bool ws);
+cudaError_t launch_ycorr_fft(const Geometry &g, int precision, const void *spec, const void *rspec, const void *ypow,
+                             const void *tw_y, double *part, bool ws, cudaStream_t st);
+// the shares summed and inverted along y at the pairs' lags -> ysum [nkf][nent] (ws: W x S_m entries)
+cudaError_t launch_yinv(const Geometry &g, int precision, const double *part, const void *twi, double *ysum, bool ws,
+                        cudaStream_t st);
 // K2: y-direction correlations at the kernel lags, per segment and frequency -> ypart
 // (ws_only: only the W x S_m items)
+// (ypow: the FP32 yh^q table, read by the refinement kernel on the y-FFT route)
 cudaError_t launch_ycorr(const Geometry &g, int precision, const void *spec, double *ypart, bool ws_only, const void *rspec,
-                         cudaStream_t st);
+                         const void *ypow, cudaStream_t st);
 // K3: segment sum + x-direction inverse DFT at the kernel lags -> lag tables (ws_only: W x S_m only)
+// (have_ysum: ysum is already complete -- the y-FFT route -- and only the x-direction
+// inverse and the moment reduction run)
 cudaError_t launch_lag_tables(const Geometry &g, const double *ypart, double *ysum, const double *tw_x,
                               double *lagww, double *lagwg, double *lagws, const double *mom_part,
-                              double *mom, bool ws_only, bool pairs, cudaStream_t st);
+                              double *mom, bool ws_only, bool pairs, bool have_ysum, cudaStream_t st);
 // refinement right-hand side c = [lagws ; science-moment part of mom]
 cudaError_t launch_refine_rhs(const Geometry &g, const double *lagws, const double *mom, double *c,
                               cudaStream_t st);

@@ -390,10 +390,12 @@ cudaError_t launch_moments(const Geometry &g, int dtype, int precision, const vo
 
 cudaError_t launch_lag_tables(const Geometry &g, const double *ypart, double *ysum, const double *tw_x,
                               double *lagww, double *lagwg, double *lagws, const double *mom_part, double *mom,
-                              bool ws_only, bool pairs, cudaStream_t st) {
+                              bool ws_only, bool pairs, bool have_ysum, cudaStream_t st) {
     size_t total = (size_t)g.nkf * g.nent;
-    note_launch();
-    if (ws_only && pairs) {
+    if (!have_ysum) note_launch();
+    if (have_ysum) {
+        // the y-FFT route's inverse already wrote ysum
+    } else if (ws_only && pairs) {
         size_t per = (size_t)g.nkf * g.nk * g.L;  // one warp each
         k_ysum_ws<<<(unsigned)((per * 32 + 255) / 256), 256, 0, st>>>((const float4 *)ypart, g, (double2 *)ysum);
     } else {

@@ -6,7 +6,7 @@
 // (W_i = w_i T_m, w_i = xh^p yh^q) and takes their P-point real DFTs (forward,
 // exp(-2 pi i k j / P), unnormalised).  Two real images share one complex FFT; P = 256 is
 // done as 16 x 16 (a 16-point DFT in registers, a twiddle, one padded shared-memory
-// transpose, a second 16-point DFT).  Output: spec[s][k][y][img], k in [0, P/2].
+// transpose, a second 16-point DFT).  Output: spec[s][y][k][img], k in [0, P/2].
 //
 // These spectra feed the lag correlations of the normal matrix of the delta-basis fit
 // (SFFT subtraction step, Sec. "Pipeline steps", step 6).
@@ -110,19 +110,34 @@ constexpr int kEx = 16 * 17 + 1;
 //   b = 2(DK+1)+p    xh^p m on the window (p <= DB)
 //   b = nbase-1      S_m on the window
 // two to a complex FFT, and writes every output image from its base spectrum times yh^q.
+// Two real images packed into one complex FFT share its rounding, which is relative to the
+// larger of them: the star images (T, S) are up to ~1e5 times the mask images (m xh^p), so
+// the FFT slots keep the two families apart -- T-side and S images in slots 0 .. 2(DK+1)
+// (a zero pad after S), then the mask images (a zero pad if their count is odd).
 __host__ __device__ __forceinline__ int n_base(int dk, int db) { return 2 * (dk + 1) + (db + 1) + 1; }
+__host__ __device__ __forceinline__ int n_fft_slots(int dk, int db) { return 2 * (dk + 1) + 2 + 2 * ((db + 2) / 2); }
+// FFT slot of base image b
+__host__ __device__ __forceinline__ int slot_of_base(int b, int dk, int db) {
+    const int na = dk + 1;
+    if (b < 2 * na) return b;                  // A_p, B_p
+    if (b == n_base(dk, db) - 1) return 2 * na;  // S_m
+    return 2 * na + 2 + (b - 2 * na);          // m xh^p
+}
 
 // Spectra of every image of a row segment, rows_pp rows per pass.  Layout of the output:
-// spec[s][y][k][img] (a contiguous block of nkf * nimg_pad values per row segment).
+// spec[s][y][k][img] (a contiguous block of nkf * nrec values per row segment).  On the
+// y-FFT route the records hold the base images themselves (img = b, no yh^q factor: the
+// y correlation applies it); on the direct route every image W_i, Psi_r, S_m of the normal
+// matrix, each its base spectrum times yh^q.
 template <class R, class In, int MAXT, int MINB>
 __global__ void __launch_bounds__(MAXT, MINB) k_segment_fft(const In *__restrict__ sci, const In *__restrict__ tmpl,
                                                     const uint8_t *__restrict__ mask, Geometry g, int rows_pp,
                                                     const cpx<R> *__restrict__ tw_g, const R *__restrict__ xpow_g,
                                                     const R *__restrict__ ypow_g, cpx<R> *__restrict__ spec) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int nk = g.nk, nb = g.nb, G = g.G, U = g.U, nx = g.nx, ny = g.ny, NI = g.nimg_pad, nkf = g.nkf;
+    const int nk = g.nk, nb = g.nb, G = g.G, U = g.U, nx = g.nx, ny = g.ny, NI = g.nrec, nkf = g.nkf;
     const int maxdeg = g.dk > g.db ? g.dk : g.db;
-    const int nbase = n_base(g.dk, g.db), nbfft = (nbase + 1) / 2;
+    const int nbase = n_base(g.dk, g.db), nbfft = n_fft_slots(g.dk, g.db) / 2;
     const int s = blockIdx.x;
     const int x0 = s * U;
     const int tid = threadIdx.x, nthr = blockDim.x;
@@ -138,8 +153,8 @@ __global__ void __launch_bounds__(MAXT, MINB) k_segment_fft(const In *__restrict
     R *mv = sv + rows_pp * kP;                          // [rows_pp][P] m
     int *bk = reinterpret_cast<int *>(mv + rows_pp * kP);  // [2 nbfft] base kind
     int *bp = bk + 2 * nbfft;                           // [2 nbfft] base x power
-    int *ob = bp + 2 * nbfft;                           // [nimg_pad] base of each output image (-1: zero)
-    int *oq = ob + NI;                                  // [nimg_pad] y power of each output image
+    int *ob = bp + 2 * nbfft;                           // [nrec] base of each output image (-1: zero)
+    int *oq = ob + NI;                                  // [nrec] y power of each output image
     int *wcol = oq + NI;                                // [P] frame column of each window column
 
     for (int i = tid; i < kP; i += nthr) {
@@ -153,13 +168,14 @@ __global__ void __launch_bounds__(MAXT, MINB) k_segment_fft(const In *__restrict
         wcol[i] = xw;
     }
     for (int b = tid; b < 2 * nbfft; b += nthr) {
-        // kinds: 0 = A (own columns), 1 = B (window), 2 = m (window), 3 = S_m, 4 = zero pad
+        // kinds per FFT slot: 0 = A (own columns), 1 = B (window), 2 = m (window), 3 = S_m,
+        // 4 = zero pad
         const int na = g.dk + 1;
         int kind, p = 0;
         if (b < na) { kind = 0; p = b; }
         else if (b < 2 * na) { kind = 1; p = b - na; }
-        else if (b < 2 * na + g.db + 1) { kind = 2; p = b - 2 * na; }
-        else if (b == nbase - 1) { kind = 3; }
+        else if (b == 2 * na) { kind = 3; }
+        else if (b >= 2 * na + 2 && b < 2 * na + 2 + g.db + 1) { kind = 2; p = b - 2 * na - 2; }
         else { kind = 4; }
         bk[b] = kind;
         bp[b] = p;
@@ -167,11 +183,12 @@ __global__ void __launch_bounds__(MAXT, MINB) k_segment_fft(const In *__restrict
     for (int i = tid; i < NI; i += nthr) {
         const int na = g.dk + 1;
         int base = -1, p = 0, q = 0;
-        if (i < nk) { mono_pq(i, p, q); base = p; }
+        if (g.yfft) { base = i < nbase ? i : -1; }  // y-FFT route: the base images themselves
+        else if (i < nk) { mono_pq(i, p, q); base = p; }
         else if (i < 2 * nk) { mono_pq(i - nk, p, q); base = na + p; }
         else if (i < 2 * nk + nb) { mono_pq(i - 2 * nk, p, q); base = 2 * na + p; }
         else if (i == 2 * nk + nb) { base = nbase - 1; q = 0; }
-        ob[i] = base;
+        ob[i] = base < 0 ? -1 : slot_of_base(base, g.dk, g.db);  // the FFT slot it is unpacked from
         oq[i] = q;
     }
 
@@ -331,7 +348,7 @@ __global__ void __launch_bounds__(128) k_segment_fft_single(const In *__restrict
                                                            cpx<R> *__restrict__ spec, cpx<R> *__restrict__ rspec) {
     __shared__ cpx<R> tw[kP], twl[kP];
     __shared__ cpx<R> ex[8][kEx];
-    const int G = g.G, nx = g.nx, ny = g.ny, NI = g.nimg_pad, nkf = g.nkf;
+    const int G = g.G, nx = g.nx, ny = g.ny, NI = g.nrec, nkf = g.nkf;
     const int s = blockIdx.x, x0 = s * g.U;
     for (int i = threadIdx.x; i < kP; i += blockDim.x) {
         tw[i] = tw_g[i];
@@ -374,7 +391,7 @@ struct SegLaunch {
     int rows_pp, threads;
 };
 SegLaunch seg_launch(const Geometry &g) {
-    const int nbfft = (n_base(g.dk, g.db) + 1) / 2;
+    const int nbfft = n_fft_slots(g.dk, g.db) / 2;
     SegLaunch l;
     l.rows_pp = std::max(1, std::min(kMaxRowsPP, 384 / (nbfft * 16)));
     l.threads = std::max(256, (l.rows_pp * nbfft * 16 + 31) / 32 * 32);
@@ -384,10 +401,10 @@ SegLaunch seg_launch(const Geometry &g) {
 template <class R>
 size_t segfft_smem(const Geometry &g, int rows_pp) {
     const int maxdeg = g.dk > g.db ? g.dk : g.db;
-    const int nbfft = (n_base(g.dk, g.db) + 1) / 2;
+    const int nbfft = n_fft_slots(g.dk, g.db) / 2;
     return sizeof(cpx<R>) * (2 * kP + (size_t)rows_pp * nbfft * kEx) +
            sizeof(R) * ((size_t)(maxdeg + 2) * kP + 3 * (size_t)rows_pp * kP) +
-           sizeof(int) * (4 * nbfft + 2 * g.nimg_pad + kP);
+           sizeof(int) * (4 * nbfft + 2 * g.nrec + kP);
 }
 
 template <class R, class In>
@@ -431,7 +448,7 @@ cudaError_t launch_segment_fft_single(const Geometry &g, int dtype, int precisio
 cudaError_t launch_segment_fft(const Geometry &g, int dtype, int precision, const void *sci, const void *tmpl,
                                const uint8_t *mask, const void *tw_fft, const void *xpow, const void *ypow,
                                void *spec, cudaStream_t st) {
-    if (g.P != kP || n_base(g.dk, g.db) > 48) return cudaErrorInvalidValue;
+    if (g.P != kP || n_fft_slots(g.dk, g.db) > 48) return cudaErrorInvalidValue;
     if (precision == SFFT_PREC_FP64) {
         return dtype == SFFT_F64 ? run<double, double>(g, sci, tmpl, mask, tw_fft, xpow, ypow, spec, st)
                                  : run<double, float>(g, sci, tmpl, mask, tw_fft, xpow, ypow, spec, st);

@@ -412,10 +412,13 @@ __global__ void __launch_bounds__(256) k_ycorr_f64(const cpx<double> *__restrict
 // from global memory with the L residual values of the lag window in a rotating register
 // window (the loop is unrolled by C so the rotation is free).  Output: (hi, lo) float pairs
 // per (segment, chunk, frequency, i, dy) -> wspart.
+// On the y-FFT route the spectrum records hold the x-weighted base images: W_i = yh^q xh^p
+// T_m is then yh(y)^q times the A-side base p, applied per row here (ypow: the FP32 table).
 template <int C>
 __global__ void __launch_bounds__(256) k_ycorr_ws(const cpx<float> *__restrict__ spec, const cpx<float> *__restrict__ rspec,
-                                                 Geometry g, int ychunks, float4 *__restrict__ wspart) {
-    const int nk = g.nk, nkf = g.nkf, ny = g.ny, NI = g.nimg_pad, h = g.h;
+                                                 Geometry g, int ychunks, float4 *__restrict__ wspart,
+                                                 const float *__restrict__ ypow) {
+    const int nk = g.nk, nkf = g.nkf, ny = g.ny, NI = g.nrec, h = g.h;
     const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
     const long total = (long)g.nseg * ychunks * nkf * nk;
     if (t >= total) return;
@@ -426,6 +429,9 @@ __global__ void __launch_bounds__(256) k_ycorr_ws(const cpx<float> *__restrict__
     const int chunk = (ny + ychunks - 1) / ychunks;
     const int ya = ych * chunk, yb = min(ny, ya + chunk);
     const size_t rowstride = (size_t)nkf * NI;  // complex values between consecutive rows
+    int slot = i, qy = 0;                       // record slot of W_i and its row power
+    if (g.yfft) mono_pq(i, slot, qy);
+    const float *yqr = qy ? ypow + (size_t)qy * ny : nullptr;
     const cpx<float> *base = spec + ((size_t)s * ny * nkf + k) * NI;
     const cpx<float> *rbase = rspec + (size_t)s * ny * nkf + k;  // the residual, compact: row stride nkf
     float2 acc[C], hi[C], lo[C], w[C];
@@ -451,9 +457,10 @@ __global__ void __launch_bounds__(256) k_ycorr_ws(const cpx<float> *__restrict__
             int yy = y + u + h;
             yy = yy >= ny ? yy - ny : yy;
             const cpx<float> v = ok ? rbase[(size_t)yy * nkf] : cpx<float>{0.f, 0.f};
-            const cpx<float> a = ok ? base[(size_t)(y + u) * rowstride + i] : cpx<float>{0.f, 0.f};
+            const cpx<float> a = ok ? base[(size_t)(y + u) * rowstride + slot] : cpx<float>{0.f, 0.f};
+            const float w = (ok && yqr) ? yqr[y + u] : 1.f;
             rin[u] = make_float2(v.re, v.im);
-            av[u] = make_float2(a.re, a.im);
+            av[u] = make_float2(a.re * w, a.im * w);
         }
 #pragma unroll
         for (int u = 0; u < C; u++) {
@@ -489,18 +496,20 @@ __global__ void __launch_bounds__(256) k_ycorr_ws(const cpx<float> *__restrict__
 }
 
 template <int C>
-cudaError_t run_ws(const Geometry &g, const void *spec, const void *rspec, float4 *wspart, cudaStream_t st) {
+cudaError_t run_ws(const Geometry &g, const void *spec, const void *rspec, float4 *wspart, const void *ypow,
+                   cudaStream_t st) {
     const long total = (long)g.nseg * g.ychunks_ws * g.nkf * g.nk;
     note_launch();
     k_ycorr_ws<C><<<(unsigned)((total + 255) / 256), 256, 0, st>>>((const cpx<float> *)spec, (const cpx<float> *)rspec, g,
-                                                                  g.ychunks_ws, wspart);
+                                                                  g.ychunks_ws, wspart, (const float *)ypow);
     return cudaGetLastError();
 }
 
 template <int C>
 cudaError_t run(const Geometry &g, int precision, const void *spec, double *ypart, bool ws_only, const void *rspec,
-                cudaStream_t st) {
-    if (ws_only && precision != SFFT_PREC_FP64) return run_ws<C>(g, spec, rspec, reinterpret_cast<float4 *>(ypart), st);
+                const void *ypow, cudaStream_t st) {
+    if (ws_only && precision != SFFT_PREC_FP64)
+        return run_ws<C>(g, spec, rspec, reinterpret_cast<float4 *>(ypart), ypow, st);
     Launch ln;
     ln.ws_only = ws_only;
     ln.items = ws_only ? g.nk : g.items_per_k;
@@ -535,16 +544,19 @@ cudaError_t run(const Geometry &g, int precision, const void *spec, double *ypar
 }  // namespace
 
 cudaError_t launch_ycorr(const Geometry &g, int precision, const void *spec, double *ypart, bool ws_only,
-                         const void *rspec, cudaStream_t st) {
+                         const void *rspec, const void *ypow, cudaStream_t st) {
+    // the direct kernels of the main pass read the per-image records only; the refinement's
+    // W x R kernel reads either layout
+    if (g.yfft && !(ws_only && precision != SFFT_PREC_FP64)) return cudaErrorInvalidValue;
     switch (g.C) {
-        case 1: return run<1>(g, precision, spec, ypart, ws_only, rspec, st);
-        case 3: return run<3>(g, precision, spec, ypart, ws_only, rspec, st);
-        case 5: return run<5>(g, precision, spec, ypart, ws_only, rspec, st);
-        case 7: return run<7>(g, precision, spec, ypart, ws_only, rspec, st);
-        case 9: return run<9>(g, precision, spec, ypart, ws_only, rspec, st);
-        case 11: return run<11>(g, precision, spec, ypart, ws_only, rspec, st);
-        case 13: return run<13>(g, precision, spec, ypart, ws_only, rspec, st);
-        case 15: return run<15>(g, precision, spec, ypart, ws_only, rspec, st);
+        case 1: return run<1>(g, precision, spec, ypart, ws_only, rspec, ypow, st);
+        case 3: return run<3>(g, precision, spec, ypart, ws_only, rspec, ypow, st);
+        case 5: return run<5>(g, precision, spec, ypart, ws_only, rspec, ypow, st);
+        case 7: return run<7>(g, precision, spec, ypart, ws_only, rspec, ypow, st);
+        case 9: return run<9>(g, precision, spec, ypart, ws_only, rspec, ypow, st);
+        case 11: return run<11>(g, precision, spec, ypart, ws_only, rspec, ypow, st);
+        case 13: return run<13>(g, precision, spec, ypart, ws_only, rspec, ypow, st);
+        case 15: return run<15>(g, precision, spec, ypart, ws_only, rspec, ypow, st);
         default: return cudaErrorInvalidValue;
     }
 }

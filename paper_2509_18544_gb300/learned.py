@@ -24,34 +24,42 @@ def n_kernel(L: int, dk: int) -> int:
 
 
 def make_training_set(n: int, seed: int, size: int = 256, L: int = 11, dk: int = 2, db: int = 2,
-                      device: str = "cuda"):
+                      device: str = "cuda", workers: int = 0, chunk: int = 128):
     """(stamps [n][18][32][32] float32, targets [n][L^2 nP(dk)] float32, full coefficients
-    [n][n_unknowns] float64), all on the device."""
+    [n][n_unknowns] float64), all on the device.
+
+    The frames and stamps are drawn on the host (``synth.training_sample``), in `workers`
+    processes (0: one per host core, up to 16; started with "spawn", so no CUDA state is
+    forked) a chunk at a time; each chunk is copied to the device in one transfer per array
+    and fitted by queued sfft_fit calls while the workers draw the next chunks."""
+    import multiprocessing as mp
+    import os
+
     dev = torch.device(device)
     nk = n_kernel(L, dk)
     stamps = torch.empty((n, 18, synth.STAMP, synth.STAMP), dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    nw = workers if workers > 0 else max(1, min(16, (os.cpu_count() or 2) - 1))
+    jobs = [(seed + s0, min(chunk, n - s0), size) for s0 in range(0, n, chunk)]
     # the targets need no refinement: the plain FP32 mode is well inside the network's error
     with sfft.sfft_plan(sfft.make_desc(size, size, L, dk, db, precision=sfft.PREC_FP32, solver=sfft.SOLVE_PCG),
-                        stream=torch.cuda.current_stream(dev)) as plan:
+                        stream=stream) as plan:
         coeffs = torch.empty((n, plan.n), dtype=torch.float64, device=dev)
-        S_h = torch.empty((size, size), dtype=torch.float32).pin_memory()
-        T_h = torch.empty_like(S_h).pin_memory()
-        st_h = torch.empty((18, synth.STAMP, synth.STAMP), dtype=torch.float32).pin_memory()
-        S_d = torch.empty((size, size), dtype=torch.float32, device=dev)
+        S_d = torch.empty((chunk, size, size), dtype=torch.float32, device=dev)
         T_d = torch.empty_like(S_d)
-        for i in range(n):
-            field = synth.psf_field(seed + i)
-            S, T = synth.psf_grid_pair(field, seed=seed + i, size=size)
-            # the previous sample's copies and fit are queued on the same stream; wait for
-            # them before the pinned staging buffers are rewritten
-            torch.cuda.current_stream(dev).synchronize()
-            S_h.numpy()[...] = S
-            T_h.numpy()[...] = T
-            st_h.numpy()[...] = synth.psf_stamps(field)
-            S_d.copy_(S_h, non_blocking=True)
-            T_d.copy_(T_h, non_blocking=True)
-            stamps[i].copy_(st_h, non_blocking=True)
-            sfft.sfft_fit(plan, S_d, T_d, None, None, coeffs[i], want_info=False)
+        ctx = mp.get_context("spawn")
+        with ctx.Pool(nw) as pool:
+            s0 = 0
+            for Sc, Tc, stc in pool.imap(synth.training_chunk, jobs):
+                c = Sc.shape[0]
+                # the previous chunk's fits read S_d, T_d: wait for them before the copies
+                stream.synchronize()
+                S_d[:c].copy_(torch.from_numpy(Sc))
+                T_d[:c].copy_(torch.from_numpy(Tc))
+                stamps[s0:s0 + c].copy_(torch.from_numpy(stc))
+                for i in range(c):
+                    sfft.sfft_fit(plan, S_d[i], T_d[i], None, None, coeffs[s0 + i], want_info=False)
+                s0 += c
         sfft.sfft_sync_status(plan)
     targets = coeffs[:, :nk].to(torch.float32).contiguous()
     return stamps, targets, coeffs

@@ -24,6 +24,7 @@ EXPORTED = ("sfft_plan", "sfft_destroy", "sfft_n_unknowns", "sfft_workspace_size
             "sfft_batch_create", "sfft_batch_run", "sfft_batch_info", "sfft_batch_destroy",
             "sfft_tuning_get", "sfft_tuning_set", "sfft_autotune", "sfft_tuning_save", "sfft_tuning_load",
             "sfft_profile", "sfft_stage_times", "sfft_launch_count", "sfft_subtract_noalloc",
+            "sfft_cross_convolve",
             "sfft_status_string", "sfft_last_error",
             "sfft_cnn_create", "sfft_cnn_destroy", "sfft_cnn_param_count", "sfft_cnn_set_params",
             "sfft_cnn_get_params", "sfft_cnn_forward", "sfft_cnn_gradients", "sfft_cnn_train_step",
@@ -66,7 +67,8 @@ class sfft_pair(ctypes.Structure):
 class sfft_tuning(ctypes.Structure):
     _fields_ = [("ycorr_bins", ctypes.c_int32), ("ycorr_split", ctypes.c_int32),
                 ("ycorr_scalar", ctypes.c_int32), ("subtract_ctas", ctypes.c_int32),
-                ("pcg_cluster", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+                ("pcg_cluster", ctypes.c_int32), ("ycorr_direct", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 2)]
 
 
 BATCH_GRAPH, BATCH_AUTOTUNE = 1, 2
@@ -110,6 +112,7 @@ def load_library(path: str = LIB_PATH):
         lib.sfft_tuning_save.argtypes = [ctypes.c_char_p]
         lib.sfft_tuning_load.argtypes = [ctypes.c_char_p]
         lib.sfft_subtract_noalloc.argtypes = [ctypes.POINTER(sfft_desc), P, P, P, P, P]
+        lib.sfft_cross_convolve.argtypes = [I32, I32, I32, I32, I32, P, P, P, P, P, P, P]
         lib.sfft_profile.argtypes = [P, I32]
         lib.sfft_stage_times.argtypes = [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(I32)]
         lib.sfft_launch_count.argtypes = [ctypes.POINTER(ctypes.c_uint64)]
@@ -368,6 +371,14 @@ def sfft_launch_count() -> int:
     v = ctypes.c_uint64()
     _check(load_library().sfft_launch_count(ctypes.byref(v)))
     return v.value
+
+
+def sfft_cross_convolve(ny: int, nx: int, K: int, sci, tmpl, psf_sci, psf_tmpl, sci_out, tmpl_out, dtype: int = F32,
+                        pitch: int = 0, stream=None):
+    """sci_out = sci (x) psf_tmpl and tmpl_out = tmpl (x) psf_sci: cyclic convolutions with
+    K x K float32 stamps (device); a half whose image, stamp or output is None is skipped."""
+    _check(load_library().sfft_cross_convolve(ny, nx, pitch, dtype, K, _ptr(sci), _ptr(tmpl), _ptr(psf_sci),
+                                              _ptr(psf_tmpl), _ptr(sci_out), _ptr(tmpl_out), _stream(stream)))
 
 
 def sfft_subtract_noalloc(desc: sfft_desc, sci, tmpl, coeffs, diff, stream=None):

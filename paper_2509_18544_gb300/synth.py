@@ -100,12 +100,17 @@ def gaussian_pair(seed: int = 0, size: int = 64, n_stars: int = 30):
 
 def roman_pair(ny: int = 4088, nx: int = 4088, seed: int = 1000, n_stars: int | None = None,
                fwhm=(1.8, 2.4), sky: float = 80.0, mask_frac: float = 0.005,
-               flux_mode: str = "lognormal", dtype=np.float32, radius: int = 12):
+               flux_mode: str = "lognormal", dtype=np.float32, radius: int = 12, field=None):
     """Roman-like pair: returns (sci, tmpl, mask) with mask bytes 1 = masked.
 
     ``n_stars`` defaults to 3000 per 4088^2 frame, scaled by area.  ``flux_mode`` is
     "lognormal" (exp N(8, 1) e-) or "dynamic" (log-uniform over 1e2..1e7 e-, a 1e5 range).
+    ``field`` (a PSF-field pair as ``psf_field`` / ``roman_field`` return) draws each star
+    with the field's PSF at its position instead of the default fields (FWHM along x in the
+    template, along y in the science image).
     """
+    if field is not None:
+        return _roman_pair_field(ny, nx, seed, n_stars, field, sky, mask_frac, flux_mode, dtype, radius)
     rng = np.random.Generator(np.random.PCG64(seed))
     if n_stars is None:
         n_stars = max(1, int(round(3000 * ny * nx / 4088.0 ** 2)))
@@ -135,6 +140,53 @@ def roman_pair(ny: int = 4088, nx: int = 4088, seed: int = 1000, n_stars: int | 
     m2 = rng.random((ny, nx)) < mask_frac
     mask = (m1 | m2).astype(np.uint8)
     return sci.astype(dtype), tmpl.astype(dtype), mask
+
+
+def _roman_pair_field(ny, nx, seed, n_stars, field, sky, mask_frac, flux_mode, dtype, radius):
+    """``roman_pair`` with the stars drawn by a given pair of PSF fields (same random stream
+    for positions, fluxes, noise and masks)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    if n_stars is None:
+        n_stars = max(1, int(round(3000 * ny * nx / 4088.0 ** 2)))
+    xs = rng.uniform(0, nx, n_stars)
+    ys = rng.uniform(0, ny, n_stars)
+    if flux_mode == "lognormal":
+        flux = np.exp(rng.normal(8.0, 1.0, n_stars))
+    elif flux_mode == "dynamic":
+        flux = 10.0 ** rng.uniform(2.0, 7.0, n_stars)
+    else:
+        raise ValueError(flux_mode)
+    xh = 2.0 * xs / max(nx - 1, 1) - 1.0
+    yh = 2.0 * ys / max(ny - 1, 1) - 1.0
+    models = {}
+    for key in ("tmpl", "sci"):
+        fd = field[key]
+        al = moffat_alpha(_fwhm_at(fd, xh, yh))
+        models[key] = np.zeros(ny * nx)
+        for s0 in range(0, n_stars, 512):
+            sl = slice(s0, s0 + 512)
+            models[key] += _render_signed(ny, nx, xs[sl], ys[sl], flux[sl], al[sl], fd["e"], fd["phi"],
+                                          radius).ravel()
+    tmpl = rng.poisson(models["tmpl"].reshape(ny, nx) + sky).astype(np.float64) - sky
+    sci = rng.poisson(models["sci"].reshape(ny, nx) + sky).astype(np.float64) - sky
+    m1 = rng.random((ny, nx)) < mask_frac
+    m2 = rng.random((ny, nx)) < mask_frac
+    mask = (m1 | m2).astype(np.uint8)
+    return sci.astype(dtype), tmpl.astype(dtype), mask
+
+
+def linear_field(theta_sci: float, theta_tmpl: float, fwhm=(1.8, 2.4)):
+    """Round Moffat fields whose FWHM runs linearly from fwhm[0] to fwhm[1] across the frame
+    along the direction theta (radians from the x axis), one direction per image;
+    ``roman_field`` is theta_sci = pi/2, theta_tmpl = 0."""
+    c, g = 0.5 * (fwhm[0] + fwhm[1]), 0.5 * (fwhm[1] - fwhm[0])
+
+    def one(th):
+        cx, sy = np.cos(th), np.sin(th)
+        n = abs(cx) + abs(sy)  # the extreme of cx xh + sy yh over [-1, 1]^2
+        return dict(f0=c, fx=g * cx / n, fy=g * sy / n, e=0.0, phi=0.0)
+
+    return dict(sci=one(theta_sci), tmpl=one(theta_tmpl))
 
 
 def cutout_sizes(n: int, seed: int, choices=(512, 1024, 1536, 2048)):
@@ -246,6 +298,22 @@ def _render_signed(ny, nx, xs, ys, flux, alpha, e, phi, radius):
     prof *= flux[:, None, None]
     np.add.at(img, (np.mod(py, ny) * nx + np.mod(px, nx)).ravel(), prof.ravel())
     return img.reshape(ny, nx)
+
+
+def training_sample(seed: int, size: int = 256):
+    """One training sample of the warm-start network: (sci, tmpl, stamps) float32 for the PSF
+    field pair ``psf_field(seed)`` (frames from ``psf_grid_pair``, stamps from ``psf_stamps``)."""
+    field = psf_field(seed)
+    S, T = psf_grid_pair(field, seed=seed, size=size)
+    return S, T, psf_stamps(field)
+
+
+def training_chunk(args):
+    """Training samples seed0 .. seed0 + count - 1 stacked: (sci, tmpl, stamps).  A process-
+    pool worker function: it needs numpy only."""
+    seed0, count, size = args
+    out = [training_sample(seed0 + i, size) for i in range(count)]
+    return tuple(np.stack([o[j] for o in out]) for j in range(3))
 
 
 def cnn_init(n_out: int, seed: int) -> np.ndarray:

@@ -41,10 +41,12 @@ def test_every_declared_symbol_is_exported(lib):
 def test_workspace_size_and_validation_on_host(lib):
     d = sfft.make_desc(4088, 4088, 11, 2, 2)
     ws = sfft.sfft_workspace_size(d)
-    # spectra dominate: 18 segments x 129 bins x 4088 rows x 20 images x 8 bytes; the rest is
-    # the y-correlation partials, the refinement's residual image and its compact spectrum
-    # (67 + 76 MB) and small tables
-    assert 18 * 129 * 4088 * 20 * 8 < ws < 18 * 129 * 4088 * 20 * 8 + 300 * 2 ** 20
+    # spectra dominate: 18 segments x 129 bins x 4088 rows x 10 base images x 8 bytes; the rest
+    # is the y-correlation partials (at most 16 CTAs per frequency x 129 x 63 pairs x 128 x 16
+    # bytes), the refinement's residual image and its compact spectrum (67 + 76 MB) and small
+    # tables
+    spec = 18 * 129 * 4088 * 10 * 8
+    assert spec < ws < spec + 16 * 129 * 63 * 128 * 16 + 300 * 2 ** 20
     for bad in (dict(L=4), dict(L=0), dict(ny=3, L=5), dict(dk=-1), dict(dtype=7), dict(precision=9),
                 dict(pitch=10, nx=20)):
         kw = dict(ny=64, nx=64, L=5, dk=0, db=0)

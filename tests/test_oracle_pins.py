@@ -313,3 +313,27 @@ def test_band_lag_tables_are_row_restricted_sums():
     assert got == pytest.approx(want, rel=1e-12)
     with pytest.raises(oracle.OracleError):
         oracle.lag_tables_band(S, T, m, L, dk, db, 5, 5)
+
+
+def test_convolution_pins():
+    """Cross-convolution oracle: a centred delta is the identity, an off-centre delta is a
+    cyclic shift (np.roll), and a random stamp equals numpy's FFT convolution (a library
+    primitive) with the stamp placed cyclically around the origin."""
+    rng = np.random.default_rng(3)
+    X = rng.normal(size=(21, 17))
+    K = 5
+    P = np.zeros((K, K))
+    P[2, 2] = 1.0
+    assert np.array_equal(oracle.convolve(X, P), X)
+    P = np.zeros((K, K))
+    P[0, 3] = 1.0  # d = (-2, +1): out(u) = X(u - d)
+    assert np.allclose(oracle.convolve(X, P), np.roll(X, shift=(-2, 1), axis=(0, 1)), rtol=0, atol=1e-15)
+    P = rng.normal(size=(7, 7))
+    kimg = np.zeros_like(X)
+    for a in range(7):
+        for b in range(7):
+            kimg[(a - 3) % 21, (b - 3) % 17] += P[a, b]
+    ref = np.real(np.fft.ifft2(np.fft.fft2(X) * np.fft.fft2(kimg)))
+    assert np.allclose(oracle.convolve(X, P), ref, rtol=1e-12, atol=1e-12)
+    with pytest.raises(oracle.OracleError):
+        oracle.convolve(X, np.ones((4, 4)))
