@@ -290,15 +290,16 @@ __global__ void __launch_bounds__(MAXT, MINB) k_segment_fft(const In *__restrict
         // unpack the packed real pairs, scale by yh^q; each row segment is one contiguous block
         const int per_out = nkf * NI;
         const int nrow = min(rows_pp, yend - y0);
-        if (nthr % NI == 0) {
+        const int nun = (nthr / NI) * NI;  // threads that unpack: whole sets of NI
+        if (nun > 0) {
             // every thread keeps one image and walks the bins (consecutive threads write
             // consecutive values), so no index is divided per value
-            const int img = tid % NI, kstep = nthr / NI;
+            const int img = tid % NI, kstep = nun / NI;
             const int b = ob[img];
             const bool odd = b & 1;
 #pragma unroll
             for (int rr = 0; rr < kMaxRowsPP; rr++) {
-                if (rr >= nrow) break;
+                if (rr >= nrow || tid >= nun) break;
                 const int y = y0 + rr;
                 const cpx<R> *e = ex + (rr * nbfft + (b < 0 ? 0 : b >> 1)) * kEx;
                 cpx<R> *o = spec + ((size_t)s * ny + y) * per_out + img;

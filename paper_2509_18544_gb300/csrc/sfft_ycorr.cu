@@ -414,7 +414,7 @@ __global__ void __launch_bounds__(256) k_ycorr_f64(const cpx<double> *__restrict
 // per (segment, chunk, frequency, i, dy) -> wspart.
 // On the y-FFT route the spectrum records hold the x-weighted base images: W_i = yh^q xh^p
 // T_m is then yh(y)^q times the A-side base p, applied per row here (ypow: the FP32 table).
-template <int C>
+template <int C, bool BASE>
 __global__ void __launch_bounds__(256) k_ycorr_ws(const cpx<float> *__restrict__ spec, const cpx<float> *__restrict__ rspec,
                                                  Geometry g, int ychunks, float4 *__restrict__ wspart,
                                                  const float *__restrict__ ypow) {
@@ -430,8 +430,8 @@ __global__ void __launch_bounds__(256) k_ycorr_ws(const cpx<float> *__restrict__
     const int ya = ych * chunk, yb = min(ny, ya + chunk);
     const size_t rowstride = (size_t)nkf * NI;  // complex values between consecutive rows
     int slot = i, qy = 0;                       // record slot of W_i and its row power
-    if (g.yfft) mono_pq(i, slot, qy);
-    const float *yqr = qy ? ypow + (size_t)qy * ny : nullptr;
+    if (BASE) mono_pq(i, slot, qy);
+    const float *yqr = ypow + (size_t)qy * ny;  // row 0 of the table is all ones
     const cpx<float> *base = spec + ((size_t)s * ny * nkf + k) * NI;
     const cpx<float> *rbase = rspec + (size_t)s * ny * nkf + k;  // the residual, compact: row stride nkf
     float2 acc[C], hi[C], lo[C], w[C];
@@ -458,9 +458,13 @@ __global__ void __launch_bounds__(256) k_ycorr_ws(const cpx<float> *__restrict__
             yy = yy >= ny ? yy - ny : yy;
             const cpx<float> v = ok ? rbase[(size_t)yy * nkf] : cpx<float>{0.f, 0.f};
             const cpx<float> a = ok ? base[(size_t)(y + u) * rowstride + slot] : cpx<float>{0.f, 0.f};
-            const float w = (ok && yqr) ? yqr[y + u] : 1.f;
             rin[u] = make_float2(v.re, v.im);
-            av[u] = make_float2(a.re * w, a.im * w);
+            if (BASE) {
+                const float w = ok ? yqr[y + u] : 0.f;
+                av[u] = make_float2(a.re * w, a.im * w);
+            } else {
+                av[u] = make_float2(a.re, a.im);
+            }
         }
 #pragma unroll
         for (int u = 0; u < C; u++) {
@@ -500,8 +504,12 @@ cudaError_t run_ws(const Geometry &g, const void *spec, const void *rspec, float
                    cudaStream_t st) {
     const long total = (long)g.nseg * g.ychunks_ws * g.nkf * g.nk;
     note_launch();
-    k_ycorr_ws<C><<<(unsigned)((total + 255) / 256), 256, 0, st>>>((const cpx<float> *)spec, (const cpx<float> *)rspec, g,
-                                                                  g.ychunks_ws, wspart, (const float *)ypow);
+    if (g.yfft)
+        k_ycorr_ws<C, true><<<(unsigned)((total + 255) / 256), 256, 0, st>>>(
+            (const cpx<float> *)spec, (const cpx<float> *)rspec, g, g.ychunks_ws, wspart, (const float *)ypow);
+    else
+        k_ycorr_ws<C, false><<<(unsigned)((total + 255) / 256), 256, 0, st>>>(
+            (const cpx<float> *)spec, (const cpx<float> *)rspec, g, g.ychunks_ws, wspart, (const float *)ypow);
     return cudaGetLastError();
 }
 
