@@ -45,10 +45,10 @@ def parse():
     ap.add_argument("--pairs", type=int, default=8, help="pairs per step per rank")
     ap.add_argument("--lanes", type=int, default=8, help="streams of the batched form (at most --pairs)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--train-samples", type=int, default=2048, help="warm-start network training fits")
+    ap.add_argument("--train-samples", type=int, default=20000, help="warm-start network training fits")
     ap.add_argument("--frame", type=int, default=NY, help="frame side (smaller frames are for profiling runs)")
     ap.add_argument("--plain-only", action="store_true", help="time the plain form only (profiling runs)")
-    ap.add_argument("--train-epochs", type=int, default=40)
+    ap.add_argument("--train-epochs", type=int, default=8)
     ap.add_argument("--pcg-cluster", type=int, default=0, choices=[0, 8, 16],
                     help="PCG cluster size for the batched form (0: the tuner's / largest available)")
     ap.add_argument("--workload", default="roman4088",
@@ -249,11 +249,11 @@ def run_ours(args, world, rank, local):
     del tr_stamps, tr_targets
     # each pair's own PSF fields
     stamps = torch.from_numpy(np.stack([synth.psf_stamps(pair_field(sd)) for sd in seeds])).to(dev)
-    x0 = torch.zeros((args.pairs, n), dtype=torch.float64, device=dev)
     bcoeffs = [torch.empty(n, dtype=torch.float64, device=dev) for _ in pairs]
     bdiffs = [torch.empty((NY, NX), dtype=torch.float32, device=dev) for _ in pairs]
-    sfft.sfft_cnn_warm_start(cnn, stamps, args.pairs, n, x0)
-    bpairs = [sfft.make_pair(S, T, M, th, D, NY, NX, x0=x0[k])
+    # the network runs inside the batch: each run evaluates it on the pairs' stamps and starts
+    # their PCG solves from its warm starts
+    bpairs = [sfft.make_pair(S, T, M, th, D, NY, NX, stamps=stamps[k])
               for k, ((S, T, M), th, D) in enumerate(zip(dev_pairs, bcoeffs, bdiffs))]
     if args.pcg_cluster:
         tn = sfft.sfft_tuning()
@@ -262,12 +262,11 @@ def run_ours(args, world, rank, local):
     t0 = time.perf_counter()
     batch = sfft.sfft_batch_create(sfft.make_desc(NY, NX, L, DK, DB, solver=sfft.SOLVE_PCG), bpairs,
                                    lanes=min(args.pairs, args.lanes), flags=sfft.BATCH_GRAPH | sfft.BATCH_AUTOTUNE,
-                                   stream=stream)
+                                   stream=stream, cnn=cnn)
     create_s = time.perf_counter() - t0
     tuning, _ = sfft.sfft_tuning_get(sfft.make_desc(NY, NX, L, DK, DB, solver=sfft.SOLVE_PCG))
 
     def batched_step():
-        sfft.sfft_cnn_warm_start(cnn, stamps, args.pairs, n, x0)
         sfft.sfft_batch_run(batch)
 
     for _ in range(args.warmup):
@@ -282,6 +281,18 @@ def run_ours(args, world, rank, local):
     value = weak_value(args.steps, args.pairs, world, ms)
     binfos = sfft.sfft_batch_info(batch)
 
+    # ---- the same batch from cold starts (no warm start): what the network contributes
+    cold_pairs = [sfft.make_pair(S, T, M, th, D, NY, NX)
+                  for (S, T, M), th, D in zip(dev_pairs, bcoeffs, bdiffs)]
+    cold = sfft.sfft_batch_create(sfft.make_desc(NY, NX, L, DK, DB, solver=sfft.SOLVE_PCG), cold_pairs,
+                                  lanes=min(args.pairs, args.lanes), flags=sfft.BATCH_GRAPH, stream=stream)
+    for _ in range(args.warmup):
+        sfft.sfft_batch_run(cold)
+    cold_ms = timed(lambda: sfft.sfft_batch_run(cold), args.steps, "cold")
+    cold_value = weak_value(args.steps, args.pairs, world, cold_ms)
+    cinfos = sfft.sfft_batch_info(cold)
+    cold.close()
+
     # ---- end to end through the public API with pinned host buffers (batched + learned): a
     # second batch whose pairs carry their host buffers, so each lane copies its pair's inputs
     # in before the fit and D and theta out after the subtraction, overlapping other lanes
@@ -291,13 +302,13 @@ def run_ours(args, world, rank, local):
     e2e_in = [tuple(torch.empty_like(t) for t in p) for p in dev_pairs]
     e2e_th = [torch.empty(n, dtype=torch.float64, device=dev) for _ in pairs]
     e2e_D = [torch.empty((NY, NX), dtype=torch.float32, device=dev) for _ in pairs]
-    e2e_pairs = [sfft.make_pair(dS, dT, dM, th, D, NY, NX, x0=x0[k], host=host[k])
+    e2e_pairs = [sfft.make_pair(dS, dT, dM, th, D, NY, NX, host=host[k], stamps=stamps[k])
                  for k, ((dS, dT, dM), th, D) in enumerate(zip(e2e_in, e2e_th, e2e_D))]
     e2e_batch = sfft.sfft_batch_create(sfft.make_desc(NY, NX, L, DK, DB, solver=sfft.SOLVE_PCG), e2e_pairs,
-                                       lanes=min(args.pairs, args.lanes), flags=sfft.BATCH_GRAPH, stream=stream)
+                                       lanes=min(args.pairs, args.lanes), flags=sfft.BATCH_GRAPH, stream=stream,
+                                       cnn=cnn)
 
     def e2e_step():
-        sfft.sfft_cnn_warm_start(cnn, stamps, args.pairs, n, x0)
         sfft.sfft_batch_run(e2e_batch)
 
     for _ in range(2):
@@ -309,31 +320,70 @@ def run_ours(args, world, rank, local):
     d2h = args.pairs * (host[0]["diff"].numel() * 4 + n * 8)
     e2e_batch.close()
 
-    # ---- roofline of the dominant kernel (y-direction lag correlation, ALU bound), from the
-    # plain pass's per-stage events on the plan's stream
+    # ---- HBM roofline (the metric's HBM roofline %), per stage of the plain pass, from its
+    # per-stage CUDA events on the plan's stream.  Algorithmic bytes: the per-pixel figures of
+    # the two-pass FFT model of the hot path for the steps each stage performs (a1 + a2 row
+    # pass: read S, T, m and write the spectra, 61 B/px; a2 column pass: 104 B/px; a3 + a4
+    # cross-spectra and pruned inverse: 55 B/px; a7 convolve-subtract: 120 B/px), beside this
+    # design's own minimum traffic (each input read once, each output written once).
+    px = float(NY * NX)
     g_nseg = -(-NX // (256 - 2 * (L - 1)))
     nk, nb = (DK + 1) * (DK + 2) // 2, (DB + 1) * (DB + 2) // 2
-    nent = nk * (nk + 1) // 2 * (2 * L - 1) + nk * (nb + 1) * L
-    flops_per_launch = g_nseg * 129 * NY * nent * 8.0  # one complex multiply-add = 8 flops
-    ycorr_ms_per_launch = stages["ycorr"] / max(calls, 1)
-    achieved_tflops = flops_per_launch / (ycorr_ms_per_launch * 1e-3) / 1e12
+    nrec = (2 * (DK + 1) + (DB + 1) + 1 + 1) // 2 * 2
+    spec_bytes = g_nseg * NY * 129 * nrec * 8.0
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
     peaks = measured_peaks()
-    sm_max = peaks.get("sm_max_mhz", 2070.0)
-    fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12  # TFLOP/s: SMs x FP32 lanes x (mul+add) x clock
-    # DRAM bytes of one launch (dram__bytes_read.sum + dram__bytes_write.sum) from an ncu capture of
-    # this kernel, unchanged since, on a 2048^2 pair: 439 MB, scaled to the frame by its pixel count
-    # (the spectra it reads grow in proportion)
-    traffic = 439.0e6 * (NY * NX) / (2048.0 * 2048.0)
-    roofline = {"bound": "alu", "kernel": "k_ycorr_f32x2 (y-direction lag correlation)",
-                "achieved": round(achieved_tflops, 3), "peak": round(fp32_peak, 2), "unit": "TFLOP/s",
-                "frac": round(achieved_tflops / fp32_peak, 4), "traffic": round(traffic),
-                "traffic_note": "bytes per launch from an ncu capture at 2048^2, scaled by pixel count",
-                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x %.0f MHz (MEASURED_PEAKS sm_max_mhz)" % sm_max,
-                "flops_per_launch": flops_per_launch, "ms_per_launch": round(ycorr_ms_per_launch, 4)}
-    seg_bytes = NY * NX * 9.0 + g_nseg * NY * 129 * 20 * 8.0  # read S,T,mask; write 20 spectra
-    seg_ms = stages["segment_fft"] / max(calls, 1)
     hbm = peaks.get("hbm_gbs", 6785.5)
-    stage_ms = {k: round(v / max(calls, 1), 4) for k, v in stages.items()}
+    calls_ = max(calls, 1)
+    stage_ms = {k: round(v / calls_, 4) for k, v in stages.items()}
+
+    def hbm_stage(name, steps, survey_bpx, own_bytes):
+        t = stages[name] / calls_ * 1e-3
+        a = survey_bpx * px / t / 1e9
+        return {"steps": steps, "ms": round(t * 1e3, 4), "bytes": round(survey_bpx * px), "achieved": round(a, 1),
+                "frac": round(a / hbm, 4), "own_bytes": round(own_bytes),
+                "own_frac": round(own_bytes / t / 1e9 / hbm, 4)}
+
+    # CTAs per frequency of the y-FFT kernel (the library's choice: the fullest last wave of
+    # one CTA per SM, at least 8 (segment, block) units per CTA)
+    units = g_nseg * (-(-NY // (128 - 2 * (L - 1))))
+    best, y2split = -1.0, 1
+    for sp in range(1, 17):
+        if sp > 1 and units // sp < 8:
+            break
+        ctas = 129 * sp
+        eff = ctas / (-(-ctas // sms) * sms)
+        if eff > best + 1e-9:
+            best, y2split = eff, sp
+    hbm_stages = {
+        "segment_fft": hbm_stage("segment_fft", "a1 + a2 row pass", 61.0, 9.0 * px + spec_bytes),
+        "ycorr": hbm_stage("ycorr", "a2 column pass + a3 (+ a4 reads)", 104.0 + 55.0,
+                           spec_bytes + y2split * 129 * (nk * (nk + 1) // 2 + nk * (nb + 1)) * 128 * 16.0),
+        "subtract": hbm_stage("subtract", "a7 (direct route)", 120.0, 12.0 * px),
+    }
+    pair_ms = plain_ms / (args.steps * args.pairs)
+    whole = {"plain_ms_per_pair": round(pair_ms, 4), "batched_ms_per_pair": round(ms / (args.steps * args.pairs), 4),
+             "bytes": round(340.0 * px),
+             "plain_frac": round(340.0 * px / (pair_ms * 1e-3) / 1e9 / hbm, 4),
+             "batched_frac": round(340.0 * px / (ms / (args.steps * args.pairs) * 1e-3) / 1e9 / hbm, 4)}
+    # the dominant GPU-wide kernel: the y correlation (k_ycorr_fft32); DRAM bytes of one
+    # launch from an ncu capture of this kernel on a 2048^2 pair (190.8 MB read + 85.2 MB
+    # written), scaled to the frame by its pixel count (its traffic grows in proportion)
+    yc = hbm_stages["ycorr"]
+    traffic = (190.808e6 + 85.236e6) * px / (2048.0 * 2048.0)
+    ycorr_flops = 129 * g_nseg * (-(-NY // 108)) * ((2 * nk + nb + 1) * 2824.0 + (nk * (nk + 1) // 2 + nk * (nb + 1)) * 128 * 8.0)
+    fp32_peak = sms * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    roofline = {"bound": "hbm", "kernel": "k_ycorr_fft32 (y correlation: block FFTs + cross-spectra)",
+                "achieved": yc["achieved"], "peak": hbm, "unit": "GB/s", "frac": yc["frac"], "traffic": round(traffic),
+                "bytes_per_launch": yc["bytes"], "ms_per_launch": yc["ms"],
+                "peak_source": "MEASURED_PEAKS hbm_gbs (copy bandwidth)",
+                "traffic_note": "dram__bytes_read.sum + dram__bytes_write.sum of one launch at 2048^2, scaled by pixels",
+                "own_bytes_frac": yc["own_frac"],
+                "alu": {"flops_per_launch": ycorr_flops, "achieved_tflops": round(ycorr_flops / (yc["ms"] * 1e-3) / 1e12, 2),
+                        "peak_tflops": round(fp32_peak, 2),
+                        "frac": round(ycorr_flops / (yc["ms"] * 1e-3) / 1e12 / fp32_peak, 4),
+                        "peak_source": "derived: %d SMs x 128 FP32 lanes x 2 flop x %.0f MHz" % (sms, peaks.get("sm_max_mhz", 2070.0))}}
 
     result = {
         "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -353,7 +403,12 @@ def run_ours(args, world, rank, local):
         "batched_over_plain": round(value / plain_value, 3),
         "learned": {"train_samples": args.train_samples, "train_epochs": args.train_epochs,
                     "train_s": round(train_s, 1), "loss_first": losses[0], "loss_last": losses[-1],
+                    "warm_value": round(value, 3), "cold_value": round(cold_value, 3),
+                    "warm_over_cold": round(value / cold_value, 4),
                     "pcg_iterations": [i.iterations for i in binfos],
+                    "pcg_iterations_cold": [i.iterations for i in cinfos],
+                    "mean_iterations_warm": sum(i.iterations for i in binfos) / len(binfos),
+                    "mean_iterations_cold": sum(i.iterations for i in cinfos) / len(cinfos),
                     "start_residual": [round(i.start_residual, 4) for i in binfos],
                     "fallbacks": sum(i.fallback for i in binfos)},
         "batch": {"create_s": round(create_s, 2),
@@ -361,8 +416,8 @@ def run_ours(args, world, rank, local):
                              "ycorr_scalar": tuning.ycorr_scalar, "subtract_ctas": tuning.subtract_ctas,
                              "pcg_cluster": tuning.pcg_cluster}},
         "roofline": roofline,
-        "segment_fft_hbm": {"bound": "hbm", "achieved": round(seg_bytes / (seg_ms * 1e-3) / 1e9, 1),
-                            "peak": hbm, "unit": "GB/s", "frac": round(seg_bytes / (seg_ms * 1e-3) / 1e9 / hbm, 4)},
+        "hbm_stages": hbm_stages,
+        "hbm_whole_path": whole,
         "e2e": {"value": round(e2e_value, 3), "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": int(launches),
         "clocks": clk,

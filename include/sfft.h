@@ -171,6 +171,11 @@ typedef struct {
     int32_t ny, nx;           /* cutout size */
     int32_t pitch;            /* row pitch of the frames the cutouts lie in (elements; 0 = nx) */
     int32_t reserved;
+    /* device, nullable: the pair's 18 x 32 x 32 float PSF stamps (the warm-start network's
+     * input).  With a network given to sfft_batch_create, every run first evaluates it on
+     * the stamps of all pairs that have them and starts their PCG solves from its warm
+     * starts (replacing x0). */
+    const float *psf_stamps;
     /* Optional pinned host buffers (same pitch as the device ones).  With sci_host set, a run
      * first copies sci_host, tmpl_host and (if both are set) mask_host into sci, tmpl and mask,
      * and after the subtraction copies coeffs into coeffs_host and diff into diff_host (each
@@ -186,11 +191,17 @@ enum {
     SFFT_BATCH_GRAPH = 1,     /* capture the whole batch into one CUDA graph; runs replay it */
     SFFT_BATCH_AUTOTUNE = 2   /* autotune every geometry without a cached tuning first */
 };
+typedef struct sfft_cnn_s *sfft_cnn_t;
 /* Build a batch (plans, lanes, and with SFFT_BATCH_GRAPH the graph) and run it once,
  * ordered after the work already queued on `stream`, synchronising before it returns.
- * base supplies L, dk, db, dtype, precision, solver, refine; lanes <= 0 means 4. */
+ * base supplies L, dk, db, dtype, precision, solver, refine; lanes <= 0 means 4.
+ * cnn (nullable): the warm-start network (n_out = L^2 nP(dk)); every run then evaluates it
+ * on the psf_stamps of the pairs that carry them, on the creation stream before the pairs
+ * fork into the lanes (inside the graph with SFFT_BATCH_GRAPH), and those pairs' solves
+ * start from its warm starts.  The network must outlive the batch and may not be used on
+ * another stream while a run is in flight. */
 sfft_status sfft_batch_create(sfft_batch_t *batch, const sfft_desc *base, const sfft_pair *pairs,
-                              int32_t npairs, int32_t lanes, int32_t flags, sfft_stream_t stream);
+                              int32_t npairs, int32_t lanes, int32_t flags, sfft_cnn_t cnn, sfft_stream_t stream);
 /* Queue one run of every pair on the creation stream (one graph launch with
  * SFFT_BATCH_GRAPH). */
 sfft_status sfft_batch_run(sfft_batch_t batch);
@@ -199,10 +210,11 @@ sfft_status sfft_batch_run(sfft_batch_t batch);
 sfft_status sfft_batch_info(sfft_batch_t batch, sfft_fit_info *infos);
 void sfft_batch_destroy(sfft_batch_t batch);
 /* One-shot: all n_sci x n_tmpl pairs (science-major, pair (i, j) at i*n_tmpl + j), run once
- * and synchronised; infos (host, nullable) receives each pair's outcome, a non-positive-
- * definite pair is reported there rather than failing the call. */
+ * and synchronised; cnn (nullable) as for sfft_batch_create; infos (host, nullable)
+ * receives each pair's outcome, a non-positive-definite pair is reported there rather than
+ * failing the call. */
 sfft_status sfft_batch(const sfft_desc *base, int32_t n_sci, int32_t n_tmpl, const sfft_pair *pairs,
-                       sfft_fit_info *infos, sfft_stream_t stream);
+                       sfft_cnn_t cnn, sfft_fit_info *infos, sfft_stream_t stream);
 
 /* ---------------------------------------------------------------------------------
  * Launch tuning.  Plans take their y-correlation shape and subtract grid density from a
@@ -296,12 +308,13 @@ sfft_status sfft_cross_convolve(int32_t ny, int32_t nx, int32_t pitch, int32_t d
  * All pointers are device memory except where marked host; calls are queued on the
  * network's stream.  Stamps are [batch][18][32][32] float, targets and outputs
  * [batch][n_out] float.  A network is not thread-safe. */
-typedef struct sfft_cnn_s *sfft_cnn_t;
 /* Allocate a network (parameters, Adam moments, activations for up to max_batch samples),
  * zero-initialised; SFFT_ERR_OOM if the allocation fails. */
 sfft_status sfft_cnn_create(sfft_cnn_t *cnn, int32_t n_out, int32_t max_batch, sfft_stream_t stream);
 void sfft_cnn_destroy(sfft_cnn_t cnn);
 sfft_status sfft_cnn_param_count(sfft_cnn_t cnn, int64_t *count /* host */);
+/* Change the stream later calls are queued on. */
+sfft_status sfft_cnn_set_stream(sfft_cnn_t cnn, sfft_stream_t stream);
 /* Copy params (host or device, param_count floats) in; resets the Adam moments and step.
  * Synchronises the stream. */
 sfft_status sfft_cnn_set_params(sfft_cnn_t cnn, const float *params);

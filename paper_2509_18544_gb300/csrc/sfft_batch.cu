@@ -144,6 +144,11 @@ struct sfft_batch_s {
     std::vector<cudaEvent_t> ev_join;
     std::vector<cudaEvent_t> ev_in;  // per lane: its first pair's host inputs are on the device
     double *rec = nullptr;                         // per pair: [status, flag0 flag1, flag2, scal0, scal1, scal2, -, -]
+    sfft_cnn_t cnn = nullptr;                      // warm-start network (nullable)
+    std::vector<int> stamp_row;                    // per pair: its row of stamps_buf / x0_buf, -1: none
+    int nstamped = 0, n_unk = 0;
+    float *stamps_buf = nullptr;                   // [nstamped][18][32][32] gathered stamps
+    double *x0_buf = nullptr;                      // [nstamped][n_unk] the network's warm starts
     cudaGraph_t graph_h = nullptr;
     cudaGraphExec_t exec = nullptr;
     uint64_t launches_per_run = 0;
@@ -161,9 +166,33 @@ cudaError_t copy_frame(void *dst, const void *src, size_t pitch, size_t width, i
     return cudaMemcpy2DAsync(dst, pitch, src, pitch, width, ny, kind, s);
 }
 
-// queue the whole batch: fork from `origin` into the lanes, run each lane's pairs, join
+constexpr size_t kStampFloats = 18 * 32 * 32;
+
+// queue the whole batch: the warm starts of the stamped pairs (network on the origin
+// stream), fork from `origin` into the lanes, run each lane's pairs, join
 cudaError_t queue_batch(sfft_batch_t b, sfft_status *st) {
-    cudaError_t e = cudaEventRecord(b->ev_fork, b->origin);
+    cudaError_t e = cudaSuccess;
+    if (b->cnn && b->nstamped > 0) {
+        for (size_t i = 0; i < b->pairs.size() && e == cudaSuccess; i++)
+            if (b->stamp_row[i] >= 0)
+                e = cudaMemcpyAsync(b->stamps_buf + (size_t)b->stamp_row[i] * kStampFloats, b->pairs[i].psf_stamps,
+                                    kStampFloats * sizeof(float), cudaMemcpyDeviceToDevice, b->origin);
+        const cudaStream_t prev = cnn_stream(b->cnn);
+        sfft_cnn_set_stream(b->cnn, reinterpret_cast<sfft_stream_t>(b->origin));
+        const int mb = cnn_max_batch(b->cnn);
+        for (int r0 = 0; r0 < b->nstamped && e == cudaSuccess; r0 += mb) {
+            const int cnt = std::min(mb, b->nstamped - r0);
+            sfft_status s = sfft_cnn_warm_start(b->cnn, b->stamps_buf + (size_t)r0 * kStampFloats, cnt, b->n_unk,
+                                                b->x0_buf + (size_t)r0 * b->n_unk);
+            if (s != SFFT_OK) {
+                *st = s;
+                e = cudaErrorUnknown;
+            }
+        }
+        sfft_cnn_set_stream(b->cnn, reinterpret_cast<sfft_stream_t>(prev));
+        if (e != cudaSuccess) return e;
+    }
+    e = cudaEventRecord(b->ev_fork, b->origin);
     int prev_in = -1;  // last lane whose first pair copied host inputs
     for (int l = 0; l < b->lanes && e == cudaSuccess; l++) {
         e = cudaStreamWaitEvent(b->ls[l], b->ev_fork, 0);
@@ -194,7 +223,8 @@ cudaError_t queue_batch(sfft_batch_t b, sfft_status *st) {
                 if (e != cudaSuccess) break;
             }
             first = false;
-            sfft_status s = sfft_fit(p, q.sci, q.tmpl, q.mask, q.x0, q.coeffs, nullptr);
+            const double *x0 = b->stamp_row[pi] >= 0 ? b->x0_buf + (size_t)b->stamp_row[pi] * b->n_unk : q.x0;
+            sfft_status s = sfft_fit(p, q.sci, q.tmpl, q.mask, x0, q.coeffs, nullptr);
             if (s == SFFT_OK) s = sfft_subtract(p, q.sci, q.tmpl, q.coeffs, q.diff);
             if (s != SFFT_OK) {
                 *st = s;
@@ -236,6 +266,8 @@ void free_batch(sfft_batch_t b) {
     for (cudaEvent_t ev : b->ev_in)
         if (ev) cudaEventDestroy(ev);
     if (b->rec) cudaFree(b->rec);
+    if (b->stamps_buf) cudaFree(b->stamps_buf);
+    if (b->x0_buf) cudaFree(b->x0_buf);
     delete b;
 }
 
@@ -419,7 +451,7 @@ sfft_status sfft_autotune(const sfft_desc *desc, const void *sci, const void *tm
 }
 
 sfft_status sfft_batch_create(sfft_batch_t *out, const sfft_desc *base, const sfft_pair *pairs, int32_t npairs,
-                              int32_t lanes, int32_t flags, sfft_stream_t stream) {
+                              int32_t lanes, int32_t flags, sfft_cnn_t cnn, sfft_stream_t stream) {
     if (!out) return set_global_error("sfft_batch_create: null output"), SFFT_ERR_INVALID_ARG;
     *out = nullptr;
     if (!base || !pairs || npairs < 1) return set_global_error("sfft_batch_create: empty batch"), SFFT_ERR_INVALID_ARG;
@@ -432,9 +464,25 @@ sfft_status sfft_batch_create(sfft_batch_t *out, const sfft_desc *base, const sf
             return SFFT_ERR_INVALID_ARG;
         }
     }
+    Geometry g0;
+    char gerr[256];
+    if (!make_geometry(*base, g0, gerr, sizeof gerr)) {
+        errf("sfft_batch_create: %s", gerr);
+        return SFFT_ERR_INVALID_ARG;
+    }
+    if (cnn && cnn_n_out(cnn) != g0.nker) {
+        errf("sfft_batch_create: the network has %d outputs, the basis %d kernel coefficients", cnn_n_out(cnn), g0.nker);
+        return SFFT_ERR_INVALID_ARG;
+    }
     sfft_batch_t b = new sfft_batch_s;
     b->base = *base;
     b->pairs.assign(pairs, pairs + npairs);
+    b->cnn = cnn;
+    b->n_unk = g0.n;
+    b->stamp_row.assign(npairs, -1);
+    if (cnn)
+        for (int i = 0; i < npairs; i++)
+            if (pairs[i].psf_stamps) b->stamp_row[i] = b->nstamped++;
     b->lanes = std::max(1, std::min(lanes > 0 ? lanes : 4, npairs));
     b->graph = (flags & SFFT_BATCH_GRAPH) != 0;
     b->user = reinterpret_cast<cudaStream_t>(stream);
@@ -456,6 +504,8 @@ sfft_status sfft_batch_create(sfft_batch_t *out, const sfft_desc *base, const sf
     }
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaMalloc(&b->rec, sizeof(double) * kRec * npairs);
+    if (e == cudaSuccess && b->nstamped > 0) e = cudaMalloc(&b->stamps_buf, sizeof(float) * kStampFloats * b->nstamped);
+    if (e == cudaSuccess && b->nstamped > 0) e = cudaMalloc(&b->x0_buf, sizeof(double) * b->n_unk * b->nstamped);
     if (e == cudaSuccess) e = cudaMemset(b->rec, 0, sizeof(double) * kRec * npairs);
     if (e != cudaSuccess) {
         errf("sfft_batch_create: %s", cudaGetErrorString(e));
@@ -598,11 +648,11 @@ sfft_status sfft_batch_info(sfft_batch_t b, sfft_fit_info *infos) {
 
 void sfft_batch_destroy(sfft_batch_t b) { free_batch(b); }
 
-sfft_status sfft_batch(const sfft_desc *base, int32_t n_sci, int32_t n_tmpl, const sfft_pair *pairs,
+sfft_status sfft_batch(const sfft_desc *base, int32_t n_sci, int32_t n_tmpl, const sfft_pair *pairs, sfft_cnn_t cnn,
                        sfft_fit_info *infos, sfft_stream_t stream) {
     if (!base || n_sci < 1 || n_tmpl < 1 || !pairs) return set_global_error("sfft_batch: empty batch"), SFFT_ERR_INVALID_ARG;
     sfft_batch_t b = nullptr;
-    sfft_status s = sfft_batch_create(&b, base, pairs, n_sci * n_tmpl, 0, 0, stream);
+    sfft_status s = sfft_batch_create(&b, base, pairs, n_sci * n_tmpl, 0, 0, cnn, stream);
     if (s != SFFT_OK) return s;
     // the creation pass already ran every pair once; its records are current
     if (infos) {

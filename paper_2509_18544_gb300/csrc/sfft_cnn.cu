@@ -579,6 +579,18 @@ sfft_status sfft_cnn_warm_start(sfft_cnn_t c, const float *stamps, int32_t batch
     return SFFT_OK;
 }
 
+sfft_status sfft_cnn_set_stream(sfft_cnn_t c, sfft_stream_t stream) {
+    if (!c) return cnn_err(c, SFFT_ERR_INVALID_ARG, "null network");
+    c->stream = reinterpret_cast<cudaStream_t>(stream);
+    return SFFT_OK;
+}
+
 const char *sfft_cnn_last_error(sfft_cnn_t c) { return c ? c->err : sfft_last_error(nullptr); }
 
 }  // extern "C"
+
+namespace sfft {
+int cnn_n_out(sfft_cnn_t c) { return c ? c->n_out : -1; }
+int cnn_max_batch(sfft_cnn_t c) { return c ? c->max_batch : 0; }
+cudaStream_t cnn_stream(sfft_cnn_t c) { return c ? c->stream : nullptr; }
+}  // namespace sfft

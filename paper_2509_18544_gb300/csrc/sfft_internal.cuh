@@ -118,6 +118,11 @@ struct Workspace {
 
 size_t workspace_bytes(const Geometry &g, int precision, int dtype);
 
+// the warm-start network's output width, batch capacity and current stream
+int cnn_n_out(sfft_cnn_t c);
+int cnn_max_batch(sfft_cnn_t c);
+cudaStream_t cnn_stream(sfft_cnn_t c);
+
 // process-wide count of kernel launches (every launcher calls this before each launch)
 void note_launch(int count = 1);
 uint64_t launch_count();

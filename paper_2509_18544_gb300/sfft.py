@@ -28,7 +28,8 @@ EXPORTED = ("sfft_plan", "sfft_destroy", "sfft_n_unknowns", "sfft_workspace_size
             "sfft_status_string", "sfft_last_error",
             "sfft_cnn_create", "sfft_cnn_destroy", "sfft_cnn_param_count", "sfft_cnn_set_params",
             "sfft_cnn_get_params", "sfft_cnn_forward", "sfft_cnn_gradients", "sfft_cnn_train_step",
-            "sfft_cnn_train", "sfft_cnn_warm_start", "sfft_cnn_save", "sfft_cnn_load", "sfft_cnn_last_error")
+            "sfft_cnn_train", "sfft_cnn_warm_start", "sfft_cnn_save", "sfft_cnn_load", "sfft_cnn_last_error",
+            "sfft_cnn_set_stream")
 NSTAGES = 8
 STAGES = ("segment_fft", "moments", "ycorr", "lag_tables", "assemble", "solve", "subtract", "refine")
 
@@ -59,7 +60,7 @@ class sfft_pair(ctypes.Structure):
     _fields_ = [("sci", ctypes.c_void_p), ("tmpl", ctypes.c_void_p), ("mask", ctypes.c_void_p),
                 ("x0", ctypes.c_void_p), ("coeffs", ctypes.c_void_p), ("diff", ctypes.c_void_p),
                 ("ny", ctypes.c_int32), ("nx", ctypes.c_int32), ("pitch", ctypes.c_int32),
-                ("reserved", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("psf_stamps", ctypes.c_void_p),
                 ("sci_host", ctypes.c_void_p), ("tmpl_host", ctypes.c_void_p), ("mask_host", ctypes.c_void_p),
                 ("coeffs_host", ctypes.c_void_p), ("diff_host", ctypes.c_void_p)]
 
@@ -97,10 +98,10 @@ def load_library(path: str = LIB_PATH):
         lib.sfft_fit.argtypes = [P, P, P, P, P, P, ctypes.POINTER(sfft_fit_info)]
         lib.sfft_subtract.argtypes = [P, P, P, P, P]
         lib.sfft_sync_status.argtypes = [P]
-        lib.sfft_batch.argtypes = [ctypes.POINTER(sfft_desc), I32, I32, ctypes.POINTER(sfft_pair),
+        lib.sfft_batch.argtypes = [ctypes.POINTER(sfft_desc), I32, I32, ctypes.POINTER(sfft_pair), P,
                                    ctypes.POINTER(sfft_fit_info), P]
         lib.sfft_batch_create.argtypes = [ctypes.POINTER(P), ctypes.POINTER(sfft_desc), ctypes.POINTER(sfft_pair),
-                                          I32, I32, I32, P]
+                                          I32, I32, I32, P, P]
         lib.sfft_batch_run.argtypes = [P]
         lib.sfft_batch_info.argtypes = [P, ctypes.POINTER(sfft_fit_info)]
         lib.sfft_batch_destroy.argtypes = [P]
@@ -133,6 +134,7 @@ def load_library(path: str = LIB_PATH):
                                        ctypes.POINTER(ctypes.c_float)]
         lib.sfft_cnn_warm_start.argtypes = [P, P, I32, I32, P]
         lib.sfft_cnn_save.argtypes = [P, ctypes.c_char_p]
+        lib.sfft_cnn_set_stream.argtypes = [P, P]
         lib.sfft_cnn_load.argtypes = [P, ctypes.c_char_p]
         lib.sfft_cnn_last_error.argtypes = [P]
         lib.sfft_cnn_last_error.restype = ctypes.c_char_p
@@ -257,11 +259,13 @@ def sfft_sync_status(plan: Plan):
     _check(load_library().sfft_sync_status(plan.handle), plan.handle)
 
 
-def make_pair(sci, tmpl, mask, coeffs, diff, ny, nx, pitch=0, x0=None, host=None) -> sfft_pair:
+def make_pair(sci, tmpl, mask, coeffs, diff, ny, nx, pitch=0, x0=None, host=None, stamps=None) -> sfft_pair:
     """host: optional dict of pinned host tensors (sci, tmpl, mask, coeffs, diff) that a run
-    copies in before the fit and out after the subtraction."""
+    copies in before the fit and out after the subtraction; stamps: the pair's 18 x 32 x 32
+    float PSF stamps on the device (read when the batch has a warm-start network)."""
     q = sfft_pair()
     q.sci, q.tmpl, q.mask, q.x0 = _ptr(sci), _ptr(tmpl), _ptr(mask), _ptr(x0)
+    q.psf_stamps = _ptr(stamps)
     q.coeffs, q.diff = _ptr(coeffs), _ptr(diff)
     q.ny, q.nx, q.pitch = ny, nx, pitch
     if host:
@@ -274,10 +278,11 @@ def _pairs(pairs):
     return (sfft_pair * len(pairs))(*pairs)
 
 
-def sfft_batch(desc: sfft_desc, n_sci: int, n_tmpl: int, pairs, want_info=True, stream=None):
+def sfft_batch(desc: sfft_desc, n_sci: int, n_tmpl: int, pairs, want_info=True, stream=None, cnn=None):
     """One-shot run of all S x T pairs (science-major list of sfft_pair); returns the infos."""
     infos = (sfft_fit_info * len(pairs))() if want_info else None
-    _check(load_library().sfft_batch(ctypes.byref(desc), n_sci, n_tmpl, _pairs(pairs), infos, _stream(stream)))
+    _check(load_library().sfft_batch(ctypes.byref(desc), n_sci, n_tmpl, _pairs(pairs),
+                                     cnn.handle if cnn is not None else None, infos, _stream(stream)))
     return list(infos) if infos is not None else None
 
 
@@ -305,10 +310,11 @@ class Batch:
         self.close()
 
 
-def sfft_batch_create(desc: sfft_desc, pairs, lanes: int = 0, flags: int = 0, stream=None) -> Batch:
+def sfft_batch_create(desc: sfft_desc, pairs, lanes: int = 0, flags: int = 0, stream=None, cnn=None) -> Batch:
+    """cnn: a warm-start network (Cnn) evaluated on the pairs' stamps at every run."""
     h = ctypes.c_void_p()
     _check(load_library().sfft_batch_create(ctypes.byref(h), ctypes.byref(desc), _pairs(pairs), len(pairs), lanes,
-                                            flags, _stream(stream)))
+                                            flags, cnn.handle if cnn is not None else None, _stream(stream)))
     return Batch(h.value, len(pairs))
 
 

@@ -200,3 +200,44 @@ def test_batch_with_contiguous_host_frames():
         assert info.status == 0
         assert torch.equal(host["coeffs"], th.cpu())
         assert torch.equal(host["diff"], D.cpu())
+
+
+def test_batch_runs_the_warm_start_network_inside_the_graph():
+    """Pairs that carry PSF stamps, with a warm-start network given to the batch: every run
+    evaluates the network on the stamps (inside the graph) and starts those pairs' PCG solves
+    from its warm starts.  The coefficients equal, bit for bit, a batch whose warm starts
+    were computed beforehand by sfft_cnn_warm_start and passed as x0; a pair without stamps
+    starts cold as before."""
+    cuts = _cutouts(SIZES[:4], seed=300)
+    n = oracle.n_unknowns(L, DK, DB)
+    nker = L * L * (DK + 1) * (DK + 2) // 2
+    cnn = sfft.sfft_cnn_create(nker, 8)
+    sfft.sfft_cnn_set_params(cnn, torch.from_numpy(synth.cnn_init(nker, 3) * 0.05).to(DEV))
+    stamps = torch.from_numpy(np.stack([synth.psf_stamps(synth.psf_field(40 + k)) for k in range(3)])).to(DEV)
+    x0 = torch.zeros((3, n), dtype=torch.float64, device=DEV)
+    sfft.sfft_cnn_warm_start(cnn, stamps, 3, n, x0)
+    desc = sfft.make_desc(128, 128, L, DK, DB, solver=sfft.SOLVE_PCG)
+    # reference: x0 given explicitly (the fourth pair cold)
+    pairs_ref, th_ref, _ = _pairs(cuts, n, x0=[x0[0], x0[1], x0[2], None])
+    with sfft.sfft_batch_create(desc, pairs_ref, lanes=2, flags=sfft.BATCH_GRAPH) as b:
+        sfft.sfft_batch_run(b)
+        i_ref = sfft.sfft_batch_info(b)
+    # the network inside the batch, fed each pair's stamps
+    pairs, th, _ = _pairs(cuts, n)
+    for k in range(3):
+        pairs[k].psf_stamps = stamps[k].data_ptr()
+    with sfft.sfft_batch_create(desc, pairs, lanes=2, flags=sfft.BATCH_GRAPH, cnn=cnn) as b:
+        for t in th:
+            t.fill_(float("nan"))
+        sfft.sfft_batch_run(b)
+        infos = sfft.sfft_batch_info(b)
+    for a, r in zip(th, th_ref):
+        assert torch.equal(a, r)
+    assert [i.iterations for i in infos] == [i.iterations for i in i_ref]
+    assert [i.start_residual for i in infos] == [i.start_residual for i in i_ref]
+    # a network whose width does not match the basis is rejected
+    with sfft.sfft_cnn_create(nker + 1, 4) as bad:
+        with pytest.raises(sfft.SfftError) as ei:
+            sfft.sfft_batch_create(desc, pairs, lanes=2, cnn=bad)
+        assert ei.value.status == sfft.ERR_INVALID_ARG
+    cnn.close()
