@@ -294,6 +294,104 @@ sfft_status sfft_cross_convolve(int32_t ny, int32_t nx, int32_t pitch, int32_t d
                                 void *tmpl_out, sfft_stream_t stream);
 
 /* ---------------------------------------------------------------------------------
+ * Alignment and resampling (Sec. "Pipeline steps", step 4: the template image, its
+ * detection mask and its PSF are aligned to the science frame on the GPU; Sec. "GPU
+ * acceleration and performance" names alignment and resampling as where much of the
+ * porting effort went).  The paper fixes neither a coordinate model nor an interpolation
+ * kernel; the library's definitions:
+ *   coordinates   science pixel (x, y) (column, row) reads template position (u, v),
+ *                 u = sum_j cu[j] (x - x_ref)^p_j (y - y_ref)^q_j, v likewise with cv, over
+ *                 the first (degree + 1)(degree + 2)/2 monomials of (0,0), (1,0), (0,1),
+ *                 (2,0), (1,1), (0,2), (3,0), (2,1), (1,2), (0,3) (p = x power), degree 1..3:
+ *                 the affine part of two WCS solutions plus a low-order distortion between
+ *                 them, fitted by the caller;
+ *   interpolation Lanczos-3 (taps floor(u) - 2 .. floor(u) + 3, window sinc(t) sinc(t/3),
+ *                 exactly 1 at t = 0 and 0 at the other integers) or bilinear, separable,
+ *                 normalised by the sum of all tap weights;
+ *   bad taps      a tap with non-zero weight that falls outside the template or on a masked
+ *                 pixel (mask byte != 0) adds no value and its pixel is not read; out_mask = 1
+ *                 where more than 1 % of the taps' |weight| is bad.  With
+ *                 SFFT_RESAMPLE_ZERO_OUTSIDE outside taps are zeros and are not bad (stamps);
+ *   flux          SFFT_RESAMPLE_FLUX multiplies by |det d(u,v)/d(x,y)| (values are fluxes
+ *                 per pixel and the pixel area changes).
+ * Coordinates are evaluated in FP64 at the corner of each 16 x 16 output tile and by an FP32
+ * Taylor expansion inside it (error a few 1e-6 pixel); weights and sums are FP32. */
+typedef struct {
+    int32_t degree;            /* 1 .. 3 */
+    int32_t reserved;          /* 0 */
+    double x_ref, y_ref;       /* origin of the polynomials, science pixels */
+    double cu[10], cv[10];     /* coefficients in the monomial order above; the tail past the
+                                  degree's count is ignored */
+} sfft_warp;
+enum { SFFT_LANCZOS3 = 0, SFFT_BILINEAR = 1 };
+enum { SFFT_RESAMPLE_FLUX = 1, SFFT_RESAMPLE_ZERO_OUTSIDE = 2 };
+/* Resample `in` (in_ny x in_nx, row pitch in_pitch elements, 0 = in_nx; dtype SFFT_F32 or
+ * SFFT_F64; device) onto the out_ny x out_nx science grid `out` (same dtype, pitch out_pitch,
+ * 0 = out_nx; device).  in_mask / out_mask: device bytes with the image's pitch, each
+ * nullable.  warp: host struct, copied.  Queued on `stream`; no allocation.
+ * SFFT_ERR_INVALID_ARG on a bad size, degree, method, flag or an output aliasing an input. */
+sfft_status sfft_resample(const sfft_warp *warp, int32_t method, int32_t flags, int32_t in_ny, int32_t in_nx,
+                          int32_t in_pitch, int32_t dtype, const void *in, const uint8_t *in_mask, int32_t out_ny,
+                          int32_t out_nx, int32_t out_pitch, void *out, uint8_t *out_mask, sfft_stream_t stream);
+/* The template PSF aligned to the science grid at science position (x, y): with J the warp's
+ * Jacobian at (x, y) (host, FP64), output stamp offset d reads template stamp offset J d;
+ * Lanczos-3, zeros outside the stamp, flux-conserving (|det J|).  psf_in, psf_out: device
+ * K x K float32 stamps centred on the middle element, K odd, 1 <= K <= 63, not aliased. */
+sfft_status sfft_align_psf(const sfft_warp *warp, double x, double y, int32_t K, const float *psf_in,
+                           float *psf_out, sfft_stream_t stream);
+
+/* ---------------------------------------------------------------------------------
+ * Decorrelation kernel (Sec. "Pipeline steps", step 7: fitted, then applied to the
+ * difference image, the science PSF and the cross-convolved science image).  The paper
+ * cites the kernel without a formula; the library's definition: the fit matches
+ * S' = S (x) P_T against T' = T (x) P_S, so white pixel noise sigma_S, sigma_T leaves
+ * D = S' - K (x) T' with the noise spectrum
+ *     den(k) = sigma_S^2 |P_T(k)|^2 + sigma_T^2 |K(k)|^2 |P_S(k)|^2,
+ * and the kernel whitens it at unit gain for a point source's flux:
+ *     Phi(k) = sqrt(num / max(den(k), 1e-8 num)),   num = sigma_S^2 + K(0)^2 sigma_T^2,
+ * on the M x M cyclic grid (every stamp centred on it, offset d at index d mod M);
+ * phi = IDFT(Phi) and the decorrelated science PSF IDFT(P_S P_T Phi) are written as centred
+ * M x M float32 stamps.  K(d) is the fitted matching kernel at science pixel (x, y):
+ * K(d) = sum_pq a_{pq,d} xh^p yh^q from the first L^2 nP(dk) entries of `coeffs` (the fit's
+ * theta, device FP64; xh, yh normalised on the ny x nx frame).  psf_sci, psf_tmpl: device
+ * K x K float32 stamps (the cross-convolution's); M odd with max(K, L) <= M <= 31 so that
+ * sfft_cross_convolve can apply phi (to D and to the cross-convolved science image, one call);
+ * sigma_sci > 0, sigma_tmpl >= 0.  DFTs and Phi in FP64.  psf_out nullable.  One CTA,
+ * queued on `stream`; no allocation. */
+sfft_status sfft_decorrelation_kernel(int32_t ny, int32_t nx, int32_t L, int32_t dk, const double *coeffs,
+                                      double x, double y, int32_t K, const float *psf_sci,
+                                      const float *psf_tmpl, double sigma_sci, double sigma_tmpl, int32_t M,
+                                      float *phi, float *psf_out, sfft_stream_t stream);
+
+/* ---------------------------------------------------------------------------------
+ * Forced PSF photometry (Sec. "Pipeline steps", step 9: the PSF fitted to the decorrelated
+ * difference image at the transient's coordinates; step 8 fits the same PSF to field stars).
+ * One job = one image and one position; a launch takes any number of jobs (all pairs of a
+ * batch, or many stars of one image).  Definition: the source at (x, y) sits on pixel
+ * (X, Y) = (floor(x + 0.5), floor(y + 0.5)) with offset (fx, fy) = (x - X, y - Y); the model
+ * P(a, b) is the K x K stamp moved by (fx, fy) (Lanczos-3 as in sfft_resample, zeros outside
+ * the stamp), placed on the footprint (Y + a, X + b), |a|, |b| <= (K - 1)/2.  Footprint
+ * pixels inside the frame, unmasked and with weight > 0 enter
+ *     minimise sum w (D - f P - b)^2    (b = 0 unless SFFT_PHOT_BACKGROUND),
+ * solved from the 1 x 1 or 2 x 2 normal equations in FP64. */
+typedef struct {
+    const void *image;     /* device ny x pitch, dtype */
+    const float *weight;   /* device inverse variances with the image's pitch; NULL = all 1 */
+    const uint8_t *mask;   /* device bytes with the image's pitch, non-zero = excluded; nullable */
+    const float *psf;      /* device K x K float32 stamp centred on its middle element */
+    double x, y;           /* source position, pixels (column, row) */
+    int32_t ny, nx, pitch, dtype;  /* pitch in elements (0 = nx); SFFT_F32 or SFFT_F64 */
+} sfft_phot_job;
+enum { SFFT_PHOT_BACKGROUND = 1 };
+/* jobs: device array of njobs entries (caller-owned, read by the kernel).  results: device,
+ * 8 doubles per job: flux, formal flux error sqrt([(A^T W A)^-1]_ff), background (0 without
+ * the flag), chi2 = sum w r^2, pixels used, status (0 = solved, 1 = no usable pixel or a
+ * singular system: the other fields 0), 0, 0.  K odd, 1 <= K <= 63.  Queued on `stream`;
+ * no allocation; per-job problems are reported in `status`, not as a call error. */
+sfft_status sfft_forced_photometry(int32_t njobs, const sfft_phot_job *jobs, int32_t K, int32_t flags,
+                                   double *results, sfft_stream_t stream);
+
+/* ---------------------------------------------------------------------------------
  * Warm-start network (the learned warm start of the PCG solve).  A small CNN maps the
  * point-spread functions of a pair -- 32 x 32 stamps of unit mean at the centres of a
  * 3 x 3 grid over the frame, 18 channels ordered (cell row-major, then science, template)

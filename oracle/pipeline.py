@@ -12,7 +12,7 @@ TEST INFRASTRUCTURE ONLY: the tests, ``__graft_entry__.smoke()`` and the CPU leg
 The paper names these steps but fixes neither an interpolation kernel, a coordinate model,
 a decorrelation formula nor a photometry estimator.  The definitions below are the readings
 this oracle and the CUDA path share (each stated in its function), written plainly in
-numpy FP64 with explicit loops over taps and footprints.  Parity pins: tests/test_oracle_pins.py.
+numpy FP64 with explicit loops over taps and footprints.  Pins: tests/test_pipeline_oracle_pins.py.
 """
 from __future__ import annotations
 
@@ -136,6 +136,19 @@ def resample(img, warp, out_shape, mask=None, method=LANCZOS3, flux=False, zero_
     return out, (frac > MASK_FRACTION).astype(np.uint8), frac
 
 
+def resample_pixels(img, warp, ys, xs, mask=None, method=LANCZOS3, flux=False, zero_outside=False):
+    """resample() at the listed output pixels only (any frame size): (values, bad fractions)."""
+    vals, fracs = [], []
+    for y, x in zip(ys, xs):
+        u, v = warp_eval(warp, float(x), float(y))
+        val, fr = _interp_one(img, mask, u, v, method, zero_outside)
+        if flux:
+            val *= abs(np.linalg.det(warp_jacobian(warp, float(x), float(y))))
+        vals.append(val)
+        fracs.append(fr)
+    return np.array(vals), np.array(fracs)
+
+
 def psf_warp(warp, x, y, K):
     """The affine map that aligns a K x K template PSF stamp (centre c = (K - 1) / 2) to the
     science frame at science position (x, y): stamp offset d maps to J(x, y) d, i.e.
@@ -149,8 +162,8 @@ def psf_warp(warp, x, y, K):
 
 
 def align_psf(psf, warp, x, y, method=LANCZOS3):
-    """Template PSF stamp resampled onto the science pixel grid at (x, y) (step 4: "align
-    the reference PSF"): zeros outside the stamp, flux-conserving (|det J|)."""
+    """Template PSF stamp resampled onto the science pixel grid at (x, y) (step 4 aligns the
+    template's PSF with its image): zeros outside the stamp, flux-conserving (|det J|)."""
     K = psf.shape[0]
     out, _, _ = resample(psf, psf_warp(warp, x, y, K), (K, K), None, method, flux=True, zero_outside=True)
     return out

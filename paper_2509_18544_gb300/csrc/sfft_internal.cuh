@@ -38,6 +38,36 @@ __host__ __device__ __forceinline__ void mono_pq(int idx, int &p, int &q) {
     p = d - idx;
 }
 
+// ------------------------------------------------------------------ Lanczos-3 window
+// Weights of the six taps floor - 2 .. floor + 3 at fractional position f in [0, 1):
+// w[j] = L(f - m), m = j - 2, L(t) = sinc(t) sinc(t / 3) = 3 sin(pi t) sin(pi t / 3) / (pi t)^2.
+// sin(pi (f - m)) = (-1)^m sin(pi f) serves every tap; sin(pi (f - m) / 3) comes from the
+// angle-difference identity on sin/cos(pi f / 3), except for m = 1, where that difference
+// cancels as f -> 1, which takes its own sinpi of the (exact) t = f - 1.  f == 0 gives
+// exactly (0, 0, 1, 0, 0, 0).  FP32.
+__device__ __forceinline__ void lanczos3_taps(float f, float w[6]) {
+    if (f == 0.f) {
+#pragma unroll
+        for (int j = 0; j < 6; j++) w[j] = j == 2 ? 1.f : 0.f;
+        return;
+    }
+    const float s1 = sinpif(f);
+    float s3, c3;
+    sincospif(f * (1.f / 3.f), &s3, &c3);
+    const float h3 = 0.86602540378443864676f;  // sin(pi / 3)
+    // sin(pi (f - m) / 3) for m = -2 .. 3
+    const float sm[6] = {-0.5f * s3 + h3 * c3, 0.5f * s3 + h3 * c3, s3, sinpif((f - 1.f) * (1.f / 3.f)),
+                         -0.5f * s3 - h3 * c3, -s3};
+    const float k = 0.30396355092701331433f;  // 3 / pi^2
+#pragma unroll
+    for (int j = 0; j < 6; j++) {
+        const int m = j - 2;
+        const float t = f - (float)m;
+        const float sg = (m & 1) ? -s1 : s1;
+        w[j] = sg * sm[j] * k / (t * t);
+    }
+}
+
 // ------------------------------------------------------------------ geometry of a plan
 // The lag correlations are computed per row segment: segment s owns the columns
 // [s*U, s*U + U) of every row ("A" side, zero-padded to P) and reads the cyclic window

@@ -1,0 +1,309 @@
+// Alignment and resampling (Sec. "Pipeline steps", step 4; Sec. "GPU acceleration and
+// performance"): the template image and its detection mask resampled onto the science
+// grid, and the template PSF aligned to it.
+//
+// Coordinate model, window, bad-tap rule and flux scaling are the ones sfft.h states for
+// sfft_resample.  Kernel design: one CTA per 16 x 16 output tile, one pixel per thread.
+// Twenty threads first re-expand the coordinate polynomials about the tile corner in FP64
+// (d_{p'q'} = sum_{p >= p', q >= q'} c_pq C(p, p') C(q, q') ax^(p - p') ay^(q - q'),
+// (ax, ay) the corner's offset from the origin), keeping the corner value in FP64 and the
+// other terms in FP32; each pixel then adds its FP32 Taylor part (|i|, |j| < 16) to the
+// fractional part of the corner value, so the integer tap position is exact and the
+// fraction carries an error of a few 1e-6 pixel.  Taps read the template through the
+// read-only path; a tile whose taps all land inside an unmasked template skips the
+// per-tap tests.  FP32 weights and sums (FP64 images are converted on load).
+#include <math.h>
+#include <stdio.h>
+
+#include "sfft_internal.cuh"
+
+namespace sfft {
+
+void set_global_error(const char *msg);
+
+namespace {
+
+constexpr int kTile = 16, kThreads = kTile * kTile;
+
+struct WarpArg {
+    int n;  // monomials in use
+    double xr, yr;
+    double cu[10], cv[10];
+};
+
+__device__ __forceinline__ double ipow(double a, int e) {
+    double r = 1.0;
+    for (int i = 0; i < e; i++) r *= a;
+    return r;
+}
+
+__device__ __forceinline__ double binom3(int n, int k) {  // n <= 3
+    const int t[4][4] = {{1, 0, 0, 0}, {1, 1, 0, 0}, {1, 2, 1, 0}, {1, 3, 3, 1}};
+    return t[n][k];
+}
+
+template <int METHOD>
+struct Taps;
+template <>
+struct Taps<SFFT_LANCZOS3> {
+    static constexpr int n = 6, first = -2;
+    __device__ __forceinline__ static void weights(float f, float *w) { lanczos3_taps(f, w); }
+};
+template <>
+struct Taps<SFFT_BILINEAR> {
+    static constexpr int n = 2, first = 0;
+    __device__ __forceinline__ static void weights(float f, float *w) {
+        w[0] = 1.f - f;
+        w[1] = f;
+    }
+};
+
+template <class In, int METHOD>
+__global__ void __launch_bounds__(kThreads) k_resample(WarpArg wa, int flags, const In *__restrict__ in,
+                                                       const uint8_t *__restrict__ in_mask, int in_ny, int in_nx,
+                                                       int in_pitch, In *__restrict__ out,
+                                                       uint8_t *__restrict__ out_mask, int out_ny, int out_nx,
+                                                       int out_pitch) {
+    using T = Taps<METHOD>;
+    __shared__ double s_c0[2];
+    __shared__ float s_d[2][10];
+    const int x0 = blockIdx.x * kTile, y0 = blockIdx.y * kTile, t = threadIdx.x;
+    if (t < 2 * wa.n) {
+        const int k = t % wa.n;
+        const double *c = t < wa.n ? wa.cu : wa.cv;
+        int pk, qk;
+        mono_pq(k, pk, qk);
+        const double ax = (double)x0 - wa.xr, ay = (double)y0 - wa.yr;
+        double s = 0.0;
+        for (int j = 0; j < wa.n; j++) {
+            int p, q;
+            mono_pq(j, p, q);
+            if (p < pk || q < qk) continue;
+            s += c[j] * binom3(p, pk) * binom3(q, qk) * ipow(ax, p - pk) * ipow(ay, q - qk);
+        }
+        if (k == 0)
+            s_c0[t < wa.n ? 0 : 1] = s;
+        else
+            s_d[t < wa.n ? 0 : 1][k] = (float)s;
+    }
+    __syncthreads();
+    const int i = t % kTile, j = t / kTile;
+    const int x = x0 + i, y = y0 + j;
+    const bool live = x < out_nx && y < out_ny;
+    // Taylor part about the tile corner
+    float mono[10];
+    mono[0] = 1.f;
+    const float fi = (float)i, fj = (float)j;
+    float du = 0.f, dv = 0.f;
+#pragma unroll
+    for (int k = 1; k < 10; k++) {
+        int p, q;
+        mono_pq(k, p, q);
+        mono[k] = (p == 0 ? 1.f : p == 1 ? fi : p == 2 ? fi * fi : fi * fi * fi) *
+                  (q == 0 ? 1.f : q == 1 ? fj : q == 2 ? fj * fj : fj * fj * fj);
+        if (k < wa.n) {
+            du = fmaf(s_d[0][k], mono[k], du);
+            dv = fmaf(s_d[1][k], mono[k], dv);
+        }
+    }
+    const double U0 = s_c0[0], V0 = s_c0[1];
+    // far outside (or not finite): every tap is outside
+    const bool far = !(fabs(U0) < 1.0e9 && fabs(V0) < 1.0e9);
+    const double iu0 = far ? 0.0 : floor(U0), iv0 = far ? 0.0 : floor(V0);
+    const float tu = far ? 0.f : (float)(U0 - iu0) + du, tv = far ? 0.f : (float)(V0 - iv0) + dv;
+    const float flu = floorf(tu), flv = floorf(tv);
+    const float fu = tu - flu, fv = tv - flv;
+    long long iu = (long long)iu0 + (long long)flu + T::first;  // first tap column
+    long long iv = (long long)iv0 + (long long)flv + T::first;
+    const bool zero_outside = flags & SFFT_RESAMPLE_ZERO_OUTSIDE;
+    float wx[T::n], wy[T::n];
+    T::weights(fu, wx);
+    T::weights(fv, wy);
+    float sx = 0.f, sy = 0.f, ax = 0.f, ay = 0.f;
+#pragma unroll
+    for (int k = 0; k < T::n; k++) {
+        sx += wx[k];
+        sy += wy[k];
+        ax += fabsf(wx[k]);
+        ay += fabsf(wy[k]);
+    }
+    // interior tiles without a mask: taps need no test
+    const bool inside = !far && iu >= 0 && iu + T::n <= in_nx && iv >= 0 && iv + T::n <= in_ny;
+    const bool fast = __syncthreads_and(!live || (inside && in_mask == nullptr));
+    if (!live) return;
+    float acc = 0.f, bad = 0.f;
+    if (fast) {
+        const In *row = in + (size_t)iv * in_pitch + iu;
+#pragma unroll
+        for (int a = 0; a < T::n; a++) {
+            float r = 0.f;
+#pragma unroll
+            for (int b = 0; b < T::n; b++) r = fmaf(wx[b], (float)__ldg(row + b), r);
+            acc = fmaf(wy[a], r, acc);
+            row += in_pitch;
+        }
+    } else if (far) {
+        bad = zero_outside ? 0.f : ax * ay;
+    } else {
+        for (int a = 0; a < T::n; a++) {
+            if (wy[a] == 0.f) continue;
+            const long long r = iv + a;
+            const bool rin = r >= 0 && r < in_ny;
+            for (int b = 0; b < T::n; b++) {
+                if (wx[b] == 0.f) continue;
+                const float w = wy[a] * wx[b];
+                const long long c = iu + b;
+                if (!rin || c < 0 || c >= in_nx) {
+                    if (!zero_outside) bad += fabsf(w);
+                    continue;
+                }
+                const size_t o = (size_t)r * in_pitch + (size_t)c;
+                if (in_mask && __ldg(in_mask + o)) {
+                    bad += fabsf(w);
+                    continue;
+                }
+                acc = fmaf(w, (float)__ldg(in + o), acc);
+            }
+        }
+    }
+    float val = acc / (sx * sy);
+    if (flags & SFFT_RESAMPLE_FLUX) {
+        float j00 = 0.f, j01 = 0.f, j10 = 0.f, j11 = 0.f;
+#pragma unroll
+        for (int k = 1; k < 10; k++) {
+            if (k >= wa.n) break;
+            int p, q;
+            mono_pq(k, p, q);
+            // d/di and d/dj of i^p j^q
+            const float ddi = p == 0 ? 0.f : (float)p * (p == 1 ? 1.f : p == 2 ? fi : fi * fi) *
+                                                 (q == 0 ? 1.f : q == 1 ? fj : q == 2 ? fj * fj : fj * fj * fj);
+            const float ddj = q == 0 ? 0.f : (float)q * (q == 1 ? 1.f : q == 2 ? fj : fj * fj) *
+                                                 (p == 0 ? 1.f : p == 1 ? fi : p == 2 ? fi * fi : fi * fi * fi);
+            j00 = fmaf(s_d[0][k], ddi, j00);
+            j01 = fmaf(s_d[0][k], ddj, j01);
+            j10 = fmaf(s_d[1][k], ddi, j10);
+            j11 = fmaf(s_d[1][k], ddj, j11);
+        }
+        val *= fabsf(j00 * j11 - j01 * j10);
+    }
+    const size_t oo = (size_t)y * out_pitch + x;
+    out[oo] = (In)val;
+    if (out_mask) out_mask[oo] = bad > 0.01f * (ax * ay) ? 1 : 0;
+}
+
+template <class In>
+cudaError_t launch(int method, const WarpArg &wa, int flags, const void *in, const uint8_t *in_mask, int in_ny,
+                   int in_nx, int in_pitch, void *out, uint8_t *out_mask, int out_ny, int out_nx, int out_pitch,
+                   cudaStream_t st) {
+    dim3 grid((out_nx + kTile - 1) / kTile, (out_ny + kTile - 1) / kTile);
+    note_launch();
+    if (method == SFFT_LANCZOS3)
+        k_resample<In, SFFT_LANCZOS3><<<grid, kThreads, 0, st>>>(
+            wa, flags, (const In *)in, in_mask, in_ny, in_nx, in_pitch, (In *)out, out_mask, out_ny, out_nx, out_pitch);
+    else
+        k_resample<In, SFFT_BILINEAR><<<grid, kThreads, 0, st>>>(
+            wa, flags, (const In *)in, in_mask, in_ny, in_nx, in_pitch, (In *)out, out_mask, out_ny, out_nx, out_pitch);
+    return cudaGetLastError();
+}
+
+bool ranges_overlap(const void *a, size_t na, const void *b, size_t nb) {
+    if (!a || !b) return false;
+    const char *pa = (const char *)a, *pb = (const char *)b;
+    return pa < pb + nb && pb < pa + na;
+}
+
+sfft_status run(const WarpArg &wa, int method, int flags, int in_ny, int in_nx, int in_pitch, int dtype,
+                const void *in, const uint8_t *in_mask, int out_ny, int out_nx, int out_pitch, void *out,
+                uint8_t *out_mask, cudaStream_t st, const char *who) {
+    char buf[256];
+    const size_t es = dtype == SFFT_F64 ? 8 : 4;
+    const size_t in_n = (size_t)(in_ny - 1) * in_pitch + in_nx, out_n = (size_t)(out_ny - 1) * out_pitch + out_nx;
+    if (ranges_overlap(out, out_n * es, in, in_n * es) || ranges_overlap(out, out_n * es, in_mask, in_n) ||
+        ranges_overlap(out_mask, out_n, in, in_n * es) || ranges_overlap(out_mask, out_n, in_mask, in_n) ||
+        ranges_overlap(out_mask, out_n, out, out_n * es)) {
+        snprintf(buf, sizeof buf, "%s: an output overlaps an input or the other output", who);
+        set_global_error(buf);
+        return SFFT_ERR_INVALID_ARG;
+    }
+    cudaError_t e = dtype == SFFT_F64 ? launch<double>(method, wa, flags, in, in_mask, in_ny, in_nx, in_pitch, out,
+                                                       out_mask, out_ny, out_nx, out_pitch, st)
+                                      : launch<float>(method, wa, flags, in, in_mask, in_ny, in_nx, in_pitch, out,
+                                                      out_mask, out_ny, out_nx, out_pitch, st);
+    if (e != cudaSuccess) {
+        snprintf(buf, sizeof buf, "%s: %s", who, cudaGetErrorString(e));
+        set_global_error(buf);
+        return SFFT_ERR_CUDA;
+    }
+    return SFFT_OK;
+}
+
+}  // namespace
+}  // namespace sfft
+
+using namespace sfft;
+
+extern "C" sfft_status sfft_resample(const sfft_warp *warp, int32_t method, int32_t flags, int32_t in_ny,
+                                     int32_t in_nx, int32_t in_pitch, int32_t dtype, const void *in,
+                                     const uint8_t *in_mask, int32_t out_ny, int32_t out_nx, int32_t out_pitch,
+                                     void *out, uint8_t *out_mask, sfft_stream_t stream) {
+    if (!warp || !in || !out || warp->degree < 1 || warp->degree > 3 || in_ny < 1 || in_nx < 1 || out_ny < 1 ||
+        out_nx < 1 || (method != SFFT_LANCZOS3 && method != SFFT_BILINEAR) ||
+        (flags & ~(SFFT_RESAMPLE_FLUX | SFFT_RESAMPLE_ZERO_OUTSIDE)) || (dtype != SFFT_F32 && dtype != SFFT_F64)) {
+        set_global_error("sfft_resample: need a warp of degree 1..3, non-empty frames, device images, "
+                         "a known method, flags and dtype");
+        return SFFT_ERR_INVALID_ARG;
+    }
+    if (in_pitch == 0) in_pitch = in_nx;
+    if (out_pitch == 0) out_pitch = out_nx;
+    if (in_pitch < in_nx || out_pitch < out_nx) {
+        set_global_error("sfft_resample: pitch smaller than the row length");
+        return SFFT_ERR_INVALID_ARG;
+    }
+    WarpArg wa;
+    wa.n = npoly(warp->degree);
+    wa.xr = warp->x_ref;
+    wa.yr = warp->y_ref;
+    for (int k = 0; k < 10; k++) {
+        wa.cu[k] = k < wa.n ? warp->cu[k] : 0.0;
+        wa.cv[k] = k < wa.n ? warp->cv[k] : 0.0;
+    }
+    return run(wa, method, flags, in_ny, in_nx, in_pitch, dtype, in, in_mask, out_ny, out_nx, out_pitch, out,
+               out_mask, reinterpret_cast<cudaStream_t>(stream), "sfft_resample");
+}
+
+extern "C" sfft_status sfft_align_psf(const sfft_warp *warp, double x, double y, int32_t K, const float *psf_in,
+                                      float *psf_out, sfft_stream_t stream) {
+    if (!warp || !psf_in || !psf_out || warp->degree < 1 || warp->degree > 3 || K < 1 || K > 63 || K % 2 == 0) {
+        set_global_error("sfft_align_psf: need a warp of degree 1..3, device stamps and an odd K <= 63");
+        return SFFT_ERR_INVALID_ARG;
+    }
+    // Jacobian of the warp at (x, y), term by term in FP64
+    const int n = npoly(warp->degree);
+    const double dx = x - warp->x_ref, dy = y - warp->y_ref;
+    double J[2][2] = {{0, 0}, {0, 0}};
+    for (int k = 0; k < n; k++) {
+        int p, q;
+        mono_pq(k, p, q);
+        const double ddx = p > 0 ? p * pow(dx, p - 1) * pow(dy, q) : 0.0;
+        const double ddy = q > 0 ? q * pow(dx, p) * pow(dy, q - 1) : 0.0;
+        J[0][0] += warp->cu[k] * ddx;
+        J[0][1] += warp->cu[k] * ddy;
+        J[1][0] += warp->cv[k] * ddx;
+        J[1][1] += warp->cv[k] * ddy;
+    }
+    // output stamp pixel (r, s) reads template stamp position c + J (s - c, r - c)
+    const double c = (K - 1) / 2.0;
+    WarpArg wa;
+    wa.n = 3;
+    wa.xr = c;
+    wa.yr = c;
+    for (int k = 0; k < 10; k++) wa.cu[k] = wa.cv[k] = 0.0;
+    wa.cu[0] = c;
+    wa.cu[1] = J[0][0];
+    wa.cu[2] = J[0][1];
+    wa.cv[0] = c;
+    wa.cv[1] = J[1][0];
+    wa.cv[2] = J[1][1];
+    return run(wa, SFFT_LANCZOS3, SFFT_RESAMPLE_FLUX | SFFT_RESAMPLE_ZERO_OUTSIDE, K, K, K, SFFT_F32, psf_in, nullptr,
+               K, K, K, psf_out, nullptr, reinterpret_cast<cudaStream_t>(stream), "sfft_align_psf");
+}

@@ -24,7 +24,8 @@ EXPORTED = ("sfft_plan", "sfft_destroy", "sfft_n_unknowns", "sfft_workspace_size
             "sfft_batch_create", "sfft_batch_run", "sfft_batch_info", "sfft_batch_destroy",
             "sfft_tuning_get", "sfft_tuning_set", "sfft_autotune", "sfft_tuning_save", "sfft_tuning_load",
             "sfft_profile", "sfft_stage_times", "sfft_launch_count", "sfft_subtract_noalloc",
-            "sfft_cross_convolve",
+            "sfft_cross_convolve", "sfft_resample", "sfft_align_psf", "sfft_decorrelation_kernel",
+            "sfft_forced_photometry",
             "sfft_status_string", "sfft_last_error",
             "sfft_cnn_create", "sfft_cnn_destroy", "sfft_cnn_param_count", "sfft_cnn_set_params",
             "sfft_cnn_get_params", "sfft_cnn_forward", "sfft_cnn_gradients", "sfft_cnn_train_step",
@@ -72,7 +73,22 @@ class sfft_tuning(ctypes.Structure):
                 ("reserved", ctypes.c_int32 * 2)]
 
 
+class sfft_warp(ctypes.Structure):
+    _fields_ = [("degree", ctypes.c_int32), ("reserved", ctypes.c_int32), ("x_ref", ctypes.c_double),
+                ("y_ref", ctypes.c_double), ("cu", ctypes.c_double * 10), ("cv", ctypes.c_double * 10)]
+
+
+class sfft_phot_job(ctypes.Structure):
+    _fields_ = [("image", ctypes.c_void_p), ("weight", ctypes.c_void_p), ("mask", ctypes.c_void_p),
+                ("psf", ctypes.c_void_p), ("x", ctypes.c_double), ("y", ctypes.c_double),
+                ("ny", ctypes.c_int32), ("nx", ctypes.c_int32), ("pitch", ctypes.c_int32),
+                ("dtype", ctypes.c_int32)]
+
+
 BATCH_GRAPH, BATCH_AUTOTUNE = 1, 2
+LANCZOS3, BILINEAR = 0, 1
+RESAMPLE_FLUX, RESAMPLE_ZERO_OUTSIDE = 1, 2
+PHOT_BACKGROUND = 1
 
 _lib = None
 _lock = threading.Lock()
@@ -114,6 +130,12 @@ def load_library(path: str = LIB_PATH):
         lib.sfft_tuning_load.argtypes = [ctypes.c_char_p]
         lib.sfft_subtract_noalloc.argtypes = [ctypes.POINTER(sfft_desc), P, P, P, P, P]
         lib.sfft_cross_convolve.argtypes = [I32, I32, I32, I32, I32, P, P, P, P, P, P, P]
+        D = ctypes.c_double
+        lib.sfft_resample.argtypes = [ctypes.POINTER(sfft_warp), I32, I32, I32, I32, I32, I32, P, P, I32, I32, I32,
+                                      P, P, P]
+        lib.sfft_align_psf.argtypes = [ctypes.POINTER(sfft_warp), D, D, I32, P, P, P]
+        lib.sfft_decorrelation_kernel.argtypes = [I32, I32, I32, I32, P, D, D, I32, P, P, D, D, I32, P, P, P]
+        lib.sfft_forced_photometry.argtypes = [I32, P, I32, I32, P, P]
         lib.sfft_profile.argtypes = [P, I32]
         lib.sfft_stage_times.argtypes = [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(I32)]
         lib.sfft_launch_count.argtypes = [ctypes.POINTER(ctypes.c_uint64)]
@@ -385,6 +407,64 @@ def sfft_cross_convolve(ny: int, nx: int, K: int, sci, tmpl, psf_sci, psf_tmpl, 
     K x K float32 stamps (device); a half whose image, stamp or output is None is skipped."""
     _check(load_library().sfft_cross_convolve(ny, nx, pitch, dtype, K, _ptr(sci), _ptr(tmpl), _ptr(psf_sci),
                                               _ptr(psf_tmpl), _ptr(sci_out), _ptr(tmpl_out), _stream(stream)))
+
+
+def make_warp(degree: int, cu, cv, x_ref: float = 0.0, y_ref: float = 0.0) -> sfft_warp:
+    """Coordinate polynomials u(x, y), v(x, y) about (x_ref, y_ref) (monomial order of sfft.h)."""
+    w = sfft_warp()
+    w.degree, w.x_ref, w.y_ref = degree, x_ref, y_ref
+    for k in range(10):
+        w.cu[k] = float(cu[k]) if k < len(cu) else 0.0
+        w.cv[k] = float(cv[k]) if k < len(cv) else 0.0
+    return w
+
+
+def sfft_resample(warp: sfft_warp, src, out, src_mask=None, out_mask=None, method: int = LANCZOS3, flags: int = 0,
+                  dtype: int = F32, in_shape=None, out_shape=None, in_pitch: int = 0, out_pitch: int = 0,
+                  stream=None):
+    """Resample the template (device) onto the science grid; shapes default to the tensors'."""
+    iny, inx = in_shape if in_shape is not None else tuple(src.shape)
+    ony, onx = out_shape if out_shape is not None else tuple(out.shape)
+    _check(load_library().sfft_resample(ctypes.byref(warp), method, flags, iny, inx, in_pitch, dtype, _ptr(src),
+                                        _ptr(src_mask), ony, onx, out_pitch, _ptr(out), _ptr(out_mask),
+                                        _stream(stream)))
+
+
+def sfft_align_psf(warp: sfft_warp, x: float, y: float, psf_in, psf_out, stream=None):
+    """The template PSF stamp (device, K x K float32) aligned to the science grid at (x, y)."""
+    _check(load_library().sfft_align_psf(ctypes.byref(warp), x, y, psf_in.shape[0], _ptr(psf_in), _ptr(psf_out),
+                                         _stream(stream)))
+
+
+def sfft_decorrelation_kernel(ny: int, nx: int, L: int, dk: int, coeffs, x: float, y: float, psf_sci, psf_tmpl,
+                              sigma_sci: float, sigma_tmpl: float, phi, psf_out=None, stream=None):
+    """Decorrelation kernel phi (device M x M float32; M = phi.shape[0]) at pixel (x, y) and,
+    optionally, the decorrelated science PSF."""
+    _check(load_library().sfft_decorrelation_kernel(ny, nx, L, dk, _ptr(coeffs), x, y, psf_sci.shape[0],
+                                                    _ptr(psf_sci), _ptr(psf_tmpl), sigma_sci, sigma_tmpl,
+                                                    phi.shape[0], _ptr(phi), _ptr(psf_out), _stream(stream)))
+
+
+def phot_jobs(jobs) -> "ctypes.Array":
+    """Host array of sfft_phot_job from dicts (image, psf, x, y, [weight, mask, ny, nx, pitch, dtype])."""
+    arr = (sfft_phot_job * len(jobs))()
+    for a, j in zip(arr, jobs):
+        img = j["image"]
+        a.image, a.psf = _ptr(img), _ptr(j["psf"])
+        a.weight, a.mask = _ptr(j.get("weight")), _ptr(j.get("mask"))
+        a.x, a.y = float(j["x"]), float(j["y"])
+        a.ny = j.get("ny", img.shape[0] if hasattr(img, "shape") else 0)
+        a.nx = j.get("nx", img.shape[1] if hasattr(img, "shape") else 0)
+        a.pitch = j.get("pitch", 0)
+        a.dtype = j.get("dtype", F64 if getattr(img, "dtype", None) is not None and "64" in str(img.dtype) else F32)
+    return arr
+
+
+def sfft_forced_photometry(jobs_dev, njobs: int, K: int, results, flags: int = 0, stream=None):
+    """PSF fluxes of njobs jobs; jobs_dev: device copy of a :func:`phot_jobs` array; results:
+    device float64 (njobs, 8)."""
+    _check(load_library().sfft_forced_photometry(njobs, _ptr(jobs_dev), K, flags, _ptr(results),
+                                                 _stream(stream)))
 
 
 def sfft_subtract_noalloc(desc: sfft_desc, sci, tmpl, coeffs, diff, stream=None):
