@@ -320,6 +320,9 @@ def run_ours(args, world, rank, local):
     d2h = args.pairs * (host[0]["diff"].numel() * 4 + n * 8)
     e2e_batch.close()
 
+    # ---- the other GPU steps of the pipeline on the same pairs, per pair
+    steps_info = pipeline_steps(args, dev, stream, dev_pairs, seeds, bcoeffs, bdiffs, NY, NX, ms / (args.steps * args.pairs))
+
     # ---- HBM roofline (the metric's HBM roofline %), per stage of the plain pass, from its
     # per-stage CUDA events on the plan's stream.  Algorithmic bytes: the per-pixel figures of
     # the two-pass FFT model of the hot path for the steps each stage performs (a1 + a2 row
@@ -418,6 +421,7 @@ def run_ours(args, world, rank, local):
         "roofline": roofline,
         "hbm_stages": hbm_stages,
         "hbm_whole_path": whole,
+        "pipeline_steps": steps_info,
         "e2e": {"value": round(e2e_value, 3), "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": int(launches),
         "clocks": clk,
@@ -433,6 +437,103 @@ def run_ours(args, world, rank, local):
     plan.close()
     if world > 1:
         dist.destroy_process_group()
+
+
+def pipeline_steps(args, dev, stream, dev_pairs, seeds, coeffs, diffs, NY, NX, fit_ms_per_pair):
+    """Per-pair device time of the GPU steps around the fit (Sec. "Pipeline steps"), on the
+    benchmark's own pairs: step 4 (template and mask resampled onto the science grid with a
+    0.3 degree rotation, a 1e-4 scale change, a sub-pixel shift and a cubic distortion;
+    Lanczos-3; the template PSF aligned), step 5 (cross-convolution with 25 x 25 stamps),
+    step 7 (decorrelation kernel at the frame centre, applied to D and to the cross-convolved
+    science image) and steps 8-9 (forced photometry of 500 field stars and the transient per
+    pair, constant background).  Roofline per step: the own-traffic HBM fraction (each
+    input read once, each output written once) for the resampler, the FP32 fraction
+    (K^2 FMAs per output pixel) for the two convolutions."""
+    import math
+
+    import numpy as np
+    import torch
+
+    from paper_2509_18544_gb300 import sfft, synth
+
+    P = len(dev_pairs)
+    K, M = 25, 25
+    fields = [pair_field(sd) for sd in seeds]
+    ps = [torch.from_numpy(synth.psf_stamp_at(f, "sci", 0.0, 0.0, K)).to(dev) for f in fields]
+    pt = [torch.from_numpy(synth.psf_stamp_at(f, "tmpl", 0.0, 0.0, K)).to(dev) for f in fields]
+    th, sc = math.radians(0.3), 1.0001
+    c, sn, x0 = sc * math.cos(th), sc * math.sin(th), (NX - 1) / 2.0
+    warp = sfft.make_warp(3, [x0 + 3.37, c, -sn, 0, 0, 0, 1e-10, 0, 0, 0],
+                          [x0 - 2.81, sn, c, 0, 0, 0, 0, 0, 1e-10, 0], x0, x0)
+    t_al = [torch.empty_like(p[1]) for p in dev_pairs]
+    m_al = [torch.empty_like(p[2]) for p in dev_pairs]
+    psf_al = [torch.empty_like(x) for x in pt]
+    s_cc = [torch.empty_like(p[0]) for p in dev_pairs]
+    t_cc = [torch.empty_like(p[1]) for p in dev_pairs]
+    phi = [torch.empty((M, M), dtype=torch.float32, device=dev) for _ in range(P)]
+    psf_dec = [torch.empty((M, M), dtype=torch.float32, device=dev) for _ in range(P)]
+    d_dec = [torch.empty_like(p[0]) for p in dev_pairs]
+    s_dec = [torch.empty_like(p[0]) for p in dev_pairs]
+    rng = np.random.default_rng(5)
+    jobs = []
+    for k in range(P):
+        xs, ys = rng.uniform(20, NX - 20, 501), rng.uniform(20, NY - 20, 501)
+        jobs += [dict(image=d_dec[k], psf=psf_dec[k], x=x, y=y) for x, y in zip(xs, ys)]
+    arr = sfft.phot_jobs(jobs)
+    jobs_dev = torch.frombuffer(bytearray(bytes(arr)), dtype=torch.uint8).to(dev)
+    res = torch.empty((len(jobs), 8), dtype=torch.float64, device=dev)
+
+    def step4():
+        for k, (S, T, Mk) in enumerate(dev_pairs):
+            sfft.sfft_resample(warp, T, t_al[k], Mk, m_al[k], sfft.LANCZOS3, 0, stream=stream)
+            sfft.sfft_align_psf(warp, x0, x0, pt[k], psf_al[k], stream=stream)
+
+    def step5():
+        for k, (S, T, Mk) in enumerate(dev_pairs):
+            sfft.sfft_cross_convolve(NY, NX, K, S, T, ps[k], pt[k], s_cc[k], t_cc[k], stream=stream)
+
+    def step7k():
+        for k in range(P):
+            sfft.sfft_decorrelation_kernel(NY, NX, L, DK, coeffs[k], x0, x0, ps[k], pt[k], 1.0, 1.0, phi[k],
+                                           psf_dec[k], stream=stream)
+
+    def step7a():
+        for k in range(P):
+            sfft.sfft_cross_convolve(NY, NX, M, diffs[k], s_cc[k], phi[k], phi[k], d_dec[k], s_dec[k], stream=stream)
+
+    def step9():
+        sfft.sfft_forced_photometry(jobs_dev, len(jobs), M, res, sfft.PHOT_BACKGROUND, stream=stream)
+
+    ms = {}
+    for name, fn in (("align_resample", step4), ("cross_convolve", step5), ("decorrelation_kernel", step7k),
+                     ("decorrelation_apply", step7a), ("forced_photometry", step9)):
+        fn()
+        ms[name] = _timed_once(fn, stream, reps=5) / P
+    peaks = measured_peaks()
+    hbm = peaks.get("hbm_gbs", 6785.5)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    fp32 = sms * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6
+    px = float(NY * NX)
+    conv_flops = 2 * 2.0 * K * K * px  # two images, K^2 FMAs each per pixel
+    total = sum(ms.values()) + fit_ms_per_pair
+    bad = int((res[:, 5] != 0).sum().item())
+    return {
+        "ms_per_pair": {k: round(v, 4) for k, v in ms.items()},
+        "fit_subtract_ms_per_pair": round(fit_ms_per_pair, 4),
+        "pipeline_pairs_per_s": round(1e3 / total, 2),
+        "roofline": {
+            "align_resample": {"bound": "hbm", "own_bytes": round(10.0 * px),
+                               "frac": round(10.0 * px / (ms["align_resample"] * 1e-3) / 1e9 / hbm, 4)},
+            "cross_convolve": {"bound": "alu", "flops": conv_flops,
+                               "frac": round(conv_flops / (ms["cross_convolve"] * 1e-3) / fp32, 4)},
+            "decorrelation_apply": {"bound": "alu", "flops": 2 * 2.0 * M * M * px,
+                                    "frac": round(2 * 2.0 * M * M * px / (ms["decorrelation_apply"] * 1e-3) / fp32, 4)},
+        },
+        "photometry_jobs_per_pair": 501, "photometry_unsolved": bad,
+        "config": "steps 4, 5, 7, 8-9 on the benchmark's pairs: rotation 0.3 deg + 1e-4 scale + cubic "
+                  "distortion, Lanczos-3 with mask; 25 x 25 stamps; M = 25 decorrelation kernel; 501 photometry "
+                  "jobs per pair",
+    }
 
 
 # ----------------------------------------------------------------------------- oracle arm

@@ -64,7 +64,7 @@ __device__ __forceinline__ void lanczos3_taps(float f, float w[6]) {
         const int m = j - 2;
         const float t = f - (float)m;
         const float sg = (m & 1) ? -s1 : s1;
-        w[j] = sg * sm[j] * k / (t * t);
+        w[j] = __fdividef(sg * sm[j] * k, t * t);
     }
 }
 

@@ -4,14 +4,19 @@
 //
 // Coordinate model, window, bad-tap rule and flux scaling are the ones sfft.h states for
 // sfft_resample.  Kernel design: one CTA per 16 x 16 output tile, one pixel per thread.
-// Twenty threads first re-expand the coordinate polynomials about the tile corner in FP64
+// Twenty threads first re-expand the coordinate polynomials about the tile corner
 // (d_{p'q'} = sum_{p >= p', q >= q'} c_pq C(p, p') C(q, q') ax^(p - p') ay^(q - q'),
-// (ax, ay) the corner's offset from the origin), keeping the corner value in FP64 and the
-// other terms in FP32; each pixel then adds its FP32 Taylor part (|i|, |j| < 16) to the
+// (ax, ay) the corner's offset from the origin): the corner value d_00 in FP64, the other
+// terms in FP32 (they multiply offsets below 16); each pixel then adds its FP32 Taylor part to the
 // fractional part of the corner value, so the integer tap position is exact and the
-// fraction carries an error of a few 1e-6 pixel.  Taps read the template through the
-// read-only path; a tile whose taps all land inside an unmasked template skips the
-// per-tap tests.  FP32 weights and sums (FP64 images are converted on load).
+// fraction carries an error of a few 1e-6 pixel.  The tile's tap footprint (exact, from a
+// min/max over its pixels) is staged in shared memory as (value, bad) pairs -- masked and
+// outside pixels as (0, 1), or (0, 0) outside with SFFT_RESAMPLE_ZERO_OUTSIDE -- so the taps
+// are branch-free: sum w v and sum |w| bad.  Footprints above 48 x 48 (scale changes beyond
+// ~2.6x) take a per-tap path from global memory.  A tap of weight exactly 0 then adds
+// nothing either way, except that a non-finite unmasked pixel poisons its neighbours
+// through 0 x inf: unmasked pixels are taken to be finite.  FP32 weights and sums (FP64
+// images are converted on load).
 #include <math.h>
 #include <stdio.h>
 
@@ -24,6 +29,8 @@ void set_global_error(const char *msg);
 namespace {
 
 constexpr int kTile = 16, kThreads = kTile * kTile;
+constexpr int kStage = 48 * 48;  // staged footprint (value, bad) pairs: 18 KB
+constexpr int kFar = -2147483647 - 1;
 
 struct WarpArg {
     int n;  // monomials in use
@@ -31,15 +38,17 @@ struct WarpArg {
     double cu[10], cv[10];
 };
 
-__device__ __forceinline__ double ipow(double a, int e) {
-    double r = 1.0;
-    for (int i = 0; i < e; i++) r *= a;
-    return r;
+__device__ __forceinline__ float binom3f(int n, int k) {  // C(n, k) for 0 <= k <= n <= 3
+    return (k == 0 || k == n) ? 1.f : (float)n;
 }
 
-__device__ __forceinline__ double binom3(int n, int k) {  // n <= 3
-    const int t[4][4] = {{1, 0, 0, 0}, {1, 1, 0, 0}, {1, 2, 1, 0}, {1, 3, 3, 1}};
-    return t[n][k];
+// exponents (p, q) of the ten coordinate monomials in the order of sfft.h
+__host__ __device__ constexpr int mono_p(int k) { return k == 1 || k == 4 || k == 8 ? 1 : k == 3 || k == 7 ? 2 : k == 6 ? 3 : 0; }
+__host__ __device__ constexpr int mono_q(int k) { return k == 2 || k == 4 || k == 7 ? 1 : k == 5 || k == 8 ? 2 : k == 9 ? 3 : 0; }
+
+template <class R>
+__device__ __forceinline__ R powi3(R a, int e) {  // a^e for 0 <= e <= 3, without an indexed table
+    return e == 0 ? R(1) : e == 1 ? a : e == 2 ? a * a : a * a * a;
 }
 
 template <int METHOD>
@@ -65,26 +74,45 @@ __global__ void __launch_bounds__(kThreads) k_resample(WarpArg wa, int flags, co
                                                        uint8_t *__restrict__ out_mask, int out_ny, int out_nx,
                                                        int out_pitch) {
     using T = Taps<METHOD>;
-    __shared__ double s_c0[2];
+    __shared__ int s_i0[2];    // floor of the corner's u and v
+    __shared__ float s_f0[2];  // their fractions
     __shared__ float s_d[2][10];
+    __shared__ int s_bb[4];  // tap footprint of the tile: u min, u max, v min, v max
+    __shared__ float2 s_stage[kStage];
     const int x0 = blockIdx.x * kTile, y0 = blockIdx.y * kTile, t = threadIdx.x;
-    if (t < 2 * wa.n) {
-        const int k = t % wa.n;
-        const double *c = t < wa.n ? wa.cu : wa.cv;
-        int pk, qk;
-        mono_pq(k, pk, qk);
+    if (t == 0) {
+        s_bb[0] = s_bb[2] = 2147483647;
+        s_bb[1] = s_bb[3] = -2147483647 - 1;
+    }
+    if (t < 20) {
+        // lanes 0..9: u, lanes 10..19: v; lane k of each: Taylor coefficient k about the corner
+        const int k = t % 10;
+        const double *c = t < 10 ? wa.cu : wa.cv;
+        const int pk = mono_p(k), qk = mono_q(k);
         const double ax = (double)x0 - wa.xr, ay = (double)y0 - wa.yr;
-        double s = 0.0;
-        for (int j = 0; j < wa.n; j++) {
-            int p, q;
-            mono_pq(j, p, q);
-            if (p < pk || q < qk) continue;
-            s += c[j] * binom3(p, pk) * binom3(q, qk) * ipow(ax, p - pk) * ipow(ay, q - qk);
+        if (k == 0) {
+            // the corner value in FP64, kept as integer part + FP32 fraction (far outside: flagged)
+            double sv = 0.0;
+#pragma unroll
+            for (int jm = 0; jm < 10; jm++)
+                if (jm < wa.n) sv = fma(c[jm], powi3(ax, mono_p(jm)) * powi3(ay, mono_q(jm)), sv);
+            const bool far = !(fabs(sv) < 1.0e9);
+            const double fl = far ? 0.0 : floor(sv);
+            s_i0[t < 10 ? 0 : 1] = far ? kFar : (int)fl;
+            s_f0[t < 10 ? 0 : 1] = far ? 0.f : (float)(sv - fl);
+        } else if (k < wa.n) {
+            // d_k = sum_{p >= pk, q >= qk} c_pq C(p, pk) C(q, qk) ax^(p - pk) ay^(q - qk), FP32
+            const float fx = (float)ax, fy = (float)ay;
+            float sv = 0.f;
+#pragma unroll
+            for (int jm = 1; jm < 10; jm++) {
+                const int p = mono_p(jm), q = mono_q(jm);
+                if (jm < wa.n && p >= pk && q >= qk)
+                    sv = fmaf((float)c[jm] * binom3f(p, pk) * binom3f(q, qk), powi3(fx, p - pk) * powi3(fy, q - qk),
+                              sv);
+            }
+            s_d[t < 10 ? 0 : 1][k] = sv;
         }
-        if (k == 0)
-            s_c0[t < wa.n ? 0 : 1] = s;
-        else
-            s_d[t < wa.n ? 0 : 1][k] = (float)s;
     }
     __syncthreads();
     const int i = t % kTile, j = t / kTile;
@@ -97,8 +125,7 @@ __global__ void __launch_bounds__(kThreads) k_resample(WarpArg wa, int flags, co
     float du = 0.f, dv = 0.f;
 #pragma unroll
     for (int k = 1; k < 10; k++) {
-        int p, q;
-        mono_pq(k, p, q);
+        const int p = mono_p(k), q = mono_q(k);
         mono[k] = (p == 0 ? 1.f : p == 1 ? fi : p == 2 ? fi * fi : fi * fi * fi) *
                   (q == 0 ? 1.f : q == 1 ? fj : q == 2 ? fj * fj : fj * fj * fj);
         if (k < wa.n) {
@@ -106,15 +133,13 @@ __global__ void __launch_bounds__(kThreads) k_resample(WarpArg wa, int flags, co
             dv = fmaf(s_d[1][k], mono[k], dv);
         }
     }
-    const double U0 = s_c0[0], V0 = s_c0[1];
     // far outside (or not finite): every tap is outside
-    const bool far = !(fabs(U0) < 1.0e9 && fabs(V0) < 1.0e9);
-    const double iu0 = far ? 0.0 : floor(U0), iv0 = far ? 0.0 : floor(V0);
-    const float tu = far ? 0.f : (float)(U0 - iu0) + du, tv = far ? 0.f : (float)(V0 - iv0) + dv;
+    const bool far = s_i0[0] == kFar || s_i0[1] == kFar;
+    const float tu = far ? 0.f : s_f0[0] + du, tv = far ? 0.f : s_f0[1] + dv;
     const float flu = floorf(tu), flv = floorf(tv);
     const float fu = tu - flu, fv = tv - flv;
-    long long iu = (long long)iu0 + (long long)flu + T::first;  // first tap column
-    long long iv = (long long)iv0 + (long long)flv + T::first;
+    const long long iu = far ? 0 : (long long)s_i0[0] + (long long)flu + T::first;  // first tap column
+    const long long iv = far ? 0 : (long long)s_i0[1] + (long long)flv + T::first;
     const bool zero_outside = flags & SFFT_RESAMPLE_ZERO_OUTSIDE;
     float wx[T::n], wy[T::n];
     T::weights(fu, wx);
@@ -127,42 +152,71 @@ __global__ void __launch_bounds__(kThreads) k_resample(WarpArg wa, int flags, co
         ax += fabsf(wx[k]);
         ay += fabsf(wy[k]);
     }
-    // interior tiles without a mask: taps need no test
-    const bool inside = !far && iu >= 0 && iu + T::n <= in_nx && iv >= 0 && iv + T::n <= in_ny;
-    const bool fast = __syncthreads_and(!live || (inside && in_mask == nullptr));
-    if (!live) return;
+    // the tile's tap footprint: staged in shared memory as (value, bad) pairs when it is small
+    if (live && !far) {
+        atomicMin(&s_bb[0], (int)iu);
+        atomicMax(&s_bb[1], (int)iu + T::n - 1);
+        atomicMin(&s_bb[2], (int)iv);
+        atomicMax(&s_bb[3], (int)iv + T::n - 1);
+    }
+    const bool any_far = __syncthreads_or(live && far);
+    const int bu0 = s_bb[0], bv0 = s_bb[2];
+    const int bw = s_bb[1] - bu0 + 1, bh = s_bb[3] - bv0 + 1;
+    const bool staged = !any_far && s_bb[1] >= bu0 && (long long)bw * bh <= kStage;
     float acc = 0.f, bad = 0.f;
-    if (fast) {
-        const In *row = in + (size_t)iv * in_pitch + iu;
-#pragma unroll
-        for (int a = 0; a < T::n; a++) {
-            float r = 0.f;
-#pragma unroll
-            for (int b = 0; b < T::n; b++) r = fmaf(wx[b], (float)__ldg(row + b), r);
-            acc = fmaf(wy[a], r, acc);
-            row += in_pitch;
-        }
-    } else if (far) {
-        bad = zero_outside ? 0.f : ax * ay;
-    } else {
-        for (int a = 0; a < T::n; a++) {
-            if (wy[a] == 0.f) continue;
-            const long long r = iv + a;
-            const bool rin = r >= 0 && r < in_ny;
-            for (int b = 0; b < T::n; b++) {
-                if (wx[b] == 0.f) continue;
-                const float w = wy[a] * wx[b];
-                const long long c = iu + b;
-                if (!rin || c < 0 || c >= in_nx) {
-                    if (!zero_outside) bad += fabsf(w);
-                    continue;
-                }
+    if (staged) {
+        for (int e = t; e < bw * bh; e += kThreads) {
+            const int r = bv0 + e / bw, c = bu0 + e % bw;
+            float2 vb = make_float2(0.f, zero_outside ? 0.f : 1.f);
+            if (r >= 0 && r < in_ny && c >= 0 && c < in_nx) {
                 const size_t o = (size_t)r * in_pitch + (size_t)c;
-                if (in_mask && __ldg(in_mask + o)) {
-                    bad += fabsf(w);
-                    continue;
+                if (in_mask && __ldg(in_mask + o))
+                    vb = make_float2(0.f, 1.f);
+                else
+                    vb = make_float2((float)__ldg(in + o), 0.f);
+            }
+            s_stage[e] = vb;
+        }
+        __syncthreads();
+        if (!live) return;
+        const float2 *row = s_stage + ((int)iv - bv0) * bw + ((int)iu - bu0);
+#pragma unroll
+        for (int a = 0; a < T::n; a++) {
+            float rv = 0.f, rb = 0.f;
+#pragma unroll
+            for (int b = 0; b < T::n; b++) {
+                const float2 vb = row[b];
+                rv = fmaf(wx[b], vb.x, rv);
+                rb = fmaf(fabsf(wx[b]), vb.y, rb);
+            }
+            acc = fmaf(wy[a], rv, acc);
+            bad = fmaf(fabsf(wy[a]), rb, bad);
+            row += bw;
+        }
+    } else {
+        if (!live) return;
+        if (far) {
+            bad = zero_outside ? 0.f : ax * ay;
+        } else {
+            for (int a = 0; a < T::n; a++) {
+                if (wy[a] == 0.f) continue;
+                const long long r = iv + a;
+                const bool rin = r >= 0 && r < in_ny;
+                for (int b = 0; b < T::n; b++) {
+                    if (wx[b] == 0.f) continue;
+                    const float w = wy[a] * wx[b];
+                    const long long c = iu + b;
+                    if (!rin || c < 0 || c >= in_nx) {
+                        if (!zero_outside) bad += fabsf(w);
+                        continue;
+                    }
+                    const size_t o = (size_t)r * in_pitch + (size_t)c;
+                    if (in_mask && __ldg(in_mask + o)) {
+                        bad += fabsf(w);
+                        continue;
+                    }
+                    acc = fmaf(w, (float)__ldg(in + o), acc);
                 }
-                acc = fmaf(w, (float)__ldg(in + o), acc);
             }
         }
     }

@@ -328,3 +328,14 @@ def cnn_init(n_out: int, seed: int) -> np.ndarray:
     parts.append(rng.normal(0.0, np.sqrt(2.0 / 128), (n_out, 128)).ravel())
     parts.append(np.zeros(n_out))
     return np.concatenate(parts).astype(np.float32)
+
+
+def psf_stamp_at(field, key: str, xh: float, yh: float, K: int = 25) -> np.ndarray:
+    """float32 K x K (K odd) unit-sum stamp of the ``key`` ("sci" or "tmpl") PSF of a field
+    at normalised position (xh, yh), centred on the middle element (cross-convolution,
+    decorrelation and photometry inputs)."""
+    off = np.arange(K) - K // 2
+    dy, dx = np.meshgrid(off, off, indexing="ij")
+    fd = field[key]
+    st = _moffat_ell(dx, dy, moffat_alpha(_fwhm_at(fd, xh, yh)), fd["e"], fd["phi"])
+    return (st / st.sum()).astype(np.float32)
