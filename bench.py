@@ -226,6 +226,9 @@ def run_ours(args, world, rank, local):
     sfft.sfft_profile(plan, False)
     plain_value = weak_value(args.steps, args.pairs, world, plain_ms)
     if args.plain_only:
+        # the pipeline steps around the fit on the plain fits' coefficients and differences
+        steps_info = pipeline_steps(args, dev, stream, dev_pairs, seeds, coeffs, diffs, NY, NX,
+                                    plain_ms / (args.steps * args.pairs))
         if rank == 0:
             print(json.dumps({"metric": METRIC, "value": round(plain_value, 3), "unit": UNIT, "n_gpus": world,
                               "steps": args.steps, "warmup": args.warmup,
@@ -233,7 +236,8 @@ def run_ours(args, world, rank, local):
                               "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                               "config": {"workload": workload, "mode": "plain only (profiling run)",
                                          "pairs_per_step_per_rank": args.pairs},
-                              "stages_ms_per_pair": {k: round(v / max(calls, 1), 4) for k, v in stages.items()}}),
+                              "stages_ms_per_pair": {k: round(v / max(calls, 1), 4) for k, v in stages.items()},
+                              "pipeline_steps": steps_info}),
                   flush=True)
         plan.close()
         if world > 1:
