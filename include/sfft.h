@@ -233,7 +233,9 @@ typedef struct {
                                  the summed cross-spectra at the lags; ycorr_split = CTAs per
                                  frequency); 1: direct correlation over the rows (K1 writes every
                                  image's spectrum; ycorr_bins, ycorr_split, ycorr_scalar apply) */
-    int32_t reserved[2];
+    int32_t ycorr_sets;       /* y-block FFT route, DK, DB <= 2: producer warp sets transforming
+                                 row blocks concurrently, 1 or 2 (0 = the default, 2) */
+    int32_t reserved[1];
 } sfft_tuning;
 /* The cached entry for desc (zeros and *cached = 0 when there is none). */
 sfft_status sfft_tuning_get(const sfft_desc *desc, sfft_tuning *t, int32_t *cached);

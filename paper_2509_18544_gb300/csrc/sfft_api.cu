@@ -150,6 +150,7 @@ bool make_geometry(const sfft_desc &d, Geometry &g, char *err, size_t errlen) {
             g.yfft = 0;  // this basis is too large for the y-FFT kernels: the direct route runs it
     }
     default_y2split(g);
+    g.ysets = 2;
     finish_geometry(g);
     return true;
 }

@@ -72,6 +72,8 @@ bool apply_tuning(const sfft_tuning &t, Geometry &g, char *err, size_t errlen) {
         g.ysplit = t.ycorr_split > 0 ? t.ycorr_split : default_ysplit(g);
     }
     finish_geometry(g);
+    if (t.ycorr_sets < 0 || t.ycorr_sets > 2) return snprintf(err, errlen, "ycorr_sets must be 0, 1 or 2"), false;
+    if (t.ycorr_sets > 0) g.ysets = t.ycorr_sets;
     if (t.ycorr_scalar != 0 && t.ycorr_scalar != 1) return snprintf(err, errlen, "ycorr_scalar must be 0 or 1"), false;
     g.ycorr_scalar = t.ycorr_scalar;
     if (t.subtract_ctas < 0 || t.subtract_ctas > 4)
@@ -304,14 +306,14 @@ sfft_status sfft_tuning_save(const char *path) {
     if (!f) return errf("sfft_tuning_save: cannot open %s", path), SFFT_ERR_INVALID_ARG;
     std::lock_guard<std::mutex> lk(g_tune_mu);
     fprintf(f, "# ny nx pitch L dk db dtype precision solver refine : ycorr_bins ycorr_split ycorr_scalar subtract_ctas "
-               "pcg_cluster ycorr_direct\n");
+               "pcg_cluster ycorr_direct ycorr_sets\n");
     for (auto &kv : g_tune) {
         const Key &k = kv.first;
         const sfft_tuning &t = kv.second;
-        fprintf(f, "%d %d %d %d %d %d %d %d %d %d : %d %d %d %d %d %d\n", std::get<0>(k), std::get<1>(k), std::get<2>(k),
-                std::get<3>(k), std::get<4>(k), std::get<5>(k), std::get<6>(k), std::get<7>(k), std::get<8>(k),
-                std::get<9>(k), t.ycorr_bins, t.ycorr_split, t.ycorr_scalar, t.subtract_ctas, t.pcg_cluster,
-                t.ycorr_direct);
+        fprintf(f, "%d %d %d %d %d %d %d %d %d %d : %d %d %d %d %d %d %d\n", std::get<0>(k), std::get<1>(k),
+                std::get<2>(k), std::get<3>(k), std::get<4>(k), std::get<5>(k), std::get<6>(k), std::get<7>(k),
+                std::get<8>(k), std::get<9>(k), t.ycorr_bins, t.ycorr_split, t.ycorr_scalar, t.subtract_ctas,
+                t.pcg_cluster, t.ycorr_direct, t.ycorr_sets);
     }
     const bool ok = fclose(f) == 0;
     return ok ? SFFT_OK : (errf("sfft_tuning_save: write failed"), SFFT_ERR_INVALID_ARG);
@@ -331,11 +333,11 @@ sfft_status sfft_tuning_load(const char *path) {
         memset(&d, 0, sizeof d);
         sfft_tuning t;
         memset(&t, 0, sizeof t);
-        int n = sscanf(line, "%d %d %d %d %d %d %d %d %d %d : %d %d %d %d %d %d", &d.ny, &d.nx, &d.pitch, &d.L, &d.dk,
-                       &d.db, &d.dtype, &d.precision, &d.solver, &d.refine, &t.ycorr_bins, &t.ycorr_split,
-                       &t.ycorr_scalar, &t.subtract_ctas, &t.pcg_cluster, &t.ycorr_direct);
-        if (n != 16) {
-            errf("sfft_tuning_load: %s:%d: expected 16 fields", path, lineno);
+        int n = sscanf(line, "%d %d %d %d %d %d %d %d %d %d : %d %d %d %d %d %d %d", &d.ny, &d.nx, &d.pitch, &d.L,
+                       &d.dk, &d.db, &d.dtype, &d.precision, &d.solver, &d.refine, &t.ycorr_bins, &t.ycorr_split,
+                       &t.ycorr_scalar, &t.subtract_ctas, &t.pcg_cluster, &t.ycorr_direct, &t.ycorr_sets);
+        if (n != 17) {
+            errf("sfft_tuning_load: %s:%d: expected 17 fields", path, lineno);
             result = SFFT_ERR_INVALID_ARG;
             break;
         }
@@ -398,6 +400,9 @@ sfft_status sfft_autotune(const sfft_desc *desc, const void *sci, const void *tm
                 t.ycorr_bins = kg;
                 r.push_back(t);
             }
+        sfft_tuning one_set = cur;  // the y-FFT route with one producer set
+        one_set.ycorr_sets = 1;
+        r.push_back(one_set);
         rounds.push_back(r);
     }
     for (int rd = 0; rd < 3 && result == SFFT_OK; rd++) {
@@ -406,7 +411,7 @@ sfft_status sfft_autotune(const sfft_desc *desc, const void *sci, const void *tm
             if (g0.yfft) cand = rounds[0];  // (a basis too large for the y-FFT kernels is direct already)
             else
                 for (const sfft_tuning &t : rounds[0])
-                    if (t.ycorr_scalar == 1 || t.ycorr_bins != g0.kg_max) cand.push_back(t);
+                    if (t.ycorr_direct && (t.ycorr_scalar == 1 || t.ycorr_bins != g0.kg_max)) cand.push_back(t);
         } else if (rd == 1) {
             Geometry g = g0;
             apply_tuning(cur, g, err, sizeof err);

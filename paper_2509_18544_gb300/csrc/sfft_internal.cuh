@@ -102,6 +102,7 @@ struct Geometry {
     int npair_all;             // correlation pairs: npair W-W, then nk (nb + 1) W-(Psi|S)
     int ypg, npg;              // pairs per y-FFT CTA, pair groups
     int y2split, y2split_ws;   // y-FFT CTAs per frequency (main pass, refinement pass)
+    int ysets;                 // producer sets of the specialised FP32 y-FFT kernel (1 or 2)
 };
 
 bool make_geometry(const sfft_desc &d, Geometry &g, char *err, size_t errlen);

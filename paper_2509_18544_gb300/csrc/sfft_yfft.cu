@@ -463,17 +463,27 @@ struct Basis {
     static constexpr int nst = (chunks + NP - 1) / NP;           // per producer thread
 };
 
-template <int DK, int DB>
+// thread roles of the warp-specialised kernel: NPS producer sets of B::NP threads (set s
+// transforms the units u0 + s, u0 + s + NPS, ...), then the B::NC consumers; 2 NPS column
+// buffers, so that every set double-buffers its own units
+template <int DK, int DB, int NPS>
+struct Roles {
+    using B = Basis<DK, DB>;
+    static constexpr int NP = B::NP, NPT = NPS * B::NP, NC = B::NC, NT = NPT + NC, NBUF = 2 * NPS;
+};
+
+template <int DK, int DB, int NPS>
 struct Smem32 {
     using B = Basis<DK, DB>;
     static constexpr int ncolp = (B::ncol + 1) & ~1;  // columns rounded to whole pairs
-    // tw3 [Py][3] float4, stg [2][Py][nrec] float2, yq [2][qmax][Py], cols [2][ncolp][Py]
-    // float4 (re, re, im, im), column tables [ncol][3] int
+    static constexpr int nbuf = 2 * NPS;
+    // tw3 [Py][3] float4, stg [NPS][2][Py][nrec] float2, yq [NPS][2][qmax][Py],
+    // cols [nbuf][ncolp][Py] float4 (re, re, im, im), column tables [ncol][3] int
     static constexpr size_t tw3 = 0;
     static constexpr size_t stg = tw3 + 16 * 3 * kPy;
-    static constexpr size_t yq = stg + 8 * 2 * (size_t)kPy * B::nrec;
-    static constexpr size_t cols = yq + 4 * 2 * (size_t)(B::qmax > 0 ? B::qmax : 1) * kPy;
-    static constexpr size_t tab = cols + 16 * 2 * (size_t)ncolp * kPy;
+    static constexpr size_t yq = stg + 8 * 2 * NPS * (size_t)kPy * B::nrec;
+    static constexpr size_t cols = yq + 4 * 2 * NPS * (size_t)(B::qmax > 0 ? B::qmax : 1) * kPy;
+    static constexpr size_t tab = cols + 16 * nbuf * (size_t)ncolp * kPy;
     static constexpr size_t bytes = tab + 4 * 3 * (size_t)B::ncol;
 };
 
@@ -534,11 +544,12 @@ struct ImageAcc {
 };
 
 // a consumer group: A images I0, I1, I2 (-1: none), summed over the units in FP32 and
-// folded into the CTA's share in global memory every kFold2 units
-template <int DK, int DB, int I0, int I1, int I2>
+// folded into the CTA's share in global memory every kFold2 units.  Unit u sits in column
+// buffer (u - u0) mod NBUF: barrier 1 + b says it is full, 5 + b that it has been read.
+template <int DK, int DB, int NPS, int I0, int I1, int I2>
 __device__ __forceinline__ void consume(const float4 *cols, int ky, int u0, int u1, float4 *share) {
-    using B = Basis<DK, DB>;
-    constexpr int NT = B::NT, ncolp = Smem32<DK, DB>::ncolp;
+    using R = Roles<DK, DB, NPS>;
+    constexpr int ncolp = Smem32<DK, DB, NPS>::ncolp, NB = R::NC + R::NP;
     ImageAcc<DK, DB, I0> a0;
     ImageAcc<DK, DB, I1> a1;
     ImageAcc<DK, DB, I2> a2;
@@ -546,13 +557,13 @@ __device__ __forceinline__ void consume(const float4 *cols, int ky, int u0, int 
     a1.zero();
     a2.zero();
     for (int u = u0; u < u1; u++) {
-        const int b = (u - u0) & 1;
-        nb_sync(1 + b, NT);  // cols[b] holds unit u
+        const int b = (u - u0) % R::NBUF;
+        nb_sync(1 + b, NB);  // cols[b] holds unit u
         const float4 *cb = cols + (size_t)b * ncolp * kPy + ky;
         a0.add(cb);
         a1.add(cb);
         a2.add(cb);
-        nb_arrive(3 + b, NT);  // done reading cols[b]
+        nb_arrive(5 + b, NB);  // done reading cols[b]
         if ((u - u0) % kFold2 == kFold2 - 1) {
             a0.fold(share, ky);
             a1.fold(share, ky);
@@ -564,19 +575,22 @@ __device__ __forceinline__ void consume(const float4 *cols, int ky, int u0, int 
     a2.fold(share, ky);
 }
 
-// Warp-specialised: the first NP threads are producers (stage a unit's rows, form and
-// transform its columns into cols[b], b = unit parity), the other NC threads consumers
-// (the products of cols[b]).  Barriers 1 + b ("cols[b] full") and 3 + b ("cols[b] read")
-// hand each buffer over, barrier 5 orders the producers' staging: producers transform unit
-// u + 1 while consumers multiply unit u.  The CTA's share of the sums, [pair][ky] (hi, lo)
-// float pairs, lives in its slice of `out` (zeroed here, folded into by the consumers).
-template <int DK, int DB>
-__global__ void __launch_bounds__(Basis<DK, DB>::NT, 1)
+// Warp-specialised: the first NPS x NP threads are producers in NPS sets (a set stages its
+// units' rows, forms and transforms their columns into cols[b], b = (u - u0) mod 2 NPS), the
+// other NC threads consumers (the products of cols[b], units in order).  Barriers 1 + b
+// ("cols[b] full") and 5 + b ("cols[b] read") hand each buffer over between one set and the
+// consumers; barrier 9 + s orders set s's staging.  A set transforms its next unit while the
+// consumers multiply earlier ones, and with two sets two units are transformed at once.  The
+// CTA's share of the sums, [pair][ky] (hi, lo) float pairs, lives in its slice of `out`
+// (zeroed here, folded into by the consumers).
+template <int DK, int DB, int NPS>
+__global__ void __launch_bounds__(Roles<DK, DB, NPS>::NT, 1)
     k_ycorr_fft32(const float2 *__restrict__ spec, const float *__restrict__ ypow, const float2 *__restrict__ tw_g,
                   Geometry g, int nsplit, float4 *__restrict__ out) {
     using B = Basis<DK, DB>;
-    using SM = Smem32<DK, DB>;
-    constexpr int NT = B::NT, NP = B::NP, NQ = B::qmax > 0 ? B::qmax : 1, ncolp = SM::ncolp;
+    using R = Roles<DK, DB, NPS>;
+    using SM = Smem32<DK, DB, NPS>;
+    constexpr int NT = R::NT, NP = R::NP, NQ = B::qmax > 0 ? B::qmax : 1, ncolp = SM::ncolp, NB = R::NC + R::NP;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float4 *tw3 = reinterpret_cast<float4 *>(smem_raw + SM::tw3);
     float2 *stg = reinterpret_cast<float2 *>(smem_raw + SM::stg);
@@ -617,8 +631,9 @@ __global__ void __launch_bounds__(Basis<DK, DB>::NT, 1)
     const int u0 = (int)((long)nunits * split / nsplit), u1 = (int)((long)nunits * (split + 1) / nsplit);
     __syncthreads();  // tables built, the share zeroed (each consumer later touches its own entries)
 
-    if (tid < NP) {
-        // ------------------------------------------------------------ producers
+    if (tid < R::NPT) {
+        // ------------------------------------------------------------ producers, set ps
+        const int ps = tid / NP, ptid = tid - ps * NP;
         const bool tiny = ny < kPy + 2 * G;  // rows may wrap more than once
         auto wrap = [&](int y) {
             if (tiny) {
@@ -628,40 +643,42 @@ __global__ void __launch_bounds__(Basis<DK, DB>::NT, 1)
             y += y < 0 ? ny : 0;
             return y >= ny ? y - ny : y;
         };
+        float2 *stg_s = stg + (size_t)ps * 2 * kPy * B::nrec;
+        float *yq_s = yq + (size_t)ps * 2 * NQ * kPy;
         auto stage = [&](int u, int buf) {
             const int s = u / nyb, t = u - s * nyb;
             const int yb = t * Uy - G;
-            float2 *dst = stg + (size_t)buf * kPy * B::nrec;
+            float2 *dst = stg_s + (size_t)buf * kPy * B::nrec;
 #pragma unroll
             for (int i = 0; i < B::nst; i++) {
                 // chunk `item`: row jr of the block, 16-byte piece `off / 2` of its record
-                const int item = tid + i * NP;
+                const int item = ptid + i * NP;
                 if (item >= B::chunks) continue;
                 const int jr = item / (B::nrec / 2), off = 2 * (item - jr * (B::nrec / 2));
                 const int yy = wrap(yb + jr);
                 const float2 *src = spec + (((size_t)s * ny + yy) * nkf + k) * B::nrec + off;
                 cp_async16(dst + jr * B::nrec + off, src);
             }
-            for (int v = tid; v < B::qmax * kPy; v += NP) {
+            for (int v = ptid; v < B::qmax * kPy; v += NP) {
                 const int q = v / kPy, jr = v - q * kPy;
-                cp_async4(yq + (size_t)buf * NQ * kPy + v, ypow + (size_t)(q + 1) * ny + wrap(yb + jr));
+                cp_async4(yq_s + (size_t)buf * NQ * kPy + v, ypow + (size_t)(q + 1) * ny + wrap(yb + jr));
             }
             cp_async_commit();
         };
-        const int hw = tid >> 4, lt = tid & 15;
-        const int wbase = (tid & ~31) >> 4;
-        if (u0 < u1) stage(u0, 0);
+        const int hw = ptid >> 4, lt = ptid & 15;
+        const int wbase = (ptid & ~31) >> 4;
+        if (u0 + ps < u1) stage(u0 + ps, 0);
         int sbuf = 0;
-        for (int u = u0; u < u1; u++) {
-            const int b = (u - u0) & 1;
+        for (int u = u0 + ps; u < u1; u += NPS) {
+            const int b = (u - u0) % R::NBUF;
             cp_async_wait_all();
-            nb_sync(5, NP);  // unit u staged for every producer; every transform of unit u - 1 done
-            if (u + 1 < u1) stage(u + 1, sbuf ^ 1);
-            if (u - u0 >= 2) nb_sync(3 + b, NT);  // consumers have read cols[b] (unit u - 2)
+            nb_sync(9 + ps, NP);  // unit u staged for every thread of the set; its previous transforms done
+            if (u + NPS < u1) stage(u + NPS, sbuf ^ 1);
+            if (u - u0 >= R::NBUF) nb_sync(5 + b, NB);  // consumers have read cols[b] (unit u - NBUF)
             const int t = u % nyb;
             const int avalid = min(Uy, ny - t * Uy);
-            const float2 *sb = stg + (size_t)sbuf * kPy * B::nrec;
-            const float *yqb = yq + (size_t)sbuf * NQ * kPy;
+            const float2 *sb = stg_s + (size_t)sbuf * kPy * B::nrec;
+            const float *yqb = yq_s + (size_t)sbuf * NQ * kPy;
             float4 *cb = cols + (size_t)b * ncolp * kPy;
             if (hw < B::ncp) {
                 const unsigned msk = (wbase < B::ncp ? 0x0000ffffu : 0u) | (wbase + 1 < B::ncp ? 0xffff0000u : 0u);
@@ -690,37 +707,39 @@ __global__ void __launch_bounds__(Basis<DK, DB>::NT, 1)
                     if (c1 != c0) pc[kPy + lt + 16 * m] = make_float4(v[m].re.y, v[m].re.y, v[m].im.y, v[m].im.y);
                 }
             }
-            nb_arrive(1 + b, NT);  // cols[b] holds unit u
+            nb_arrive(1 + b, NB);  // cols[b] holds unit u
             sbuf ^= 1;
         }
-        // take the consumers' last "read" arrivals, so every barrier generation completes
-        for (int u = (u1 - 2 > u0 ? u1 - 2 : u0); u < u1; u++) nb_sync(3 + ((u - u0) & 1), NT);
+        // take the consumers' last "read" arrivals on this set's buffers, so that every
+        // barrier generation completes
+        for (int u = u0 + ps; u < u1; u += NPS)
+            if (u + R::NBUF >= u1) nb_sync(5 + (u - u0) % R::NBUF, NB);
         return;
     }
     // ---------------------------------------------------------------- consumers
-    const int ct = tid - NP, ky = ct % kPy, grp = ct / kPy;
+    const int ct = tid - R::NPT, ky = ct % kPy, grp = ct / kPy;
     if constexpr (B::nk == 6) {
-        if (grp == 0) consume<DK, DB, 0, 3, 4>(cols, ky, u0, u1, share);
-        else consume<DK, DB, 1, 2, 5>(cols, ky, u0, u1, share);
+        if (grp == 0) consume<DK, DB, NPS, 0, 3, 4>(cols, ky, u0, u1, share);
+        else consume<DK, DB, NPS, 1, 2, 5>(cols, ky, u0, u1, share);
     } else if constexpr (B::nk == 3) {
-        consume<DK, DB, 0, 1, 2>(cols, ky, u0, u1, share);
+        consume<DK, DB, NPS, 0, 1, 2>(cols, ky, u0, u1, share);
     } else {
-        consume<DK, DB, 0, -1, -1>(cols, ky, u0, u1, share);
+        consume<DK, DB, NPS, 0, -1, -1>(cols, ky, u0, u1, share);
     }
 }
 
-template <int DK, int DB>
+template <int DK, int DB, int NPS>
 cudaError_t run_fft32(const Geometry &g, const void *spec, const void *ypow, const void *tw_y, double *part,
                       cudaStream_t st) {
-    using SM = Smem32<DK, DB>;
-    auto kern = k_ycorr_fft32<DK, DB>;
+    using SM = Smem32<DK, DB, NPS>;
+    auto kern = k_ycorr_fft32<DK, DB, NPS>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM::bytes);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return e;
     dim3 grid(g.nkf, g.y2split, 1);
     note_launch();
-    kern<<<grid, Basis<DK, DB>::NT, SM::bytes, st>>>((const float2 *)spec, (const float *)ypow, (const float2 *)tw_y,
+    kern<<<grid, Roles<DK, DB, NPS>::NT, SM::bytes, st>>>((const float2 *)spec, (const float *)ypow, (const float2 *)tw_y,
                                                      g, g.y2split, reinterpret_cast<float4 *>(part));
     return cudaGetLastError();
 }
@@ -730,13 +749,14 @@ cudaError_t run_fft32(const Geometry &g, const void *spec, const void *ypow, con
 bool fft32_specialised(int dk, int db) {
     return (dk == 2 && (db == 2 || db == 1 || db == 0)) || (dk == 1 && db <= 2) || (dk == 0 && db <= 2);
 }
-static_assert(Smem32<2, 2>::bytes <= 227 * 1024, "the DK = DB = 2 kernel's shared memory");
-static_assert(Basis<2, 2>::NT <= 512, "the DK = DB = 2 kernel keeps 128 registers per thread");
+static_assert(Smem32<2, 2, 2>::bytes <= 227 * 1024, "the DK = DB = 2 kernel's shared memory, two producer sets");
 
 cudaError_t dispatch_fft32(const Geometry &g, const void *spec, const void *ypow, const void *tw_y, double *part,
                            cudaStream_t st) {
-#define SFFT_Y32(a, b) \
-    if (g.dk == a && g.db == b) return run_fft32<a, b>(g, spec, ypow, tw_y, part, st);
+#define SFFT_Y32(a, b)                                                                           \
+    if (g.dk == a && g.db == b)                                                                  \
+        return g.ysets == 1 ? run_fft32<a, b, 1>(g, spec, ypow, tw_y, part, st)                  \
+                            : run_fft32<a, b, 2>(g, spec, ypow, tw_y, part, st);
     SFFT_Y32(2, 2) SFFT_Y32(2, 1) SFFT_Y32(2, 0) SFFT_Y32(1, 2) SFFT_Y32(1, 1) SFFT_Y32(1, 0) SFFT_Y32(0, 2)
     SFFT_Y32(0, 1) SFFT_Y32(0, 0)
 #undef SFFT_Y32
