@@ -288,7 +288,8 @@ sfft_status sfft_subtract_noalloc(const sfft_desc *desc, const void *sci, const 
  * d = (a - r, b - r) for stamp element [a][b] of the K x K row-major float32 stamps
  * (K = 2r + 1 odd, 1 <= K <= 31, centred on the middle element), cyclic on the ny x nx
  * frame.  Images and outputs are device arrays of `dtype` (SFFT_F32 or SFFT_F64) with a row
- * pitch of `pitch` elements (0 = nx); the arithmetic is FP32.  Either half is skipped when
+ * pitch of `pitch` elements (0 = nx); the arithmetic is FP32 (direct sums for K < 9, 256-point
+ * row-segment FFTs for K >= 9).  Either half is skipped when
  * its image, stamp or output is NULL (both NULL: SFFT_ERR_INVALID_ARG); an output may not
  * alias an input.  Queued on `stream`; no allocation. */
 sfft_status sfft_cross_convolve(int32_t ny, int32_t nx, int32_t pitch, int32_t dtype, int32_t K, const void *sci,
@@ -316,7 +317,7 @@ sfft_status sfft_cross_convolve(int32_t ny, int32_t nx, int32_t pitch, int32_t d
  *                 SFFT_RESAMPLE_ZERO_OUTSIDE outside taps are zeros and are not bad (stamps);
  *   flux          SFFT_RESAMPLE_FLUX multiplies by |det d(u,v)/d(x,y)| (values are fluxes
  *                 per pixel and the pixel area changes).
- * Coordinates are evaluated in FP64 at the corner of each 16 x 16 output tile and by an FP32
+ * Coordinates are evaluated in FP64 at the corner of each 32 x 32 output tile and by an FP32
  * Taylor expansion inside it (error a few 1e-6 pixel); weights and sums are FP32. */
 typedef struct {
     int32_t degree;            /* 1 .. 3 */

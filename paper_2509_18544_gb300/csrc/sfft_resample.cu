@@ -3,17 +3,17 @@
 // grid, and the template PSF aligned to it.
 //
 // Coordinate model, window, bad-tap rule and flux scaling are the ones sfft.h states for
-// sfft_resample.  Kernel design: one CTA per 16 x 16 output tile, one pixel per thread.
+// sfft_resample.  Kernel design: one CTA per 32 x 32 output tile, four pixels per thread.
 // Twenty threads first re-expand the coordinate polynomials about the tile corner
 // (d_{p'q'} = sum_{p >= p', q >= q'} c_pq C(p, p') C(q, q') ax^(p - p') ay^(q - q'),
 // (ax, ay) the corner's offset from the origin): the corner value d_00 in FP64, the other
 // terms in FP32 (they multiply offsets below 16); each pixel then adds its FP32 Taylor part to the
 // fractional part of the corner value, so the integer tap position is exact and the
-// fraction carries an error of a few 1e-6 pixel.  The tile's tap footprint (exact, from a
+// fraction carries an error below 1e-5 pixel.  The tile's tap footprint (exact, from a
 // min/max over its pixels) is staged in shared memory as (value, bad) pairs -- masked and
 // outside pixels as (0, 1), or (0, 0) outside with SFFT_RESAMPLE_ZERO_OUTSIDE -- so the taps
-// are branch-free: sum w v and sum |w| bad.  Footprints above 48 x 48 (scale changes beyond
-// ~2.6x) take a per-tap path from global memory.  A tap of weight exactly 0 then adds
+// are branch-free: sum w v and sum |w| bad.  Footprints above 56 x 56 (a scale change beyond
+// ~1.5x, or a rotation with a scale above ~1.1) take a per-tap path from global memory.  A tap of weight exactly 0 then adds
 // nothing either way, except that a non-finite unmasked pixel poisons its neighbours
 // through 0 x inf: unmasked pixels are taken to be finite.  FP32 weights and sums (FP64
 // images are converted on load).
@@ -28,14 +28,16 @@ void set_global_error(const char *msg);
 
 namespace {
 
-constexpr int kTile = 16, kThreads = kTile * kTile;
-constexpr int kStage = 48 * 48;  // staged footprint (value, bad) pairs: 18 KB
+constexpr int kTile = 32, kThreads = 256, kRowStep = kThreads / kTile, kPix = kTile / kRowStep;
+constexpr int kStage = 56 * 56;  // staged footprint (value, bad) pairs: 25 KB
 constexpr int kFar = -2147483647 - 1;
 
 struct WarpArg {
     int n;  // monomials in use
     double xr, yr;
     double cu[10], cv[10];
+    float xrf, yrf;          // the same rounded to FP32 (the Taylor terms)
+    float cuf[10], cvf[10];
 };
 
 __device__ __forceinline__ float binom3f(int n, int k) {  // C(n, k) for 0 <= k <= n <= 3
@@ -67,6 +69,36 @@ struct Taps<SFFT_BILINEAR> {
     }
 };
 
+// Per-pixel state derived from the tile's Taylor coefficients: the first tap's column and row
+// and the fractional positions (far: the map left the representable range; every tap outside).
+struct PixelPos {
+    long long iu, iv;
+    float fu, fv;
+};
+
+template <int FIRST>
+__device__ __forceinline__ PixelPos pixel_pos(int n, const int *i0, const float *f0, const float (*d)[10], float fi,
+                                              float fj, bool far) {
+    float du = 0.f, dv = 0.f;
+#pragma unroll
+    for (int k = 1; k < 10; k++) {
+        if (k < n) {
+            const int p = mono_p(k), q = mono_q(k);
+            const float m = powi3(fi, p) * powi3(fj, q);
+            du = fmaf(d[0][k], m, du);
+            dv = fmaf(d[1][k], m, dv);
+        }
+    }
+    const float tu = far ? 0.f : f0[0] + du, tv = far ? 0.f : f0[1] + dv;
+    const float flu = floorf(tu), flv = floorf(tv);
+    PixelPos r;
+    r.fu = tu - flu;
+    r.fv = tv - flv;
+    r.iu = far ? 0 : (long long)i0[0] + (long long)flu + FIRST;
+    r.iv = far ? 0 : (long long)i0[1] + (long long)flv + FIRST;
+    return r;
+}
+
 template <class In, int METHOD>
 __global__ void __launch_bounds__(kThreads) k_resample(WarpArg wa, int flags, const In *__restrict__ in,
                                                        const uint8_t *__restrict__ in_mask, int in_ny, int in_nx,
@@ -87,11 +119,11 @@ __global__ void __launch_bounds__(kThreads) k_resample(WarpArg wa, int flags, co
     if (t < 20) {
         // lanes 0..9: u, lanes 10..19: v; lane k of each: Taylor coefficient k about the corner
         const int k = t % 10;
-        const double *c = t < 10 ? wa.cu : wa.cv;
         const int pk = mono_p(k), qk = mono_q(k);
-        const double ax = (double)x0 - wa.xr, ay = (double)y0 - wa.yr;
         if (k == 0) {
             // the corner value in FP64, kept as integer part + FP32 fraction (far outside: flagged)
+            const double *c = t < 10 ? wa.cu : wa.cv;
+            const double ax = (double)x0 - wa.xr, ay = (double)y0 - wa.yr;
             double sv = 0.0;
 #pragma unroll
             for (int jm = 0; jm < 10; jm++)
@@ -102,71 +134,58 @@ __global__ void __launch_bounds__(kThreads) k_resample(WarpArg wa, int flags, co
             s_f0[t < 10 ? 0 : 1] = far ? 0.f : (float)(sv - fl);
         } else if (k < wa.n) {
             // d_k = sum_{p >= pk, q >= qk} c_pq C(p, pk) C(q, qk) ax^(p - pk) ay^(q - qk), FP32
-            const float fx = (float)ax, fy = (float)ay;
+            // (these terms multiply offsets below the tile size)
+            const float *c = t < 10 ? wa.cuf : wa.cvf;
+            const float fx = (float)x0 - wa.xrf, fy = (float)y0 - wa.yrf;
             float sv = 0.f;
 #pragma unroll
             for (int jm = 1; jm < 10; jm++) {
                 const int p = mono_p(jm), q = mono_q(jm);
                 if (jm < wa.n && p >= pk && q >= qk)
-                    sv = fmaf((float)c[jm] * binom3f(p, pk) * binom3f(q, qk), powi3(fx, p - pk) * powi3(fy, q - qk),
-                              sv);
+                    sv = fmaf(c[jm] * binom3f(p, pk) * binom3f(q, qk), powi3(fx, p - pk) * powi3(fy, q - qk), sv);
             }
             s_d[t < 10 ? 0 : 1][k] = sv;
         }
     }
     __syncthreads();
-    const int i = t % kTile, j = t / kTile;
-    const int x = x0 + i, y = y0 + j;
-    const bool live = x < out_nx && y < out_ny;
-    // Taylor part about the tile corner
-    float mono[10];
-    mono[0] = 1.f;
-    const float fi = (float)i, fj = (float)j;
-    float du = 0.f, dv = 0.f;
+    const bool far = s_i0[0] == kFar || s_i0[1] == kFar;
+    const int i = t % kTile, jt = t / kTile;  // column; rows jt + kRowStep r
+    const int x = x0 + i;
+    // the tile's tap footprint: staged in shared memory as (value, bad) pairs when it is small
+    int umin = 2147483647, umax = -2147483647 - 1, vmin = umin, vmax = umax;
+    bool live_any = false;
 #pragma unroll
-    for (int k = 1; k < 10; k++) {
-        const int p = mono_p(k), q = mono_q(k);
-        mono[k] = (p == 0 ? 1.f : p == 1 ? fi : p == 2 ? fi * fi : fi * fi * fi) *
-                  (q == 0 ? 1.f : q == 1 ? fj : q == 2 ? fj * fj : fj * fj * fj);
-        if (k < wa.n) {
-            du = fmaf(s_d[0][k], mono[k], du);
-            dv = fmaf(s_d[1][k], mono[k], dv);
+    for (int r = 0; r < kPix; r++) {
+        const int j = jt + kRowStep * r;
+        if (x < out_nx && y0 + j < out_ny && !far) {
+            const PixelPos pp = pixel_pos<T::first>(wa.n, s_i0, s_f0, s_d, (float)i, (float)j, far);
+            umin = min(umin, (int)pp.iu);
+            umax = max(umax, (int)pp.iu + T::n - 1);
+            vmin = min(vmin, (int)pp.iv);
+            vmax = max(vmax, (int)pp.iv + T::n - 1);
+            live_any = true;
         }
     }
-    // far outside (or not finite): every tap is outside
-    const bool far = s_i0[0] == kFar || s_i0[1] == kFar;
-    const float tu = far ? 0.f : s_f0[0] + du, tv = far ? 0.f : s_f0[1] + dv;
-    const float flu = floorf(tu), flv = floorf(tv);
-    const float fu = tu - flu, fv = tv - flv;
-    const long long iu = far ? 0 : (long long)s_i0[0] + (long long)flu + T::first;  // first tap column
-    const long long iv = far ? 0 : (long long)s_i0[1] + (long long)flv + T::first;
-    const bool zero_outside = flags & SFFT_RESAMPLE_ZERO_OUTSIDE;
-    float wx[T::n], wy[T::n];
-    T::weights(fu, wx);
-    T::weights(fv, wy);
-    float sx = 0.f, sy = 0.f, ax = 0.f, ay = 0.f;
-#pragma unroll
-    for (int k = 0; k < T::n; k++) {
-        sx += wx[k];
-        sy += wy[k];
-        ax += fabsf(wx[k]);
-        ay += fabsf(wy[k]);
+    umin = __reduce_min_sync(0xffffffffu, umin);
+    umax = __reduce_max_sync(0xffffffffu, umax);
+    vmin = __reduce_min_sync(0xffffffffu, vmin);
+    vmax = __reduce_max_sync(0xffffffffu, vmax);
+    const bool warp_live = __any_sync(0xffffffffu, live_any);  // every lane votes
+    if ((t & 31) == 0 && warp_live) {
+        atomicMin(&s_bb[0], umin);
+        atomicMax(&s_bb[1], umax);
+        atomicMin(&s_bb[2], vmin);
+        atomicMax(&s_bb[3], vmax);
     }
-    // the tile's tap footprint: staged in shared memory as (value, bad) pairs when it is small
-    if (live && !far) {
-        atomicMin(&s_bb[0], (int)iu);
-        atomicMax(&s_bb[1], (int)iu + T::n - 1);
-        atomicMin(&s_bb[2], (int)iv);
-        atomicMax(&s_bb[3], (int)iv + T::n - 1);
-    }
-    const bool any_far = __syncthreads_or(live && far);
+    __syncthreads();
     const int bu0 = s_bb[0], bv0 = s_bb[2];
-    const int bw = s_bb[1] - bu0 + 1, bh = s_bb[3] - bv0 + 1;
-    const bool staged = !any_far && s_bb[1] >= bu0 && (long long)bw * bh <= kStage;
-    float acc = 0.f, bad = 0.f;
+    const long long bw = (long long)s_bb[1] - bu0 + 1, bh = (long long)s_bb[3] - bv0 + 1;
+    const bool staged = !far && s_bb[1] >= bu0 && bw * bh <= kStage;
+    const bool zero_outside = flags & SFFT_RESAMPLE_ZERO_OUTSIDE;
     if (staged) {
-        for (int e = t; e < bw * bh; e += kThreads) {
-            const int r = bv0 + e / bw, c = bu0 + e % bw;
+        const int w = (int)bw, nst = (int)(bw * bh);
+        for (int e = t; e < nst; e += kThreads) {
+            const int r = bv0 + e / w, c = bu0 + e % w;
             float2 vb = make_float2(0.f, zero_outside ? 0.f : 1.f);
             if (r >= 0 && r < in_ny && c >= 0 && c < in_nx) {
                 const size_t o = (size_t)r * in_pitch + (size_t)c;
@@ -178,39 +197,56 @@ __global__ void __launch_bounds__(kThreads) k_resample(WarpArg wa, int flags, co
             s_stage[e] = vb;
         }
         __syncthreads();
-        if (!live) return;
-        const float2 *row = s_stage + ((int)iv - bv0) * bw + ((int)iu - bu0);
+    }
+    if (x >= out_nx) return;
+#pragma unroll 1
+    for (int r = 0; r < kPix; r++) {
+        const int j = jt + kRowStep * r, y = y0 + j;
+        if (y >= out_ny) break;
+        const PixelPos pp = pixel_pos<T::first>(wa.n, s_i0, s_f0, s_d, (float)i, (float)j, far);
+        float wx[T::n], wy[T::n];
+        T::weights(pp.fu, wx);
+        T::weights(pp.fv, wy);
+        float sx = 0.f, sy = 0.f, ax = 0.f, ay = 0.f;
 #pragma unroll
-        for (int a = 0; a < T::n; a++) {
-            float rv = 0.f, rb = 0.f;
-#pragma unroll
-            for (int b = 0; b < T::n; b++) {
-                const float2 vb = row[b];
-                rv = fmaf(wx[b], vb.x, rv);
-                rb = fmaf(fabsf(wx[b]), vb.y, rb);
-            }
-            acc = fmaf(wy[a], rv, acc);
-            bad = fmaf(fabsf(wy[a]), rb, bad);
-            row += bw;
+        for (int k = 0; k < T::n; k++) {
+            sx += wx[k];
+            sy += wy[k];
+            ax += fabsf(wx[k]);
+            ay += fabsf(wy[k]);
         }
-    } else {
-        if (!live) return;
-        if (far) {
+        float acc = 0.f, bad = 0.f;
+        if (staged) {
+            const float2 *row = s_stage + ((int)pp.iv - bv0) * (int)bw + ((int)pp.iu - bu0);
+#pragma unroll
+            for (int a = 0; a < T::n; a++) {
+                float rv = 0.f, rb = 0.f;
+#pragma unroll
+                for (int b = 0; b < T::n; b++) {
+                    const float2 vb = row[b];
+                    rv = fmaf(wx[b], vb.x, rv);
+                    rb = fmaf(fabsf(wx[b]), vb.y, rb);
+                }
+                acc = fmaf(wy[a], rv, acc);
+                bad = fmaf(fabsf(wy[a]), rb, bad);
+                row += bw;
+            }
+        } else if (far) {
             bad = zero_outside ? 0.f : ax * ay;
         } else {
             for (int a = 0; a < T::n; a++) {
                 if (wy[a] == 0.f) continue;
-                const long long r = iv + a;
-                const bool rin = r >= 0 && r < in_ny;
+                const long long rr = pp.iv + a;
+                const bool rin = rr >= 0 && rr < in_ny;
                 for (int b = 0; b < T::n; b++) {
                     if (wx[b] == 0.f) continue;
                     const float w = wy[a] * wx[b];
-                    const long long c = iu + b;
+                    const long long c = pp.iu + b;
                     if (!rin || c < 0 || c >= in_nx) {
                         if (!zero_outside) bad += fabsf(w);
                         continue;
                     }
-                    const size_t o = (size_t)r * in_pitch + (size_t)c;
+                    const size_t o = (size_t)rr * in_pitch + (size_t)c;
                     if (in_mask && __ldg(in_mask + o)) {
                         bad += fabsf(w);
                         continue;
@@ -219,30 +255,28 @@ __global__ void __launch_bounds__(kThreads) k_resample(WarpArg wa, int flags, co
                 }
             }
         }
-    }
-    float val = acc / (sx * sy);
-    if (flags & SFFT_RESAMPLE_FLUX) {
-        float j00 = 0.f, j01 = 0.f, j10 = 0.f, j11 = 0.f;
+        float val = acc / (sx * sy);
+        if (flags & SFFT_RESAMPLE_FLUX) {
+            const float fi = (float)i, fj = (float)j;
+            float j00 = 0.f, j01 = 0.f, j10 = 0.f, j11 = 0.f;
 #pragma unroll
-        for (int k = 1; k < 10; k++) {
-            if (k >= wa.n) break;
-            int p, q;
-            mono_pq(k, p, q);
-            // d/di and d/dj of i^p j^q
-            const float ddi = p == 0 ? 0.f : (float)p * (p == 1 ? 1.f : p == 2 ? fi : fi * fi) *
-                                                 (q == 0 ? 1.f : q == 1 ? fj : q == 2 ? fj * fj : fj * fj * fj);
-            const float ddj = q == 0 ? 0.f : (float)q * (q == 1 ? 1.f : q == 2 ? fj : fj * fj) *
-                                                 (p == 0 ? 1.f : p == 1 ? fi : p == 2 ? fi * fi : fi * fi * fi);
-            j00 = fmaf(s_d[0][k], ddi, j00);
-            j01 = fmaf(s_d[0][k], ddj, j01);
-            j10 = fmaf(s_d[1][k], ddi, j10);
-            j11 = fmaf(s_d[1][k], ddj, j11);
+            for (int k = 1; k < 10; k++) {
+                if (k >= wa.n) break;
+                const int p = mono_p(k), q = mono_q(k);
+                // d/di and d/dj of i^p j^q
+                const float ddi = p == 0 ? 0.f : (float)p * powi3(fi, p - 1) * powi3(fj, q);
+                const float ddj = q == 0 ? 0.f : (float)q * powi3(fi, p) * powi3(fj, q - 1);
+                j00 = fmaf(s_d[0][k], ddi, j00);
+                j01 = fmaf(s_d[0][k], ddj, j01);
+                j10 = fmaf(s_d[1][k], ddi, j10);
+                j11 = fmaf(s_d[1][k], ddj, j11);
+            }
+            val *= fabsf(j00 * j11 - j01 * j10);
         }
-        val *= fabsf(j00 * j11 - j01 * j10);
+        const size_t oo = (size_t)y * out_pitch + x;
+        out[oo] = (In)val;
+        if (out_mask) out_mask[oo] = bad > 0.01f * (ax * ay) ? 1 : 0;
     }
-    const size_t oo = (size_t)y * out_pitch + x;
-    out[oo] = (In)val;
-    if (out_mask) out_mask[oo] = bad > 0.01f * (ax * ay) ? 1 : 0;
 }
 
 template <class In>
@@ -250,13 +284,20 @@ cudaError_t launch(int method, const WarpArg &wa, int flags, const void *in, con
                    int in_nx, int in_pitch, void *out, uint8_t *out_mask, int out_ny, int out_nx, int out_pitch,
                    cudaStream_t st) {
     dim3 grid((out_nx + kTile - 1) / kTile, (out_ny + kTile - 1) / kTile);
+    WarpArg w = wa;
+    w.xrf = (float)wa.xr;
+    w.yrf = (float)wa.yr;
+    for (int k = 0; k < 10; k++) {
+        w.cuf[k] = (float)wa.cu[k];
+        w.cvf[k] = (float)wa.cv[k];
+    }
     note_launch();
     if (method == SFFT_LANCZOS3)
         k_resample<In, SFFT_LANCZOS3><<<grid, kThreads, 0, st>>>(
-            wa, flags, (const In *)in, in_mask, in_ny, in_nx, in_pitch, (In *)out, out_mask, out_ny, out_nx, out_pitch);
+            w, flags, (const In *)in, in_mask, in_ny, in_nx, in_pitch, (In *)out, out_mask, out_ny, out_nx, out_pitch);
     else
         k_resample<In, SFFT_BILINEAR><<<grid, kThreads, 0, st>>>(
-            wa, flags, (const In *)in, in_mask, in_ny, in_nx, in_pitch, (In *)out, out_mask, out_ny, out_nx, out_pitch);
+            w, flags, (const In *)in, in_mask, in_ny, in_nx, in_pitch, (In *)out, out_mask, out_ny, out_nx, out_pitch);
     return cudaGetLastError();
 }
 

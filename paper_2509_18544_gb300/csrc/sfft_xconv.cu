@@ -11,6 +11,7 @@
 // owns 8 consecutive columns of 4 rows, keeps one stamp row and one input-row window
 // (8 + 2r values, 16-byte loads) in registers and does 8 K FMAs per window.  K^2 FMAs per
 // pixel (625 for K = 25): the kernel is bound by the FP32 pipe, not by HBM.
+// Stamps of 9 x 9 and larger take the row-segment FFT route of sfft_xconv_fft.cu instead.
 #include <stdio.h>
 
 #include "sfft_internal.cuh"
@@ -137,6 +138,8 @@ cudaError_t run_in(int r, const XJob &a, const XJob &b, int njobs, int ny, int n
 }  // namespace
 
 void set_global_error(const char *msg);
+cudaError_t launch_xconv_fft(int r, int dtype, const void *src0, const float *psf0, void *dst0, const void *src1,
+                             const float *psf1, void *dst1, int njobs, int ny, int nx, int pitch, cudaStream_t st);
 
 }  // namespace sfft
 
@@ -170,7 +173,11 @@ extern "C" sfft_status sfft_cross_convolve(int32_t ny, int32_t nx, int32_t pitch
     const int njobs = do_s && do_t ? 2 : 1;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     const int r = (K - 1) / 2;
-    cudaError_t e = dtype == SFFT_F64 ? run_in<double>(r, a, b, njobs, ny, nx, pitch, st)
+    // stamps of 9 x 9 and up: the row-segment FFT route (~10x fewer instructions at K = 25);
+    // smaller stamps: the direct sum
+    cudaError_t e = r >= 4 ? launch_xconv_fft(r, dtype, a.src, a.psf, a.dst, b.src, b.psf, b.dst, njobs, ny, nx,
+                                              pitch, st)
+                  : dtype == SFFT_F64 ? run_in<double>(r, a, b, njobs, ny, nx, pitch, st)
                                       : run_in<float>(r, a, b, njobs, ny, nx, pitch, st);
     if (e != cudaSuccess) {
         char buf[256];
