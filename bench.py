@@ -451,8 +451,8 @@ def pipeline_steps(args, dev, stream, dev_pairs, seeds, coeffs, diffs, NY, NX, f
     step 7 (decorrelation kernel at the frame centre, applied to D and to the cross-convolved
     science image) and steps 8-9 (forced photometry of 500 field stars and the transient per
     pair, constant background).  Roofline per step: the own-traffic HBM fraction (each
-    input read once, each output written once) for the resampler, the FP32 fraction
-    (K^2 FMAs per output pixel) for the two convolutions."""
+    input read once, each output written once) for the resampler, the FP32 fraction of the
+    row-segment FFT route's flops for the two convolutions."""
     import math
 
     import numpy as np
@@ -518,7 +518,15 @@ def pipeline_steps(args, dev, stream, dev_pairs, seeds, coeffs, diffs, NY, NX, f
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     fp32 = sms * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6
     px = float(NY * NX)
-    conv_flops = 2 * 2.0 * K * K * px  # two images, K^2 FMAs each per pixel
+    # the convolutions run on the row-segment FFT route (K >= 9): per 256-column segment and
+    # image, a 256-point complex FFT (5 N log2 N flops) per two input rows (32 + K - 1 rows per
+    # 32 output rows), K complex multiply-adds (8 flops) per output row and half-spectrum bin
+    # (128 per U = 257 - K columns), and one inverse FFT per two output rows
+    def fft_conv_flops(k):
+        u, fft = 257 - k, 5.0 * 256 * 8
+        per_px = (fft / 2 * (32 + k - 1) / 32 + 8.0 * k * 128 + fft / 2) / u
+        return 2 * per_px * px  # two images
+    conv_flops = fft_conv_flops(K)
     total = sum(ms.values()) + fit_ms_per_pair
     bad = int((res[:, 5] != 0).sum().item())
     return {
@@ -528,10 +536,13 @@ def pipeline_steps(args, dev, stream, dev_pairs, seeds, coeffs, diffs, NY, NX, f
         "roofline": {
             "align_resample": {"bound": "hbm", "own_bytes": round(10.0 * px),
                                "frac": round(10.0 * px / (ms["align_resample"] * 1e-3) / 1e9 / hbm, 4)},
-            "cross_convolve": {"bound": "alu", "flops": conv_flops,
-                               "frac": round(conv_flops / (ms["cross_convolve"] * 1e-3) / fp32, 4)},
-            "decorrelation_apply": {"bound": "alu", "flops": 2 * 2.0 * M * M * px,
-                                    "frac": round(2 * 2.0 * M * M * px / (ms["decorrelation_apply"] * 1e-3) / fp32, 4)},
+            "cross_convolve": {"bound": "alu", "route": "row-segment FFT", "flops": conv_flops,
+                               "frac": round(conv_flops / (ms["cross_convolve"] * 1e-3) / fp32, 4),
+                               "direct_equivalent_flops": 2 * 2.0 * K * K * px,
+                               "hbm_own_frac": round(16.0 * px / (ms["cross_convolve"] * 1e-3) / 1e9 / hbm, 4)},
+            "decorrelation_apply": {"bound": "alu", "flops": fft_conv_flops(M),
+                                    "frac": round(fft_conv_flops(M) / (ms["decorrelation_apply"] * 1e-3) / fp32, 4),
+                                    "direct_equivalent_flops": 2 * 2.0 * M * M * px},
         },
         "photometry_jobs_per_pair": 501, "photometry_unsolved": bad,
         "config": "steps 4, 5, 7, 8-9 on the benchmark's pairs: rotation 0.3 deg + 1e-4 scale + cubic "

@@ -235,7 +235,8 @@ typedef struct {
                                  image's spectrum; ycorr_bins, ycorr_split, ycorr_scalar apply) */
     int32_t ycorr_sets;       /* y-block FFT route, DK, DB <= 2: producer warp sets transforming
                                  row blocks concurrently, 1 or 2 (0 = the default, 2) */
-    int32_t reserved[1];
+    int32_t subtract_fft;     /* FP32 paths, DK <= 2, 3 <= L <= 15, DB <= 4: 1 = difference image by
+                                 256-point row-segment FFTs, 0 = the direct kernel (default) */
 } sfft_tuning;
 /* The cached entry for desc (zeros and *cached = 0 when there is none). */
 sfft_status sfft_tuning_get(const sfft_desc *desc, sfft_tuning *t, int32_t *cached);

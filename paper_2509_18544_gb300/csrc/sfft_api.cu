@@ -151,6 +151,7 @@ bool make_geometry(const sfft_desc &d, Geometry &g, char *err, size_t errlen) {
     }
     default_y2split(g);
     g.ysets = 2;
+    g.subfft = 0;
     finish_geometry(g);
     return true;
 }
@@ -256,6 +257,7 @@ static size_t carve(const Geometry &g, int precision, int dtype, void *base, Wor
     o.flags = c.take<int>(base, 16);
     o.dinvf = c.take<float>(base, (size_t)g.n);
     o.cfold = c.take<char>(base, (size_t)g.ny * g.L * (g.dk + 1) * g.L * (cpx_sz / 2) + (size_t)g.ny * (g.db + 1) * (cpx_sz / 2));
+    o.kspec = c.take<float2>(base, (size_t)g.nk * g.L * 128);
     o.status = c.take<int>(base, 16);
     o.bar = c.take<unsigned>(base, 16);
     o.tw_fft = c.take<char>(base, (size_t)2 * g.P * cpx_sz);
@@ -702,8 +704,15 @@ sfft_status sfft_subtract(sfft_plan_t plan, const void *sci, const void *tmpl, c
     cudaError_t e;
     {
         StageTimer t(plan, ST_SUBTRACT);
-        e = launch_subtract(plan->g, plan->desc.dtype, plan->desc.precision, sci, tmpl, nullptr, false, coeffs,
-                            plan->ws.xpow, plan->ws.ypow, plan->ws.cfold, diff, nullptr, nullptr, plan->stream);
+        // FP32 paths with subtract_fft tuned on: the row-segment FFT route where it has kernels
+        // (DK <= 2, 3 <= L <= 15, DB <= 4); otherwise the direct kernel
+        e = plan->desc.precision == SFFT_PREC_FP64 || !plan->g.subfft
+                ? cudaErrorNotSupported
+                : launch_subtract_fft(plan->g, plan->desc.dtype, sci, tmpl, coeffs, plan->ws.tw_fft, plan->ws.xpow,
+                                      plan->ws.ypow, plan->ws.kspec, diff, plan->stream);
+        if (e == cudaErrorNotSupported)
+            e = launch_subtract(plan->g, plan->desc.dtype, plan->desc.precision, sci, tmpl, nullptr, false, coeffs,
+                                plan->ws.xpow, plan->ws.ypow, plan->ws.cfold, diff, nullptr, nullptr, plan->stream);
     }
     if (e != cudaSuccess) return cuda_fail(plan, e, "subtract launch");
     return SFFT_OK;

@@ -79,6 +79,8 @@ bool apply_tuning(const sfft_tuning &t, Geometry &g, char *err, size_t errlen) {
     if (t.subtract_ctas < 0 || t.subtract_ctas > 4)
         return snprintf(err, errlen, "subtract_ctas %d outside [0, 4]", t.subtract_ctas), false;
     g.sub_per_sm = t.subtract_ctas > 0 ? t.subtract_ctas : 2;
+    if (t.subtract_fft != 0 && t.subtract_fft != 1) return snprintf(err, errlen, "subtract_fft must be 0 or 1"), false;
+    g.subfft = t.subtract_fft;
     if (t.pcg_cluster != 0 && t.pcg_cluster != 8 && t.pcg_cluster != 16)
         return snprintf(err, errlen, "pcg_cluster must be 0, 8 or 16"), false;
     g.pcg_cluster = t.pcg_cluster;
@@ -306,14 +308,14 @@ sfft_status sfft_tuning_save(const char *path) {
     if (!f) return errf("sfft_tuning_save: cannot open %s", path), SFFT_ERR_INVALID_ARG;
     std::lock_guard<std::mutex> lk(g_tune_mu);
     fprintf(f, "# ny nx pitch L dk db dtype precision solver refine : ycorr_bins ycorr_split ycorr_scalar subtract_ctas "
-               "pcg_cluster ycorr_direct ycorr_sets\n");
+               "pcg_cluster ycorr_direct ycorr_sets subtract_fft\n");
     for (auto &kv : g_tune) {
         const Key &k = kv.first;
         const sfft_tuning &t = kv.second;
-        fprintf(f, "%d %d %d %d %d %d %d %d %d %d : %d %d %d %d %d %d %d\n", std::get<0>(k), std::get<1>(k),
+        fprintf(f, "%d %d %d %d %d %d %d %d %d %d : %d %d %d %d %d %d %d %d\n", std::get<0>(k), std::get<1>(k),
                 std::get<2>(k), std::get<3>(k), std::get<4>(k), std::get<5>(k), std::get<6>(k), std::get<7>(k),
                 std::get<8>(k), std::get<9>(k), t.ycorr_bins, t.ycorr_split, t.ycorr_scalar, t.subtract_ctas,
-                t.pcg_cluster, t.ycorr_direct, t.ycorr_sets);
+                t.pcg_cluster, t.ycorr_direct, t.ycorr_sets, t.subtract_fft);
     }
     const bool ok = fclose(f) == 0;
     return ok ? SFFT_OK : (errf("sfft_tuning_save: write failed"), SFFT_ERR_INVALID_ARG);
@@ -333,11 +335,12 @@ sfft_status sfft_tuning_load(const char *path) {
         memset(&d, 0, sizeof d);
         sfft_tuning t;
         memset(&t, 0, sizeof t);
-        int n = sscanf(line, "%d %d %d %d %d %d %d %d %d %d : %d %d %d %d %d %d %d", &d.ny, &d.nx, &d.pitch, &d.L,
+        int n = sscanf(line, "%d %d %d %d %d %d %d %d %d %d : %d %d %d %d %d %d %d %d", &d.ny, &d.nx, &d.pitch, &d.L,
                        &d.dk, &d.db, &d.dtype, &d.precision, &d.solver, &d.refine, &t.ycorr_bins, &t.ycorr_split,
-                       &t.ycorr_scalar, &t.subtract_ctas, &t.pcg_cluster, &t.ycorr_direct, &t.ycorr_sets);
-        if (n != 17) {
-            errf("sfft_tuning_load: %s:%d: expected 17 fields", path, lineno);
+                       &t.ycorr_scalar, &t.subtract_ctas, &t.pcg_cluster, &t.ycorr_direct, &t.ycorr_sets,
+                       &t.subtract_fft);
+        if (n != 18) {
+            errf("sfft_tuning_load: %s:%d: expected 18 fields", path, lineno);
             result = SFFT_ERR_INVALID_ARG;
             break;
         }
@@ -427,6 +430,11 @@ sfft_status sfft_autotune(const sfft_desc *desc, const void *sci, const void *tm
             for (int v : {1, 3, 4}) {
                 sfft_tuning t = cur;
                 t.subtract_ctas = v;
+                cand.push_back(t);
+            }
+            if (desc->precision != SFFT_PREC_FP64 && g0.dk <= 2 && g0.h >= 1 && g0.h <= 7 && g0.db <= 4) {
+                sfft_tuning t = cur;  // the FFT route of the difference image
+                t.subtract_fft = 1;
                 cand.push_back(t);
             }
         }

@@ -103,6 +103,7 @@ struct Geometry {
     int ypg, npg;              // pairs per y-FFT CTA, pair groups
     int y2split, y2split_ws;   // y-FFT CTAs per frequency (main pass, refinement pass)
     int ysets;                 // producer sets of the specialised FP32 y-FFT kernel (1 or 2)
+    int subfft;                // difference image by row-segment FFTs (FP32 paths) instead of the direct kernel
 };
 
 bool make_geometry(const sfft_desc &d, Geometry &g, char *err, size_t errlen);
@@ -137,6 +138,7 @@ struct Workspace {
     float *Lg = nullptr;         // packed FP32 factor tiles of the fast solver
     int *flags = nullptr;        // fast solver: [0] converged, [1] iterations, [2] outcome if not converged
     void *cfold = nullptr;       // subtract: folded kernel coefficients [ny][L][dk+1][L] (R)
+    float2 *kspec = nullptr;     // FFT-route subtract: stamp-row spectra [nk][L][128] complex FP32
     int *status = nullptr;       // device status word(s)
     unsigned *bar = nullptr;     // grid-barrier words of the cooperative solver [count, generation]
     void *tw_fft = nullptr;      // [2][P] complex (R): exp(-2 pi i m / P), high part then remainder
@@ -239,6 +241,11 @@ cudaError_t launch_pcg_cluster(const Geometry &g, const double *N, const double 
                                int *flags, int max_iter, double tol, bool correction, cudaStream_t st);
 // difference image (mask == nullptr), or with a mask the residual of the fit on the
 // masked frames: S_m - sum a (w T_m)(u - d) - m sum b w
+// difference image by row-segment FFTs (FP32 arithmetic); cudaErrorNotSupported where it has
+// no kernel (DK > 2, L < 3 or L > 15), and the caller takes launch_subtract
+cudaError_t launch_subtract_fft(const Geometry &g, int dtype, const void *sci, const void *tmpl, const double *coeffs,
+                                const void *tw_fft, const void *xpow, const void *ypow, float2 *kspec, void *diff,
+                                cudaStream_t st);
 cudaError_t launch_subtract(const Geometry &g, int dtype, int precision, const void *sci,
                             const void *tmpl, const uint8_t *mask, bool residual, const double *coeffs,
                             const void *xpow, const void *ypow, void *cfold, void *diff, double *mom_part, double *mom, cudaStream_t st);

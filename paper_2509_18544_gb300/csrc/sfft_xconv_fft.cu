@@ -18,7 +18,7 @@
 #include <math.h>
 #include <stdio.h>
 
-#include "sfft_fft256.cuh"
+#include "sfft_rowfft.cuh"
 
 namespace sfft {
 
@@ -28,7 +28,6 @@ namespace {
 
 constexpr int kXThreads = 256;  // 16 half-warps: one 256-point FFT each
 constexpr int kXChunk = 32;     // output rows per chunk
-constexpr int kXEx = 16 * 17 + 1;
 
 template <int R>
 struct XF {
@@ -46,50 +45,6 @@ struct XSmem {
     static constexpr size_t spec = ptab + (size_t)XF<R>::K * 128 * sizeof(float2);
     static constexpr size_t bytes = spec + (size_t)XF<R>::NIN * 128 * sizeof(float2);
 };
-
-// After fft256 of z = x1 + i x2 (lane t holds Z[t + 16 k2] in v[k2]), split the two real
-// rows' half spectra into dst1, dst2 (128 slots each, slot 0 = (X(0), X(128)), both real),
-// scaled by `scale`: X1(k) = (Z(k) + conj(Z(256 - k))) / 2, X2(k) = -i (Z(k) - conj(Z(256 - k))) / 2.
-__device__ __forceinline__ void unpack_pair(const cpx<float> (&v)[16], int t, cpx<float> *e, float2 *dst1,
-                                            float2 *dst2, float scale, unsigned msk) {
-#pragma unroll
-    for (int k2 = 0; k2 < 16; k2++) e[t + 16 * k2] = v[k2];
-    __syncwarp(msk);
-    const float h = 0.5f * scale;
-#pragma unroll
-    for (int m = 0; m < 8; m++) {
-        const int k = t + 16 * m;
-        if (k == 0) {
-            const cpx<float> z0 = e[0], zn = e[128];
-            dst1[0] = make_float2(z0.re * scale, zn.re * scale);
-            if (dst2) dst2[0] = make_float2(z0.im * scale, zn.im * scale);
-        } else {
-            const cpx<float> a = e[k], b = e[kP - k];  // B = conj(b)
-            dst1[k] = make_float2((a.re + b.re) * h, (a.im - b.im) * h);
-            if (dst2) dst2[k] = make_float2((a.im + b.im) * h, (b.re - a.re) * h);
-        }
-    }
-    __syncwarp(msk);
-}
-
-// One complex FFT of two real rows (row 2 optional): lane t loads z[t + 16 jj].
-template <class In>
-__device__ __forceinline__ void load_pair(const In *row1, const In *row2, int col0, int nx, int t,
-                                          cpx<float> (&v)[16]) {
-#pragma unroll
-    for (int jj = 0; jj < 16; jj++) {
-        int c = col0 + t + 16 * jj;  // col0 >= -r: c lies in [-r, nx + 255)
-        if (nx >= kP) {
-            c += c < 0 ? nx : 0;
-            c -= c >= nx ? nx : 0;
-        } else {
-            c %= nx;
-            c += c < 0 ? nx : 0;
-        }
-        v[jj].re = (float)row1[c];
-        v[jj].im = row2 ? (float)row2[c] : 0.f;
-    }
-}
 
 // One MAC pass over stamp rows a in [A0, A1): acc[jj] += Phat_a(slot) Zhat_{j0 + jj + 2r - a}(slot)
 // for the thread's 16 output rows.  Complex products as two packed FMAs:
@@ -119,15 +74,6 @@ __device__ __forceinline__ void mac_pass(const float2 *spec, const float2 *ptab,
             }
         }
     }
-}
-
-// the value at bin n of a row's full spectrum from its 128 half-spectrum slots
-__device__ __forceinline__ float2 half_bin(const float2 *Y, int n) {
-    if (n == 0) return make_float2(Y[0].x, 0.f);
-    if (n == kP / 2) return make_float2(Y[0].y, 0.f);
-    if (n < kP / 2) return Y[n];
-    const float2 c = Y[kP - n];
-    return make_float2(c.x, -c.y);
 }
 
 struct XJobF {
@@ -179,15 +125,25 @@ __global__ void __launch_bounds__(kXThreads, 1) k_xconv_fft(XJobF j0, XJobF j1, 
     for (int c = blockIdx.y; c < nchunks; c += gridDim.y) {
         const int y0 = c * kXChunk;
         // 2. the chunk's input rows y0 - r .. y0 + 31 + r, two to a complex FFT
-        for (int pr = hw; 2 * pr < F::NIN; pr += 16) {
+        // (the next pair's rows are loaded while the current one is transformed)
+        constexpr int NPAIR = (F::NIN + 1) / 2;
+        auto load_rows = [&](int pr, cpx<float>(&v)[16]) {
             const int r1 = 2 * pr, r2 = 2 * pr + 1;
             int yy1 = (y0 - R + r1) % ny, yy2 = (y0 - R + r2) % ny;
             yy1 += yy1 < 0 ? ny : 0;
             yy2 += yy2 < 0 ? ny : 0;
-            cpx<float> v[16];
             load_pair<In>(src + (size_t)yy1 * pitch, r2 < F::NIN ? src + (size_t)yy2 * pitch : nullptr, x0 - R, nx, lt,
                           v);
+        };
+        cpx<float> vn[16];
+        if (hw < NPAIR) load_rows(hw, vn);
+        for (int pr = hw; pr < NPAIR; pr += 16) {
+            cpx<float> v[16];
+#pragma unroll
+            for (int jj = 0; jj < 16; jj++) v[jj] = vn[jj];
+            if (pr + 16 < NPAIR) load_rows(pr + 16, vn);
             fft256(v, lt, e, tw, twl, msk);
+            const int r1 = 2 * pr, r2 = r1 + 1;
             unpack_pair(v, lt, e, spec + r1 * 128, r2 < F::NIN ? spec + r2 * 128 : nullptr, 1.f, msk);
         }
         __syncthreads();

@@ -70,7 +70,7 @@ class sfft_tuning(ctypes.Structure):
     _fields_ = [("ycorr_bins", ctypes.c_int32), ("ycorr_split", ctypes.c_int32),
                 ("ycorr_scalar", ctypes.c_int32), ("subtract_ctas", ctypes.c_int32),
                 ("pcg_cluster", ctypes.c_int32), ("ycorr_direct", ctypes.c_int32),
-                ("ycorr_sets", ctypes.c_int32), ("reserved", ctypes.c_int32 * 1)]
+                ("ycorr_sets", ctypes.c_int32), ("subtract_fft", ctypes.c_int32)]
 
 
 class sfft_warp(ctypes.Structure):
