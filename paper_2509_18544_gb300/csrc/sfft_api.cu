@@ -121,7 +121,7 @@ bool make_geometry(const sfft_desc &d, Geometry &g, char *err, size_t errlen) {
     }
     g.refine = d.refine < 0 ? 0 : (d.refine > 0 ? d.refine : (d.precision == SFFT_PREC_SPLIT ? 1 : 0));
     if (d.db > 4) return snprintf(err, errlen, "db=%d > 4 not supported", d.db), false;
-    g.mom_rows = 64;  // at most the moments kernel's 128
+    g.mom_rows = 128;  // at most the moments kernel's 128
     g.mom_ctas = moments_ctas(g);
     g.nmom = npoly(2 * d.db) + npoly(d.db);
     g.pmax = d.dk > 2 * d.db ? d.dk : 2 * d.db;

@@ -72,7 +72,7 @@ struct Taps<SFFT_BILINEAR> {
 // Per-pixel state derived from the tile's Taylor coefficients: the first tap's column and row
 // and the fractional positions (far: the map left the representable range; every tap outside).
 struct PixelPos {
-    long long iu, iv;
+    int iu, iv;  // |corner| < 1e9 and the Taylor part stays small, so 32 bits hold them
     float fu, fv;
 };
 
@@ -94,8 +94,8 @@ __device__ __forceinline__ PixelPos pixel_pos(int n, const int *i0, const float 
     PixelPos r;
     r.fu = tu - flu;
     r.fv = tv - flv;
-    r.iu = far ? 0 : (long long)i0[0] + (long long)flu + FIRST;
-    r.iv = far ? 0 : (long long)i0[1] + (long long)flv + FIRST;
+    r.iu = far ? 0 : i0[0] + (int)flu + FIRST;
+    r.iv = far ? 0 : i0[1] + (int)flv + FIRST;
     return r;
 }
 
