@@ -404,14 +404,29 @@ __device__ __forceinline__ void c2dft4(C2 &a0, C2 &a1, C2 &a2, C2 &a3) {
     a3 = {f2sub(d02.re, d13.im), f2add(d02.im, d13.re)};  // d02 + i d13
 }
 
-// forward 8-point DFT (natural order); W8^1 = tw(16), W8^3 = tw(48), W8^2 = -i
+// x / sqrt(2) with the constant split into its FP32 value and remainder (0x3F3504F3 and
+// 0x324FE77A: 1/sqrt(2) to about 2^-48), so the product is rounded once from (nearly) the
+// exact value
+__device__ __forceinline__ float2 f2rs2(float2 x) {
+    const float h = __int_as_float(0x3F3504F3), l = __int_as_float(0x324FE77A);
+    const float2 ch = make_float2(h, h), cl = make_float2(l, l);
+    return __ffma2_rn(x, ch, __fmul2_rn(x, cl));
+}
+
+// forward 8-point DFT (natural order); W8^1 = (1 - i)/sqrt(2), W8^3 = -(1 + i)/sqrt(2), W8^2 = -i
 __device__ __forceinline__ void c2dft8(C2 (&v)[8], const float4 *tw3) {
+    (void)tw3;
     C2 e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6];
     C2 o0 = v[1], o1 = v[3], o2 = v[5], o3 = v[7];
     c2dft4(e0, e1, e2, e3);
     c2dft4(o0, o1, o2, o3);
-    o1 = c2tw(o1, tw3 + 3 * 16);
-    o3 = c2tw(o3, tw3 + 3 * 48);
+    {
+        // o1 W8 = ((re + im) + i (im - re)) / sqrt(2); o3 W8^3 = ((im - re) - i (re + im)) / sqrt(2)
+        const float2 s1 = f2add(o1.re, o1.im), d1 = f2sub(o1.im, o1.re);
+        const float2 s3 = f2add(o3.re, o3.im), d3 = f2sub(o3.im, o3.re);
+        o1 = {f2rs2(s1), f2rs2(d1)};
+        o3 = {f2rs2(d3), f2rs2(make_float2(-s3.x, -s3.y))};
+    }
     v[0] = c2add(e0, o0);
     v[4] = c2sub(e0, o0);
     v[1] = c2add(e1, o1);
