@@ -121,7 +121,12 @@ bool make_geometry(const sfft_desc &d, Geometry &g, char *err, size_t errlen) {
     }
     g.refine = d.refine < 0 ? 0 : (d.refine > 0 ? d.refine : (d.precision == SFFT_PREC_SPLIT ? 1 : 0));
     if (d.db > 4) return snprintf(err, errlen, "db=%d > 4 not supported", d.db), false;
-    g.mom_rows = 128;  // at most the moments kernel's 128
+    {
+        // moments CTAs of 128 rows when that still gives 1.5 CTAs per SM, else 64 rows (at most
+        // the moments kernel's 128): fewer, fuller CTAs halve the per-CTA FP64 epilogue
+        const long ctas128 = (long)((g.nx + 511) / 512) * ((g.ny + 127) / 128);
+        g.mom_rows = 2 * ctas128 >= 3L * device_sm_count() ? 128 : 64;
+    }
     g.mom_ctas = moments_ctas(g);
     g.nmom = npoly(2 * d.db) + npoly(d.db);
     g.pmax = d.dk > 2 * d.db ? d.dk : 2 * d.db;
