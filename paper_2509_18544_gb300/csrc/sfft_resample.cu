@@ -7,15 +7,15 @@
 // Twenty threads first re-expand the coordinate polynomials about the tile corner
 // (d_{p'q'} = sum_{p >= p', q >= q'} c_pq C(p, p') C(q, q') ax^(p - p') ay^(q - q'),
 // (ax, ay) the corner's offset from the origin): the corner value d_00 in FP64, the other
-// terms in FP32 (they multiply offsets below 16); each pixel then adds its FP32 Taylor part to the
-// fractional part of the corner value, so the integer tap position is exact and the
+// terms in FP32 (they multiply offsets below 32); each pixel then adds its FP32 Taylor part
+// to the fractional part of the corner value, so the integer tap position is exact and the
 // fraction carries an error below 1e-5 pixel.  The tile's tap footprint (exact, from a
 // min/max over its pixels) is staged in shared memory as (value, bad) pairs -- masked and
 // outside pixels as (0, 1), or (0, 0) outside with SFFT_RESAMPLE_ZERO_OUTSIDE -- so the taps
 // are branch-free: sum w v and sum |w| bad.  Footprints above 56 x 56 (a scale change beyond
-// ~1.5x, or a rotation with a scale above ~1.1) take a per-tap path from global memory.  A tap of weight exactly 0 then adds
-// nothing either way, except that a non-finite unmasked pixel poisons its neighbours
-// through 0 x inf: unmasked pixels are taken to be finite.  FP32 weights and sums (FP64
+// ~1.5x, or a rotation with a scale above ~1.1) take a per-tap path from global memory.  A
+// tap of weight exactly 0 then adds nothing either way, except that a non-finite unmasked
+// pixel poisons its neighbours through 0 x inf: unmasked pixels are taken to be finite.  FP32 weights and sums (FP64
 // images are converted on load).
 #include <math.h>
 #include <stdio.h>

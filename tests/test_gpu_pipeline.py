@@ -11,7 +11,7 @@ Tolerances, from the arithmetic:
 * photometry: FP32 model weights (relative error ~1e-7), FP64 sums -> flux and its error
   within 1e-5 relative, background within 1e-5 of (|b| + sigma_f), chi^2 within 1e-4
   relative, pixel counts and status exact.
-Sizes cross several 16 x 16 tiles with ragged edges; the full-size cases (4088^2) compare
+Sizes cross several 32 x 32 tiles with ragged edges; the full-size cases (4088^2) compare
 sampled pixels and jobs."""
 import math
 
