@@ -421,7 +421,9 @@ def run_ours(args, world, rank, local):
         "batch": {"create_s": round(create_s, 2),
                   "tuning": {"ycorr_bins": tuning.ycorr_bins, "ycorr_split": tuning.ycorr_split,
                              "ycorr_scalar": tuning.ycorr_scalar, "subtract_ctas": tuning.subtract_ctas,
-                             "pcg_cluster": tuning.pcg_cluster}},
+                             "pcg_cluster": tuning.pcg_cluster, "ycorr_direct": tuning.ycorr_direct,
+                             "ycorr_sets": tuning.ycorr_sets, "subtract_fft": tuning.subtract_fft,
+                             "note": "0 = the library's default for that field"}},
         "roofline": roofline,
         "hbm_stages": hbm_stages,
         "hbm_whole_path": whole,
