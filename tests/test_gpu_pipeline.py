@@ -310,3 +310,40 @@ def test_forced_photometry_many_stars_full_size():
     assert len(ok) > 45
     _phot_compare([dict(D=D, P=P.astype(np.float64), x=xs[i], y=ys[i]) for i in ok], 31, sfft.PHOT_BACKGROUND,
                   r[ok])
+
+
+def test_edge_cases_of_the_pipeline_steps():
+    """Zero photometry jobs (a no-op), the largest stamps (K = 63) for photometry and PSF
+    alignment against the oracle, and empty frames rejected by the resampler."""
+    res = torch.full((1, 8), -1.0, dtype=torch.float64, device=DEV)
+    sfft.sfft_forced_photometry(None, 0, 25, res)
+    torch.cuda.synchronize()
+    assert float(res[0, 0]) == -1.0
+    K = 63
+    P = moffat_stamp(K, 6.0, 21)
+    rng = np.random.default_rng(22)
+    D = rng.normal(0, 1.0, (150, 170)).astype(np.float32)
+    x, y = 84.3, 70.6
+    X, Y, fx, fy = po.source_pixel(x, y)
+    D[Y - 31:Y + 32, X - 31:X + 32] += 900.0 * po.shifted_psf(P.astype(np.float64), fx, fy).astype(np.float32)
+    tD, tP = dev(D), dev(P)
+    arr = sfft.phot_jobs([dict(image=tD, psf=tP, x=x, y=y)])
+    jd = torch.frombuffer(bytearray(bytes(arr)), dtype=torch.uint8).to(DEV)
+    sfft.sfft_forced_photometry(jd, 1, K, res, sfft.PHOT_BACKGROUND)
+    torch.cuda.synchronize()
+    f, sf, b, chi2, n = po.forced_photometry(D.astype(np.float64), P.astype(np.float64), x, y, None, None, True)
+    r = res.cpu().numpy()[0]
+    assert r[5] == 0 and r[4] == n == K * K
+    assert abs(r[0] - f) <= 1e-5 * abs(f) and abs(r[2] - b) <= 1e-5 * (abs(b) + sf)
+    w = rot_warp(-0.7, 0.95, 0, 0, 0, 0)
+    out = torch.empty((K, K), dtype=torch.float32, device=DEV)
+    sfft.sfft_align_psf(w, 10.0, 20.0, tP, out)
+    torch.cuda.synchronize()
+    ref = po.align_psf(P.astype(np.float64), warp_dict(w), 10.0, 20.0)
+    assert np.abs(out.cpu().numpy() - ref).max() <= 1e-5 * np.abs(ref).max()
+    a = torch.zeros((16, 16), device=DEV)
+    b2 = torch.zeros((16, 16), device=DEV)
+    for shapes in (dict(in_shape=(0, 16)), dict(out_shape=(16, 0))):
+        with pytest.raises(sfft.SfftError) as ei:
+            sfft.sfft_resample(rot_warp(0.1, 1.0, 0, 0, 0, 0), a, b2, **shapes)
+        assert ei.value.status == sfft.ERR_INVALID_ARG
