@@ -26,7 +26,8 @@ int device_sm_count();
 
 namespace {
 
-constexpr int kXThreads = 256;  // 16 half-warps: one 256-point FFT each
+constexpr int kXThreads = 256;  // 16 half-warps; the first kXFft of them run the 256-point FFTs
+constexpr int kXFft = 8;        // FFTs in flight (exchange buffers): two CTAs fit an SM
 constexpr int kXChunk = 32;     // output rows per chunk
 
 template <int R>
@@ -41,7 +42,7 @@ template <int R>
 struct XSmem {
     static constexpr size_t tw = 0;
     static constexpr size_t ex = tw + 2 * kP * sizeof(cpx<float>);
-    static constexpr size_t ptab = ex + 16 * (size_t)kXEx * sizeof(cpx<float>);
+    static constexpr size_t ptab = ex + kXFft * (size_t)kXEx * sizeof(cpx<float>);
     static constexpr size_t spec = ptab + (size_t)XF<R>::K * 128 * sizeof(float2);
     static constexpr size_t bytes = spec + (size_t)XF<R>::NIN * 128 * sizeof(float2);
 };
@@ -83,7 +84,7 @@ struct XJobF {
 };
 
 template <class In, int R>
-__global__ void __launch_bounds__(kXThreads, 1) k_xconv_fft(XJobF j0, XJobF j1, int ny, int nx, int pitch) {
+__global__ void __launch_bounds__(kXThreads, XSmem<R>::bytes <= 113 * 1024 ? 2 : 1) k_xconv_fft(XJobF j0, XJobF j1, int ny, int nx, int pitch) {
     using F = XF<R>;
     using SM = XSmem<R>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -95,7 +96,8 @@ __global__ void __launch_bounds__(kXThreads, 1) k_xconv_fft(XJobF j0, XJobF j1, 
     In *dst = reinterpret_cast<In *>(jb.dst);
     const int x0 = blockIdx.x * F::U, t = threadIdx.x, hw = t >> 4, lt = t & 15;
     const unsigned msk = (hw & 1) ? 0xffff0000u : 0x0000ffffu;
-    cpx<float> *e = reinterpret_cast<cpx<float> *>(smem_raw + SM::ex) + hw * kXEx;
+    const bool fft_lane = hw < kXFft;  // half-warps that run FFTs
+    cpx<float> *e = reinterpret_cast<cpx<float> *>(smem_raw + SM::ex) + (hw % kXFft) * kXEx;
     // split twiddles exp(-2 pi i m / 256) = tw[m] + twl[m]
     for (int m = t; m < kP; m += kXThreads) {
         double sn, cs;
@@ -106,8 +108,8 @@ __global__ void __launch_bounds__(kXThreads, 1) k_xconv_fft(XJobF j0, XJobF j1, 
     }
     __syncthreads();
     // 1. the stamp rows' spectra, with the inverse transform's 1/256
-    if (2 * hw < F::K) {
-        const int a1 = 2 * hw, a2 = 2 * hw + 1;
+    for (int pa = hw; fft_lane && 2 * pa < F::K; pa += kXFft) {
+        const int a1 = 2 * pa, a2 = 2 * pa + 1;
         cpx<float> v[16];
 #pragma unroll
         for (int jj = 0; jj < 16; jj++) {
@@ -136,12 +138,12 @@ __global__ void __launch_bounds__(kXThreads, 1) k_xconv_fft(XJobF j0, XJobF j1, 
                           v);
         };
         cpx<float> vn[16];
-        if (hw < NPAIR) load_rows(hw, vn);
-        for (int pr = hw; pr < NPAIR; pr += 16) {
+        if (fft_lane && hw < NPAIR) load_rows(hw, vn);
+        for (int pr = hw; fft_lane && pr < NPAIR; pr += kXFft) {
             cpx<float> v[16];
 #pragma unroll
             for (int jj = 0; jj < 16; jj++) v[jj] = vn[jj];
-            if (pr + 16 < NPAIR) load_rows(pr + 16, vn);
+            if (pr + kXFft < NPAIR) load_rows(pr + kXFft, vn);
             fft256(v, lt, e, tw, twl, msk);
             const int r1 = 2 * pr, r2 = r1 + 1;
             unpack_pair(v, lt, e, spec + r1 * 128, r2 < F::NIN ? spec + r2 * 128 : nullptr, 1.f, msk);
@@ -157,9 +159,9 @@ __global__ void __launch_bounds__(kXThreads, 1) k_xconv_fft(XJobF j0, XJobF j1, 
 #pragma unroll
         for (int jj = 0; jj < 16; jj++) spec[(jh + jj) * 128 + slot] = acc[jj];
         __syncthreads();
-        // 4. output rows 2 hw, 2 hw + 1: y = conj(FFT(conj(Y1 + i Y2)))
-        {
-            const int o1 = 2 * hw, o2 = o1 + 1;
+        // 4. output rows 2 op, 2 op + 1 for the FFT half-warps' pairs op: y = conj(FFT(conj(Y1 + i Y2)))
+        for (int op = hw; fft_lane && op < kXChunk / 2; op += kXFft) {
+            const int o1 = 2 * op, o2 = o1 + 1;
             const float2 *Y1 = spec + o1 * 128, *Y2 = spec + o2 * 128;
             cpx<float> v[16];
 #pragma unroll
@@ -187,9 +189,10 @@ cudaError_t run_fft_r(const XJobF &a, const XJobF &b, int njobs, int ny, int nx,
     auto kern = k_xconv_fft<In, R>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM::bytes);
     if (e != cudaSuccess) return e;
-    // segments x chunk groups x images: one wave of one CTA per SM, each CTA a run of chunks
+    // segments x chunk groups x images: one wave of two CTAs per SM (one for the largest
+    // stamps, whose tables do not fit twice), each CTA a run of chunks
     const int nseg = (nx + XF<R>::U - 1) / XF<R>::U, nchunks = (ny + kXChunk - 1) / kXChunk;
-    int groups = device_sm_count() / (nseg * njobs);
+    int groups = device_sm_count() * (SM::bytes <= 113 * 1024 ? 2 : 1) / (nseg * njobs);  // CTAs per SM as in the launch bounds
     groups = groups < 1 ? 1 : (groups > nchunks ? nchunks : groups);
     dim3 grid(nseg, groups, njobs);
     note_launch();
