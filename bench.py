@@ -369,6 +369,12 @@ def run_ours(args, world, rank, local):
                            spec_bytes + y2split * 129 * (nk * (nk + 1) // 2 + nk * (nb + 1)) * 128 * 16.0),
         "subtract": hbm_stage("subtract", "a7 (direct route)", 120.0, 12.0 * px),
     }
+    # DRAM bytes measured by ncu on one 2048^2 launch of each stage's kernel (dram__bytes_read.sum
+    # + dram__bytes_write.sum, the profiles/ summaries), scaled by the pixel count; writes still
+    # in L2 when a launch ends are not counted there
+    for key, rd, wr in (("segment_fft", 37.885e6, 130.419e6), ("ycorr", 191.347e6, 94.921e6),
+                        ("subtract", 36.672e6, 0.006e6)):
+        hbm_stages[key]["traffic"] = round((rd + wr) * px / (2048.0 * 2048.0))
     pair_ms = plain_ms / (args.steps * args.pairs)
     whole = {"plain_ms_per_pair": round(pair_ms, 4), "batched_ms_per_pair": round(ms / (args.steps * args.pairs), 4),
              "bytes": round(340.0 * px),
