@@ -163,6 +163,11 @@ uint64_t launch_count();
 cudaError_t launch_mom_reduce(const double *part, int nparts, int nmom, double *mom, cudaStream_t st);
 // largest number of CTAs the FP32 residual kernel can have (sizes its moment partials)
 int residual_ctas_max(const Geometry &g);
+// residual of the fit on the FP32 paths, in compensated arithmetic (folds the coefficients
+// into cfold first); with mom, its background moments go to mom + npoly(2 DB)
+cudaError_t launch_residual_comp(const Geometry &g, int dtype, const void *sci, const void *tmpl,
+                                 const uint8_t *mask, const double *coeffs, const void *xpow, void *cfold,
+                                 void *resid, double *mom_part, double *mom, cudaStream_t st);
 
 enum Stage { ST_SEGFFT = 0, ST_MOMENTS, ST_YCORR, ST_LAGS, ST_ASSEMBLE, ST_SOLVE, ST_SUBTRACT, ST_REFINE, ST_COUNT };
 

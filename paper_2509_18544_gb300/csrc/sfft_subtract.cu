@@ -73,8 +73,7 @@ template <class R> struct Tile {
 // 16-byte vectors, and a 4-word pad after every 32 words puts the 8 lanes of a quarter-warp
 // (starting 8 words apart) on distinct banks.  FP64: one pad word every 4 doubles puts the
 // 16 lanes of a half-warp on distinct bank pairs.
-// (VEC = false: FP32 windows read as scalars, one pad word every 8 floats, for kernels that
-// pack two rows' values into FP32x2 operands.)
+// (VEC = false: FP32 windows read as scalars, one pad word every 8 floats.)
 template <class R, bool VEC = true>
 __host__ __device__ constexpr int skew(int c) {
     return sizeof(R) == 4 ? (VEC ? c + 4 * (c >> 5) : c + (c >> 3)) : c + (c >> 2);
@@ -433,249 +432,6 @@ __global__ void __launch_bounds__(32 * kBand, 2) k_subtract(const In *__restrict
     }
 }
 
-// ---------------------------------------------------------------------------------------
-// Residual of the fit for the FP32 path, R = S_m - sum a (w T_m)(u - d) - m sum b w, in
-// compensated arithmetic.  At a star core |S| is ~100x the residual, so plain FP32 sums
-// leave rounding errors of order u |S| in R; fitted back onto the basis by the refinement
-// step they bound the coefficients near 1e-6.  The terms that carry |S| are those of the
-// constant (x power 0) kernel plane near the kernel centre, where both the kernel and the
-// star's profile peak: for p = 0 and |dx|, |dy| <= kCore every product is split exactly
-// (p + e = c w, e from an FMA) and the running sum is a hi + lo pair updated by an
-// error-free two-sum (Knuth).  The outer lags, whose terms are the product of two wings, and
-// the xh^p planes (p >= 1, the kernel's spatial variation) accumulate in plain FP32 in a
-// separate sum.  R then carries
-// about the rounding of its operands (the folded coefficients and xh^p T_m, each rounded
-// once to FP32).  Each thread holds two output rows (ty, ty + kBand / 2) of a band as the
-// two lanes of packed FP32x2 operations.
-constexpr int kCore = 2;
-constexpr int kMaxDB = 4;               // background degree the fused moments support
-constexpr int kMaxMom = (kMaxDB + 1) * (kMaxDB + 2) / 2;
-
-__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
-
-// s + e = a + b exactly (round-to-nearest adds, no reassociation: the _rn intrinsics are
-// never contracted or reordered by the compiler)
-__device__ __forceinline__ void two_sum2(float2 a, float2 b, float2 &s, float2 &e) {
-    s = __fadd2_rn(a, b);
-    float2 bb = __fadd2_rn(s, neg2(a));
-    e = __fadd2_rn(__fadd2_rn(a, neg2(__fadd2_rn(s, neg2(bb)))), __fadd2_rn(b, neg2(bb)));
-}
-
-
-// With mom_part, the kernel also writes this CTA's part of the residual's background moments
-// sum_u m(u) w_r(u) R(u) (r < nP(DB), in the monomial order): FP32 sums over a thread's
-// pixels of a row, FP64 across rows and warps; mom_part[cta nP(DB) + r].
-template <class In, int LL>
-__global__ void __launch_bounds__(16 * kBand, 2) k_residual_comp(const In *__restrict__ sci,
-                                                                 const In *__restrict__ tmpl,
-                                                                 const uint8_t *__restrict__ mask, Geometry g,
-                                                                 int rows_per_chunk, const float *__restrict__ cfold,
-                                                                 const float *__restrict__ xpow_g,
-                                                                 In *__restrict__ resid, double *__restrict__ mom_part) {
-    using W = Win<float, LL, false>;
-    using Ly = Layout<float, In, LL, false>;
-    constexpr int h = W::h, kRX = Tile<float>::kRX;
-    constexpr int kHalf = kBand / 2;
-    constexpr int kRowBatch = (kBand * W::WC + 16 * kBand - 1) / (16 * kBand);  // a band's new rows in one batch
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int np = g.dk + 1, nx = g.nx, ny = g.ny;
-    float *Tp = reinterpret_cast<float *>(smem_raw);
-    float *cf = reinterpret_cast<float *>(smem_raw + Ly::cf(np));
-    float *xo = reinterpret_cast<float *>(smem_raw + Ly::xo(np));
-    In *ss = reinterpret_cast<In *>(smem_raw + Ly::ss(np, g.db));
-    unsigned char *sk = smem_raw + Ly::sk(np, g.db);
-    float *byp = reinterpret_cast<float *>(smem_raw + Ly::byp(np, g.db));
-    float *xps = reinterpret_cast<float *>(smem_raw + Ly::xps(np, g.db));
-    const int npx = np > g.db + 1 ? np : g.db + 1;
-
-    const int x0 = blockIdx.x * Tile<float>::kCols;
-    const int yc0 = blockIdx.y * rows_per_chunk, yc1 = min(ny, yc0 + rows_per_chunk);
-    const int cta = blockIdx.y * gridDim.x + blockIdx.x;
-    __shared__ double macc[kBand / 2][kMaxMom];  // per warp: moment sums of its rows
-    if (yc0 >= ny) {
-        if (mom_part)
-            for (int j = threadIdx.x; j < g.nb; j += blockDim.x) mom_part[(size_t)cta * g.nb + j] = 0.0;
-        return;
-    }
-    const int ring_origin = yc0 - h;
-    const int ty = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int cx = lane * kRX, wsk = cx + lane;  // wsk = skew(cx), kRX = 8
-    static_assert(kRX == 8, "the window offsets assume 8 pixels per lane");
-    const float yscale = ny > 1 ? 1.f / (float)(ny - 1) : 0.f;
-    for (int e = threadIdx.x; e < (kBand / 2) * kMaxMom; e += blockDim.x) (&macc[0][0])[e] = 0.0;
-
-    fill_xps<float, LL>(g, xpow_g, x0, npx, xps);
-    fill_xo<float, LL, false>(g, xpow_g, x0, xo);
-    __syncthreads();
-    // every global load of a band happens in the staging phase before it: the coefficients
-    // and science values as asynchronous copies that complete while the template rows load
-    async_coeffs<float, LL, true>(g, cfold, yc0, cf, byp);
-    async_sci<float, In, LL, false>(sci, g, x0, yc0, yc1, ss);
-    stage_rows<float, In, LL, false, 8>(tmpl, mask, true, g, xps, x0, yc0 - h, W::RING, ring_origin, Tp, sk);
-    cp_async_wait();
-    for (int yb = yc0; yb < yc1; yb += kBand) {
-        __syncthreads();
-        const int ya = yb + ty, yb2 = ya + kHalf;
-        float2 hi[kRX], lo[kRX], wing[kRX];
-        unsigned good = 0;  // bit 2 r + k: pixel r of row k exists and is not masked
-        const int sla = (ya - ring_origin) % W::RING, slb = (sla + kHalf) % W::RING;
-        const bool in_a = ya < yc1, in_b = yb2 < yc1;
-        const unsigned long long skip[2] = {in_a ? load_flags<kRX>(sk + sla * Ly::kC + cx) : ~0ull,
-                                            in_b ? load_flags<kRX>(sk + slb * Ly::kC + cx) : ~0ull};
-        // start from m (S - bg): S split exactly into hi + lo, the background subtracted by two-sum
-#pragma unroll
-        for (int r = 0; r < kRX; r++) {
-            float sh[2] = {0.f, 0.f}, sl[2] = {0.f, 0.f}, bg[2] = {0.f, 0.f};
-#pragma unroll
-            for (int k = 0; k < 2; k++) {
-                if (x0 + cx + r < nx && !((skip[k] >> (8 * r)) & 0xff)) {
-                    const int row = k ? ty + kHalf : ty;
-                    good |= 1u << (2 * r + k);
-                    split_input<In>(ss[row * Ly::OC + wsk + r], sh[k], sl[k]);
-                    const float *bp = byp + row * (g.db + 1);
-                    float b = 0.f;
-                    for (int p = 0; p <= g.db; p++) b = fmaf(bp[p], xo[p * Ly::OC + wsk + r], b);
-                    bg[k] = b;
-                }
-            }
-            float2 s, e;
-            two_sum2(make_float2(sh[0], sh[1]), make_float2(-bg[0], -bg[1]), s, e);
-            hi[r] = s;
-            lo[r] = __fadd2_rn(e, make_float2(sl[0], sl[1]));
-            wing[r] = make_float2(0.f, 0.f);
-        }
-        for (int dyi = 0; dyi < LL; dyi++) {
-            const int sa = (ya + h - dyi - ring_origin) % W::RING, sb = (sa + kHalf) % W::RING;
-            const bool core_row = dyi >= h - kCore && dyi <= h + kCore;
-            for (int p = 0; p < np; p++) {
-                // skew(cx + m) = wsk + m + m / 8: the window's offsets are immediates
-                const float *ta = Tp + (p * W::RING + sa) * W::WCS + wsk, *tb = Tp + (p * W::RING + sb) * W::WCS + wsk;
-                float2 wp[W::NW];
-#pragma unroll
-                for (int m = 0; m < W::NW; m++) wp[m] = make_float2(ta[m + (m >> 3)], tb[m + (m >> 3)]);
-                float2 cp[W::LLP];  // (row a, row b) coefficient pairs
-                const float4 *cq = reinterpret_cast<const float4 *>(cf + ((ty * LL + dyi) * np + p) * 2 * W::LLP);
-#pragma unroll
-                for (int k = 0; k < W::LLP / 2; k++) {
-                    const float4 v = cq[k];
-                    cp[2 * k] = make_float2(v.x, v.y);
-                    cp[2 * k + 1] = make_float2(v.z, v.w);
-                }
-                if (core_row && p == 0) {
-#pragma unroll
-                    for (int dxi = 0; dxi < LL; dxi++) {
-                        const float2 cc = cp[dxi];
-                        if (dxi >= h - kCore && dxi <= h + kCore) {
-#pragma unroll
-                            for (int r = 0; r < kRX; r++) {
-                                const float2 w = wp[r + (LL - 1) - dxi];
-                                const float2 pr = __fmul2_rn(cc, w);
-                                const float2 pe = __ffma2_rn(cc, w, neg2(pr));  // cc w - pr, exact
-                                float2 s, e;
-                                two_sum2(hi[r], neg2(pr), s, e);
-                                hi[r] = s;
-                                lo[r] = __fadd2_rn(lo[r], __fadd2_rn(e, neg2(pe)));
-                            }
-                        } else {
-#pragma unroll
-                            for (int r = 0; r < kRX; r++) wing[r] = __ffma2_rn(cc, wp[r + (LL - 1) - dxi], wing[r]);
-                        }
-                    }
-                } else {
-#pragma unroll
-                    for (int dxi = 0; dxi < LL; dxi++) {
-                        const float2 cc = cp[dxi];
-#pragma unroll
-                        for (int r = 0; r < kRX; r++) wing[r] = __ffma2_rn(cc, wp[r + (LL - 1) - dxi], wing[r]);
-                    }
-                }
-            }
-        }
-        float ma[kMaxDB + 1], mb[kMaxDB + 1];  // sum over this thread's pixels of m R xh^p, rows a, b
-#pragma unroll
-        for (int p = 0; p <= kMaxDB; p++) ma[p] = mb[p] = 0.f;
-#pragma unroll
-        for (int r = 0; r < kRX; r++) {
-            const int x = x0 + cx + r;
-            if (x >= nx) continue;
-            // R = hi + lo - wing.  FP32 output: (hi - wing) is within a few rounding units of R
-            // (lo is of the order u |hi|), so the two FP32 adds cost about one extra rounding
-            // of R; on this part an FP64 add runs at 1/64 of the FP32 rate.
-            float fa, fb;
-            if constexpr (std::is_same<In, float>::value) {
-                const float2 t = __fadd2_rn(__fadd2_rn(hi[r], neg2(wing[r])), lo[r]);
-                fa = t.x;
-                fb = t.y;
-                if (ya < yc1) resid[(size_t)ya * g.pitch + x] = fa;
-                if (yb2 < yc1) resid[(size_t)yb2 * g.pitch + x] = fb;
-            } else {
-                const double ra = (double)hi[r].x + ((double)lo[r].x - (double)wing[r].x);
-                const double rb = (double)hi[r].y + ((double)lo[r].y - (double)wing[r].y);
-                if (ya < yc1) resid[(size_t)ya * g.pitch + x] = (In)ra;
-                if (yb2 < yc1) resid[(size_t)yb2 * g.pitch + x] = (In)rb;
-                fa = (float)ra;
-                fb = (float)rb;
-            }
-            if (mom_part) {
-                fa = (good >> (2 * r)) & 1u ? fa : 0.f;
-                fb = (good >> (2 * r + 1)) & 1u ? fb : 0.f;
-#pragma unroll
-                for (int p = 0; p <= kMaxDB; p++) {
-                    if (p > g.db) break;
-                    const float xv = xo[p * Ly::OC + wsk + r];
-                    ma[p] = fmaf(fa, xv, ma[p]);
-                    mb[p] = fmaf(fb, xv, mb[p]);
-                }
-            }
-        }
-        if (mom_part) {
-#pragma unroll
-            for (int p = 0; p <= kMaxDB; p++) {
-                if (p > g.db) break;
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) {
-                    ma[p] += __shfl_xor_sync(0xffffffffu, ma[p], o);
-                    mb[p] += __shfl_xor_sync(0xffffffffu, mb[p], o);
-                }
-            }
-            // lane j < nP(DB) adds moment j of the two rows (FP32 weights yh^q) to its FP64 sum
-            if (lane < g.nb) {
-                const float yha = ny > 1 ? (float)(2 * ya - (ny - 1)) * yscale : 0.f;
-                const float yhb = ny > 1 ? (float)(2 * yb2 - (ny - 1)) * yscale : 0.f;
-                int pr, qs;
-                mono_pq(lane, pr, qs);
-                float wa = 1.f, wb = 1.f;
-                for (int q = 0; q < qs; q++) wa *= yha, wb *= yhb;
-                float va = 0.f, vb = 0.f;
-#pragma unroll
-                for (int p = 0; p <= kMaxDB; p++)
-                    if (p == pr) va = ma[p], vb = mb[p];
-                macc[ty][lane] += (double)fmaf(wa, va, wb * vb);
-            }
-        }
-        __syncthreads();
-        if (yb + kBand < yc1) {
-            async_coeffs<float, LL, true>(g, cfold, yb + kBand, cf, byp);
-            async_sci<float, In, LL, false>(sci, g, x0, yb + kBand, yc1, ss);
-            stage_rows<float, In, LL, false, kRowBatch>(tmpl, mask, true, g, xps, x0, yb + kBand + h, kBand,
-                                                        ring_origin, Tp, sk);
-            cp_async_wait();
-        }
-    }
-    if (mom_part) {
-        __syncthreads();
-        for (int j = threadIdx.x; j < g.nb; j += blockDim.x) {
-            double v = 0.0;
-            for (int w = 0; w < kBand / 2; w++) v += macc[w][j];
-            mom_part[(size_t)cta * g.nb + j] = v;
-        }
-    }
-}
-
-int residual_ctas_max_impl(const Geometry &g) {
-    return ((g.nx + Tile<float>::kCols - 1) / Tile<float>::kCols) * ((g.ny + kBand - 1) / kBand);
-}
-
 int sm_count() {
     static int sms = 0;
     if (!sms) {
@@ -707,27 +463,6 @@ cudaError_t run(const Geometry &g, const void *sci, const void *tmpl, const uint
     const int np = g.dk + 1;
     const size_t sm = Layout<R, In, LL>::bytes(np, g.db);
     const int strips = (g.nx + Tile<R>::kCols - 1) / Tile<R>::kCols;
-    if constexpr (std::is_same<R, float>::value) {
-        if (residual) {
-            auto kc = k_residual_comp<In, LL>;
-            const size_t smc = Layout<float, In, LL, false>::bytes(np, g.db);
-            cudaError_t e = cudaFuncSetAttribute(kc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smc);
-            if (e == cudaSuccess)
-                e = cudaFuncSetAttribute(kc, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                         cudaSharedmemCarveoutMaxShared);
-            if (e != cudaSuccess) return e;
-            const int rpc = rows_per_chunk(g, strips, g.sub_per_sm > 0 ? g.sub_per_sm : 2);
-            dim3 grid(strips, (g.ny + rpc - 1) / rpc);
-            note_launch();
-            kc<<<grid, 16 * kBand, smc, st>>>((const In *)sci, (const In *)tmpl, mask, g, rpc, (const float *)cfold,
-                                              (const float *)xpow, (In *)diff, mom ? mom_part : nullptr);
-            e = cudaGetLastError();
-            // the residual's background moments go after the npoly(2 DB) mask moments
-            if (e == cudaSuccess && mom)
-                e = launch_mom_reduce(mom_part, (int)(grid.x * grid.y), g.nb, mom + npoly(2 * g.db), st);
-            return e;
-        }
-    }
     auto kern = k_subtract<R, In, LL>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e == cudaSuccess)
@@ -760,14 +495,15 @@ cudaError_t dispatch_L(const Geometry &g, const void *sci, const void *tmpl, con
 
 }  // namespace
 
-int residual_ctas_max(const Geometry &g) { return residual_ctas_max_impl(g); }
-
 cudaError_t launch_subtract(const Geometry &g, int dtype, int precision, const void *sci, const void *tmpl,
                             const uint8_t *mask, bool residual, const double *coeffs, const void *xpow,
                             const void *ypow, void *cfold, void *diff, double *mom_part, double *mom,
                             cudaStream_t st) {
     (void)ypow;
     if (g.dk > 7 || g.db > 7) return cudaErrorInvalidValue;
+    // the FP32 paths' residual: compensated kernel of sfft_residual.cu
+    if (residual && precision != SFFT_PREC_FP64)
+        return launch_residual_comp(g, dtype, sci, tmpl, mask, coeffs, xpow, cfold, diff, mom_part, mom, st);
     if (precision == SFFT_PREC_FP64)
         return dtype == SFFT_F64 ? dispatch_L<double, double>(g, sci, tmpl, mask, residual, coeffs, xpow, cfold, diff, mom_part, mom, st)
                                  : dispatch_L<double, float>(g, sci, tmpl, mask, residual, coeffs, xpow, cfold, diff, mom_part, mom, st);
