@@ -264,7 +264,7 @@ __global__ void __launch_bounds__(kThreadsR, NPM <= 4 ? 4 : 2)
     float2 *ss = reinterpret_cast<float2 *>(smem_raw + Ly::ss(db));
     unsigned char *sk = smem_raw + Ly::sk(db);
     float *byp = reinterpret_cast<float *>(smem_raw + Ly::byp(db));
-    __shared__ double macc[kHalfR][kMaxMomR];  // per warp: moment sums of its rows
+    __shared__ double macc[kHalfR][kMaxMomR];  // per warp: moment sums of its rows (written at the end)
 
     const int x0 = blockIdx.x * kColsR;
     const int yc0 = blockIdx.y * rows_per_chunk, yc1 = min(ny, yc0 + rows_per_chunk);
@@ -277,7 +277,12 @@ __global__ void __launch_bounds__(kThreadsR, NPM <= 4 ? 4 : 2)
     const int ring_origin = yc0 - h;
     const int ty = threadIdx.x >> 5, lane = threadIdx.x & 31, cx = lane * kRR;
     const float yscale = ny > 1 ? 1.f / (float)(ny - 1) : 0.f;
-    for (int e = threadIdx.x; e < kHalfR * kMaxMomR; e += blockDim.x) (&macc[0][0])[e] = 0.0;
+    // lane j < nP(DB) of each warp sums moment j of the warp's rows as an FP32 hi + lo pair
+    // (two-sum), converted to FP64 once at the end: the band loop runs no FP64 instruction
+    int mpr = 0, mqs = 0;
+    if (lane < g.nb) mono_pq(lane, mpr, mqs);
+    float mh = 0.f, ml = 0.f;
+    float zya = (float)(2 * (yc0 + ty) - (ny - 1));  // 2 ya - (ny - 1) of the band's first row, exact
     for (int e = threadIdx.x; e < (db + 1) * kColsR; e += blockDim.x) {
         const int p = e / kColsR, c = e - p * kColsR;
         xo[e] = xpow_g[(size_t)p * nx + min(x0 + c, nx - 1)];
@@ -440,21 +445,22 @@ __global__ void __launch_bounds__(kThreadsR, NPM <= 4 ? 4 : 2)
                     mb[p] += __shfl_xor_sync(0xffffffffu, mb[p], o);
                 }
             }
-            // lane j < nP(DB) adds moment j of the two rows (FP32 weights yh^q) to its FP64 sum
+            // lane j < nP(DB) adds moment j of the two rows (FP32 weights yh^q) to its sum
             if (lane < g.nb) {
-                const float yha = ny > 1 ? (float)(2 * ya - (ny - 1)) * yscale : 0.f;
-                const float yhb = ny > 1 ? (float)(2 * yb2 - (ny - 1)) * yscale : 0.f;
-                int pr, qs;
-                mono_pq(lane, pr, qs);
+                const float yha = zya * yscale, yhb = (zya + (float)(2 * kHalfR)) * yscale;
                 float wa = 1.f, wb = 1.f;
-                for (int q = 0; q < qs; q++) wa *= yha, wb *= yhb;
+                for (int q = 0; q < mqs; q++) wa *= yha, wb *= yhb;
                 float va = 0.f, vb = 0.f;
 #pragma unroll
                 for (int p = 0; p <= kMaxDBR; p++)
-                    if (p == pr) va = ma[p], vb = mb[p];
-                macc[ty][lane] += (double)fmaf(wa, va, wb * vb);
+                    if (p == mpr) va = ma[p], vb = mb[p];
+                const float v = fmaf(wa, va, wb * vb);
+                const float sm = __fadd_rn(mh, v), bb = __fadd_rn(sm, -mh);
+                ml = __fadd_rn(ml, __fadd_rn(__fadd_rn(mh, -__fadd_rn(sm, -bb)), __fadd_rn(v, -bb)));
+                mh = sm;
             }
         }
+        zya += (float)(2 * kBandR);
         __syncthreads();
         // the next band reads source rows up to yb + 2 kBand + h - 1; the kBand new ones
         // replace rows yb - h .. yb - h + kBand - 1, which no later band reads
@@ -468,6 +474,7 @@ __global__ void __launch_bounds__(kThreadsR, NPM <= 4 ? 4 : 2)
         }
     }
     if (mom_part) {
+        if (lane < g.nb) macc[ty][lane] = (double)mh + (double)ml;
         __syncthreads();
         for (int j = threadIdx.x; j < g.nb; j += blockDim.x) {
             double v = 0.0;
