@@ -15,11 +15,12 @@
 //
 // Compensation.  At a star core |S| is ~100x the residual, so plain FP32 sums would leave
 // rounding errors of order u |S| in R; fitted back onto the basis by the refinement they
-// bound the coefficients near 1e-6.  The terms that carry |S| are those of the X^0 sum near
-// the kernel centre (|dx|, |dy| <= kCoreR), where the kernel and the star's profile peak:
-// each of their products is split exactly (p + e = c w, e from an FMA) and the running sum
-// is a hi + lo pair updated by an error-free two-sum (Knuth).  The other lags of the X^0
-// sum and the X^k sums (k >= 1, the kernel's spatial variation) accumulate in plain FP32.
+// bound the coefficients near 1e-6.  The terms that carry |S| are the weights' constant
+// parts ct_0 near the kernel centre (|dx|, |dy| <= kCoreR), where the kernel and the star's
+// profile peak: each of their products is split exactly (p + e = c w, e from an FMA) and the
+// running sum is a hi + lo pair updated by an error-free two-sum (Knuth).  The other lags
+// and the weights' coordinate parts (the kernel's spatial variation) accumulate in plain
+// FP32.
 //
 // Work split: a CTA of 4 warps owns a strip of 128 output columns and a chunk of rows,
 // walked in bands of 8 rows; a thread holds 4 consecutive pixels of two rows (ty and
@@ -40,7 +41,7 @@ constexpr int kHalfR = kBandR / 2;     // a thread's second row is kHalfR below 
 constexpr int kThreadsR = 16 * kBandR;  // 4 warps, two rows each
 constexpr int kRR = 4;                 // consecutive pixels per lane
 constexpr int kColsR = 32 * kRR;       // strip width
-constexpr int kCoreR = 2;              // compensated lags of the X^0 sum: |dx|, |dy| <= kCoreR
+constexpr int kCoreR = 2;              // compensated lags of ct_0: |dx|, |dy| <= kCoreR
 constexpr int kMaxDBR = 4;             // background degree the fused moments support
 constexpr int kMaxMomR = (kMaxDBR + 1) * (kMaxDBR + 2) / 2;
 
@@ -101,40 +102,48 @@ __device__ __forceinline__ void two_sum2(float2 a, float2 b, float2 &s, float2 &
 // The coefficient table, FP64 sums rounded once:
 //   ct[ys][dy][p][dx] = c_p(d, ys) / (nx - 1)^p,  c_p(d, ys) = sum_{i: p_i = p} a_{i,d} yh(ys)^q_i
 // (ct_p = 0 for p >= 1 when nx = 1, where xh = 0), then the background table
-// bg[y][p] = sum_{r: p_r = p} b_r yh(y)^q_r (as for the difference image).
-__global__ void k_fold_x(const double *__restrict__ coeffs, Geometry g, float *__restrict__ cf) {
+// bg[y][p] = sum_{r: p_r = p} b_r yh(y)^q_r (as for the difference image).  iny = 1 / (ny - 1)
+// and sx = 1 / (nx - 1) (0 for a single row or column) come from the host: no FP64 division
+// per thread; the monomial loops are unrolled over degree <= 7 so the sums stay in registers.
+__global__ void k_fold_x(const double *__restrict__ coeffs, Geometry g, double iny, double sx,
+                         float *__restrict__ cf) {
     const int L2 = g.L * g.L, np = g.dk + 1, nbp = g.db + 1;
     const size_t ncf = (size_t)g.ny * L2;
     const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t < ncf) {
-        const int ys = (int)(t / L2), l = (int)(t - (size_t)ys * L2);
-        const double yh = g.ny > 1 ? (2.0 * ys - (g.ny - 1)) / (double)(g.ny - 1) : 0.0;
-        double c[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-        for (int i = 0; i < g.nk; i++) {
-            int pi, qi;
-            mono_pq(i, pi, qi);
-            double w = 1.0;
-            for (int q = 0; q < qi; q++) w *= yh;
-            c[pi] = fma(coeffs[(size_t)i * L2 + l], w, c[pi]);
+    if (t >= ncf + (size_t)g.ny) return;
+    const bool bgrow = t >= ncf;
+    const int ys = bgrow ? (int)(t - ncf) : (int)(t / L2), l = bgrow ? 0 : (int)(t - (size_t)ys * L2);
+    const double yh = (2.0 * ys - (g.ny - 1)) * iny;
+    double pw[8], c[8];
+    pw[0] = 1.0;
+#pragma unroll
+    const int deg = bgrow ? g.db : g.dk;
+#pragma unroll
+    for (int q = 1; q < 8; q++) pw[q] = q <= deg ? pw[q - 1] * yh : 0.0;
+#pragma unroll
+    for (int p = 0; p < 8; p++) c[p] = 0.0;
+    int i = 0;  // monomial index: total degree first, then q ascending
+#pragma unroll
+    for (int d = 0; d < 8; d++) {
+        if (d > deg) break;
+#pragma unroll
+        for (int q = 0; q <= d; q++, i++) {
+            const double a = bgrow ? coeffs[g.nker + i] : coeffs[(size_t)i * L2 + l];
+            c[d - q] = fma(a, pw[q], c[d - q]);
         }
+    }
+    if (!bgrow) {
         const int dyi = l / g.L, dxi = l - dyi * g.L;
-        const double sc = g.nx > 1 ? 1.0 / (double)(g.nx - 1) : 0.0;
-        double sp = 1.0;
         float *o = cf + (((size_t)ys * g.L + dyi) * np) * g.L + dxi;
-        for (int p = 0; p < np; p++, sp *= sc) o[(size_t)p * g.L] = (float)(c[p] * sp);
-    } else if (t < ncf + (size_t)g.ny) {
-        const int y = (int)(t - ncf);
-        const double yh = g.ny > 1 ? (2.0 * y - (g.ny - 1)) / (double)(g.ny - 1) : 0.0;
-        double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-        for (int r = 0; r < g.nb; r++) {
-            int pr, qr;
-            mono_pq(r, pr, qr);
-            double w = 1.0;
-            for (int q = 0; q < qr; q++) w *= yh;
-            acc[pr] = fma(coeffs[g.nker + r], w, acc[pr]);
-        }
-        float *o = cf + ncf * np + (size_t)y * nbp;
-        for (int p = 0; p < nbp; p++) o[p] = (float)acc[p];
+        double sp = 1.0;
+#pragma unroll
+        for (int p = 0; p < 8; p++, sp *= sx)
+            if (p < np) o[(size_t)p * g.L] = (float)(c[p] * sp);
+    } else {
+        float *o = cf + ncf * np + (size_t)ys * nbp;
+#pragma unroll
+        for (int p = 0; p < 8; p++)
+            if (p < nbp) o[p] = (float)c[p];
     }
 }
 
@@ -540,7 +549,8 @@ cudaError_t launch_residual_comp(const Geometry &g, int dtype, const void *sci, 
     {
         const size_t nt = (size_t)g.ny * g.L * g.L + g.ny;
         note_launch();
-        k_fold_x<<<(unsigned)((nt + 255) / 256), 256, 0, st>>>(coeffs, g, (float *)cfold);
+        k_fold_x<<<(unsigned)((nt + 255) / 256), 256, 0, st>>>(
+            coeffs, g, g.ny > 1 ? 1.0 / (g.ny - 1) : 0.0, g.nx > 1 ? 1.0 / (g.nx - 1) : 0.0, (float *)cfold);
         const cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }

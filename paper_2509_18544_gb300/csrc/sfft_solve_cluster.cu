@@ -150,6 +150,12 @@ __global__ void __launch_bounds__(CTH) k_pcg_cluster(FastArgs A) {
     auto remote = [&](int t) { return cl.map_shared_rank(tiles, owner(t)) + (size_t)(t / CL) * TT; };
 
     if (tid == 0) bad = 0;
+    // Jacobi scaling d_i = 1 / sqrt(N_ii), once per row (FP64 square roots and divides run on
+    // the narrow FP64 pipe), visible to the whole cluster before the tiles are loaded
+    if (A.mode == 0) {
+        for (int i = rank * CTH + tid; i < n; i += CL * CTH) A.d[i] = 1.0 / sqrt(A.N[(size_t)i * n + i]);
+        cl.sync();
+    }
     // ---------------------------------------------------------------- load the tiles
     for (int t = rank; t < A.ntiles; t += CL) {
         int bi, bj;
@@ -162,8 +168,7 @@ __global__ void __launch_bounds__(CTH) k_pcg_cluster(FastArgs A) {
             if (A.mode == 1) {
                 val = A.Lg[(size_t)t * TT + rr * TS + cc];
             } else if (gi < n && gj < n) {
-                double di = 1.0 / sqrt(A.N[(size_t)gi * n + gi]), dj = 1.0 / sqrt(A.N[(size_t)gj * n + gj]);
-                val = (float)(A.N[(size_t)gi * n + gj] * di * dj);
+                val = (float)(A.N[(size_t)gi * n + gj] * __ldcg(A.d + gi) * __ldcg(A.d + gj));
             } else {
                 val = (gi == gj) ? 1.0f : 0.0f;  // identity padding past n
             }
@@ -171,9 +176,6 @@ __global__ void __launch_bounds__(CTH) k_pcg_cluster(FastArgs A) {
         }
         if (A.mode == 1 && bi == bj)
             for (int rr = tid; rr < TB; rr += CTH) T[rr * TS + TB] = A.Lg[(size_t)t * TT + rr * TS + TB];
-    }
-    if (A.mode == 0) {
-        for (int i = rank * CTH + tid; i < n; i += CL * CTH) A.d[i] = 1.0 / sqrt(A.N[(size_t)i * n + i]);
     }
     cl.sync();
 

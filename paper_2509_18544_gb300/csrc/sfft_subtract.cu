@@ -22,39 +22,55 @@ __device__ __forceinline__ R coordv(int i, int n) {
 }
 
 // cf[ys][l][p] over l = (dy+h) L + (dx+h): sum_{i: p_i = p} a_{i,l} yh(ys)^q_i, and after
-// the table bg[y][p] = sum_{r: p_r = p} b_r yh(y)^q_r
+// the table bg[y][p] = sum_{r: p_r = p} b_r yh(y)^q_r.  iny = 1 / (ny - 1) (0 when ny = 1),
+// from the host: yh = (2 y - (ny - 1)) iny (no FP64 division per thread).  The monomial
+// loops are unrolled over degree <= 7 so that the sums stay in registers.
 template <class R>
-__global__ void k_fold(const double *__restrict__ coeffs, Geometry g, R *__restrict__ cf) {
+__global__ void k_fold(const double *__restrict__ coeffs, Geometry g, double iny, R *__restrict__ cf) {
     const int L2 = g.L * g.L, np = g.dk + 1, nbp = g.db + 1;
     const size_t ncf = (size_t)g.ny * L2;
     size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t < ncf) {
         const int ys = (int)(t / L2), l = (int)(t - (size_t)ys * L2);
-        const double yh = g.ny > 1 ? (2.0 * ys - (g.ny - 1)) / (double)(g.ny - 1) : 0.0;
-        double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-        for (int i = 0; i < g.nk; i++) {
-            int pi, qi;
-            mono_pq(i, pi, qi);
-            double w = 1.0;
-            for (int q = 0; q < qi; q++) w *= yh;
-            acc[pi] = fma(coeffs[(size_t)i * L2 + l], w, acc[pi]);
+        const double yh = (2.0 * ys - (g.ny - 1)) * iny;
+        double pw[8], acc[8];
+        pw[0] = 1.0;
+#pragma unroll
+        for (int q = 1; q < 8; q++) pw[q] = q <= g.dk ? pw[q - 1] * yh : 0.0;
+#pragma unroll
+        for (int p = 0; p < 8; p++) acc[p] = 0.0;
+        int i = 0;  // monomial index: total degree first, then q ascending
+#pragma unroll
+        for (int d = 0; d < 8; d++) {
+            if (d > g.dk) break;
+#pragma unroll
+            for (int q = 0; q <= d; q++, i++) acc[d - q] = fma(coeffs[(size_t)i * L2 + l], pw[q], acc[d - q]);
         }
         const int dyi = l / g.L, dxi = l - dyi * g.L;
         R *o = cf + (((size_t)ys * g.L + dyi) * np) * g.L + dxi;
-        for (int p = 0; p < np; p++) o[(size_t)p * g.L] = (R)acc[p];
+#pragma unroll
+        for (int p = 0; p < 8; p++)
+            if (p < np) o[(size_t)p * g.L] = (R)acc[p];
     } else if (t < ncf + (size_t)g.ny) {
         const int y = (int)(t - ncf);
-        const double yh = g.ny > 1 ? (2.0 * y - (g.ny - 1)) / (double)(g.ny - 1) : 0.0;
-        double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-        for (int r = 0; r < g.nb; r++) {
-            int pr, qr;
-            mono_pq(r, pr, qr);
-            double w = 1.0;
-            for (int q = 0; q < qr; q++) w *= yh;
-            acc[pr] = fma(coeffs[g.nker + r], w, acc[pr]);
+        const double yh = (2.0 * y - (g.ny - 1)) * iny;
+        double pw[8], acc[8];
+        pw[0] = 1.0;
+#pragma unroll
+        for (int q = 1; q < 8; q++) pw[q] = q <= g.db ? pw[q - 1] * yh : 0.0;
+#pragma unroll
+        for (int p = 0; p < 8; p++) acc[p] = 0.0;
+        int r = 0;
+#pragma unroll
+        for (int d = 0; d < 8; d++) {
+            if (d > g.db) break;
+#pragma unroll
+            for (int q = 0; q <= d; q++, r++) acc[d - q] = fma(coeffs[g.nker + r], pw[q], acc[d - q]);
         }
         R *o = cf + ncf * np + (size_t)y * nbp;
-        for (int p = 0; p < nbp; p++) o[p] = (R)acc[p];
+#pragma unroll
+        for (int p = 0; p < 8; p++)
+            if (p < nbp) o[p] = (R)acc[p];
     }
 }
 
@@ -458,7 +474,8 @@ cudaError_t run(const Geometry &g, const void *sci, const void *tmpl, const uint
     {
         size_t nt = (size_t)g.ny * LL * LL + g.ny;
         note_launch();
-        k_fold<R><<<(unsigned)((nt + 255) / 256), 256, 0, st>>>(coeffs, g, (R *)cfold);
+        k_fold<R><<<(unsigned)((nt + 255) / 256), 256, 0, st>>>(coeffs, g, g.ny > 1 ? 1.0 / (g.ny - 1) : 0.0,
+                                                                 (R *)cfold);
     }
     const int np = g.dk + 1;
     const size_t sm = Layout<R, In, LL>::bytes(np, g.db);
