@@ -437,24 +437,74 @@ __device__ __forceinline__ void c2dft8(C2 (&v)[8], const float4 *tw3) {
     v[7] = c2sub(e3, o3);
 }
 
+// v (wr + i wi) with wr = rh + rl and wi = ih + il given as FP32 splits (compile-time
+// constants), in the operation order of c2tw (small terms first)
+__device__ __forceinline__ C2 c2mulk(C2 v, float rh, float rl, float ih, float il) {
+    const float2 whr = make_float2(rh, rh), nwhi = make_float2(-ih, -ih), whi = make_float2(ih, ih);
+    const float2 wlr = make_float2(rl, rl), nwli = make_float2(-il, -il), wli = make_float2(il, il);
+    float2 re = __fmul2_rn(v.im, nwli);
+    re = __ffma2_rn(v.re, wlr, re);
+    re = __ffma2_rn(v.im, nwhi, re);
+    re = __ffma2_rn(v.re, whr, re);
+    float2 im = __fmul2_rn(v.im, wlr);
+    im = __ffma2_rn(v.re, wli, im);
+    im = __ffma2_rn(v.im, whr, im);
+    im = __ffma2_rn(v.re, whi, im);
+    return {re, im};
+}
+
+// v W16^TT, W16 = exp(-2 pi i / 16), from the split constants cos(pi/8), sin(pi/8) and
+// 1/sqrt(2) (each the FP32 value and its remainder, to about 2^-48)
+template <int TT>
+__device__ __forceinline__ C2 c2w16(C2 v) {
+    const float ch = __int_as_float(0x3F6C835E), cl = __int_as_float(0x32F328D4);  // cos(pi/8)
+    const float sh = __int_as_float(0x3EC3EF15), sl = __int_as_float(0x31D5D52C);  // sin(pi/8)
+    const float rh = __int_as_float(0x3F3504F3), rl = __int_as_float(0x324FE77A);  // 1/sqrt(2)
+    if constexpr (TT == 0) return v;
+    else if constexpr (TT == 1) return c2mulk(v, ch, cl, -sh, -sl);
+    else if constexpr (TT == 2) return c2mulk(v, rh, rl, -rh, -rl);
+    else if constexpr (TT == 3) return c2mulk(v, sh, sl, -ch, -cl);
+    else if constexpr (TT == 4) return {v.im, make_float2(-v.re.x, -v.re.y)};  // -i v
+    else if constexpr (TT == 5) return c2mulk(v, -sh, -sl, -ch, -cl);
+    else if constexpr (TT == 6) return c2mulk(v, -rh, -rl, -rh, -rl);
+    else return c2mulk(v, -ch, -cl, -sh, -sl);
+}
+
+template <int TT>
+__device__ __forceinline__ void c2stage2(C2 (&v)[8], const float4 *e, int k1, bool half, float2 sg) {
+    const float4 a = e[k1 * 17 + TT], b = e[k1 * 17 + TT + 8];
+    const C2 d = {__ffma2_rn(make_float2(b.x, b.y), sg, make_float2(a.x, a.y)),
+                  __ffma2_rn(make_float2(b.z, b.w), sg, make_float2(a.z, a.w))};
+    if constexpr (TT == 0) {
+        v[0] = d;
+    } else {
+        const C2 w = c2w16<TT>(d);
+        v[TT] = {half ? w.re : d.re, half ? w.im : d.im};
+    }
+}
+
 // 128-point forward DFT of two columns by the 16 lanes of a half-warp (the decomposition of
-// fft128); e: 8 x 17 float4 exchange slots (re pair, im pair)
+// fft128); e: 8 x 17 float4 exchange slots (re pair, im pair).  tw3: the first stage's
+// twiddles W128^(t k1) as [k1 - 1][t] entries of three float4 (consecutive lanes read
+// consecutive entries: no bank conflicts); the second stage's W16^tt are constants.
 __device__ __forceinline__ void c2fft128(C2 (&v)[8], int t, float4 *e, const float4 *tw3, unsigned msk) {
     c2dft8(v, tw3);
 #pragma unroll
-    for (int k1 = 1; k1 < 8; k1++) v[k1] = c2tw(v[k1], tw3 + 3 * (t * k1));
+    for (int k1 = 1; k1 < 8; k1++) v[k1] = c2tw(v[k1], tw3 + 3 * ((k1 - 1) * 16 + t));
 #pragma unroll
     for (int k1 = 0; k1 < 8; k1++) e[k1 * 17 + t] = make_float4(v[k1].re.x, v[k1].re.y, v[k1].im.x, v[k1].im.y);
     __syncwarp(msk);
-    const int k1 = t & 7, half = t >> 3;
+    const int k1 = t & 7;
+    const bool half = t >> 3;
     const float2 sg = half ? make_float2(-1.f, -1.f) : make_float2(1.f, 1.f);
-#pragma unroll
-    for (int tt = 0; tt < 8; tt++) {
-        const float4 a = e[k1 * 17 + tt], b = e[k1 * 17 + tt + 8];
-        C2 d = {__ffma2_rn(make_float2(b.x, b.y), sg, make_float2(a.x, a.y)),
-                __ffma2_rn(make_float2(b.z, b.w), sg, make_float2(a.z, a.w))};
-        v[tt] = c2tw(d, tw3 + 3 * (half ? 8 * tt : 0));
-    }
+    c2stage2<0>(v, e, k1, half, sg);
+    c2stage2<1>(v, e, k1, half, sg);
+    c2stage2<2>(v, e, k1, half, sg);
+    c2stage2<3>(v, e, k1, half, sg);
+    c2stage2<4>(v, e, k1, half, sg);
+    c2stage2<5>(v, e, k1, half, sg);
+    c2stage2<6>(v, e, k1, half, sg);
+    c2stage2<7>(v, e, k1, half, sg);
     __syncwarp(msk);
     c2dft8(v, tw3);
 }
@@ -492,7 +542,7 @@ struct Smem32 {
     using B = Basis<DK, DB>;
     static constexpr int ncolp = (B::ncol + 1) & ~1;  // columns rounded to whole pairs
     static constexpr int nbuf = 2 * NPS;
-    // tw3 [Py][3] float4, stg [NPS][2][Py][nrec] float2, yq [NPS][2][qmax][Py],
+    // tw3 [7][16][3] float4 (room for [Py][3]), stg [NPS][2][Py][nrec] float2, yq [NPS][2][qmax][Py],
     // cols [nbuf][ncolp][Py] float4 (re, re, im, im), column tables [ncol][3] int
     static constexpr size_t tw3 = 0;
     static constexpr size_t stg = tw3 + 16 * 3 * kPy;
@@ -616,11 +666,12 @@ __global__ void __launch_bounds__(Roles<DK, DB, NPS>::NT, 1)
     const int G = g.G, ny = g.ny, nkf = g.nkf, Uy = g.Uy, nyb = g.nyb;
     float4 *share = out + ((size_t)split * nkf + k) * B::npair_all * kPy;
 
-    for (int m = tid; m < kPy; m += NT) {
-        const float2 h = tw_g[m], l = tw_g[kPy + m];  // exp(-2 pi i m / Py): high part, remainder
-        tw3[3 * m] = make_float4(h.x, h.x, -h.y, -h.y);
-        tw3[3 * m + 1] = make_float4(h.y, h.y, l.x, l.x);
-        tw3[3 * m + 2] = make_float4(-l.y, -l.y, l.y, l.y);
+    for (int i = tid; i < 7 * 16; i += NT) {
+        const int m = (i >> 4) * (i & 15) + (i & 15);  // (k1 - 1, t) -> t k1
+        const float2 h = tw_g[m], l = tw_g[kPy + m];   // exp(-2 pi i m / Py): high part, remainder
+        tw3[3 * i] = make_float4(h.x, h.x, -h.y, -h.y);
+        tw3[3 * i + 1] = make_float4(h.y, h.y, l.x, l.x);
+        tw3[3 * i + 2] = make_float4(-l.y, -l.y, l.y, l.y);
     }
     for (int c = tid; c < B::ncol; c += NT) {
         int st = 0, q = 0, a = 0, p = 0;
