@@ -78,5 +78,79 @@ __device__ __forceinline__ void fft256(cpx<R> (&v)[16], int t, cpx<R> *e, const 
     __syncwarp(msk);
 }
 
+// ---------------------------------------------------------------- FP32 form
+// The same transform with the 16-point DFTs' twiddles W16^m as split constants (no shared
+// loads) and the middle twiddles from a table laid out per (k1, lane):
+//   tw4[(k1 - 1) 16 + t] = (wh.re, wh.im, wl.re, wl.im) of W256^(t k1),  k1 = 1..15,
+// so the 16 lanes read 16 consecutive entries (no bank conflicts) with one 16-byte load.
+constexpr int kTw4 = 15 * 16;  // entries of tw4
+
+// tw4 from the split table tw_g (tw_g[m] = high part of exp(-2 pi i m / 256), tw_g[256 + m]
+// its remainder), by the threads of a CTA (the caller synchronises)
+__device__ __forceinline__ void fill_tw4(float4 *tw4, const float2 *__restrict__ tw_g) {
+    for (int i = threadIdx.x; i < kTw4; i += blockDim.x) {
+        const int m = ((i >> 4) + 1) * (i & 15);
+        const float2 h = tw_g[m], l = tw_g[kP + m];
+        tw4[i] = make_float4(h.x, h.y, l.x, l.y);
+    }
+}
+
+// v W16^m for a compile-time m (after unrolling), W16 = exp(-2 pi i / 16); the constants are
+// cos(pi/8), sin(pi/8) and 1/sqrt(2), each as its FP32 value and remainder (to about 2^-48)
+__device__ __forceinline__ cpx<float> w16f(cpx<float> v, int m) {
+    const float ch = __int_as_float(0x3F6C835E), cl = __int_as_float(0x32F328D4);  // cos(pi/8)
+    const float sh = __int_as_float(0x3EC3EF15), sl = __int_as_float(0x31D5D52C);  // sin(pi/8)
+    const float rh = __int_as_float(0x3F3504F3), rl = __int_as_float(0x324FE77A);  // 1/sqrt(2)
+    switch (m & 15) {
+        case 0: return v;
+        case 1: return twmul(v, {ch, -sh}, {cl, -sl});
+        case 2: return twmul(v, {rh, -rh}, {rl, -rl});
+        case 3: return twmul(v, {sh, -ch}, {sl, -cl});
+        case 4: return {v.im, -v.re};  // -i v
+        case 6: return twmul(v, {-rh, -rh}, {-rl, -rl});
+        case 9: return twmul(v, {-ch, sh}, {-cl, sl});
+        default: return twmul(v, {0.f, 0.f}, {0.f, 0.f});  // not reached (m = j1 k1, j1, k1 <= 3)
+    }
+}
+
+__device__ __forceinline__ void dft16f(cpx<float> (&v)[16]) {
+#pragma unroll
+    for (int j1 = 0; j1 < 4; j1++) dft4(v[j1], v[j1 + 4], v[j1 + 8], v[j1 + 12]);
+#pragma unroll
+    for (int j1 = 1; j1 < 4; j1++)
+#pragma unroll
+        for (int k1 = 1; k1 < 4; k1++) v[j1 + 4 * k1] = w16f(v[j1 + 4 * k1], j1 * k1);
+    cpx<float> t[16];
+#pragma unroll
+    for (int k1 = 0; k1 < 4; k1++) {
+        cpx<float> a0 = v[0 + 4 * k1], a1 = v[1 + 4 * k1], a2 = v[2 + 4 * k1], a3 = v[3 + 4 * k1];
+        dft4(a0, a1, a2, a3);
+        t[k1 + 0] = a0;
+        t[k1 + 4] = a1;
+        t[k1 + 8] = a2;
+        t[k1 + 12] = a3;
+    }
+#pragma unroll
+    for (int k = 0; k < 16; k++) v[k] = t[k];
+}
+
+// fft256 for FP32 with the tw4 table (same input and output order)
+__device__ __forceinline__ void fft256f(cpx<float> (&v)[16], int t, cpx<float> *e, const float4 *tw4,
+                                        unsigned msk) {
+    dft16f(v);
+#pragma unroll
+    for (int k1 = 1; k1 < 16; k1++) {
+        const float4 w = tw4[(k1 - 1) * 16 + t];
+        v[k1] = twmul(v[k1], {w.x, w.y}, {w.z, w.w});
+    }
+#pragma unroll
+    for (int k1 = 0; k1 < 16; k1++) e[k1 * 17 + t] = v[k1];
+    __syncwarp(msk);
+#pragma unroll
+    for (int tt = 0; tt < 16; tt++) v[tt] = e[t * 17 + tt];
+    dft16f(v);
+    __syncwarp(msk);
+}
+
 }  // namespace
 }  // namespace sfft

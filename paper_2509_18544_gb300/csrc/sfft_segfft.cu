@@ -12,6 +12,8 @@
 // (SFFT subtraction step, Sec. "Pipeline steps", step 6).
 #include <algorithm>
 
+#include <type_traits>
+
 #include "sfft_fft256.cuh"
 
 namespace sfft {
@@ -88,9 +90,13 @@ __global__ void __launch_bounds__(MAXT, MINB) k_segment_fft(const In *__restrict
     int *oq = ob + NI;                                  // [nrec] y power of each output image
     int *wcol = oq + NI;                                // [P] frame column of each window column
 
+    constexpr bool kF32 = std::is_same<R, float>::value;
+    if constexpr (kF32) fill_tw4(reinterpret_cast<float4 *>(tw), reinterpret_cast<const float2 *>(tw_g));
     for (int i = tid; i < kP; i += nthr) {
-        tw[i] = tw_g[i];
-        twl[i] = tw_g[kP + i];
+        if constexpr (!kF32) {
+            tw[i] = tw_g[i];
+            twl[i] = tw_g[kP + i];
+        }
         // coordinate powers come from FP64 tables rounded once: repeated FP32 products
         // are biased (~-3e-8 at power 4)
         int xw = wrapi(x0 - G + i, nx);
@@ -213,7 +219,8 @@ __global__ void __launch_bounds__(MAXT, MINB) k_segment_fft(const In *__restrict
                 v[jj] = {val[0], val[1]};
             }
             cpx<R> *e = ex + (r_fft * nbfft + f) * kEx;
-            fft256(v, t, e, tw, twl, msk);
+            if constexpr (kF32) fft256f(v, t, e, reinterpret_cast<const float4 *>(tw), msk);
+            else fft256(v, t, e, tw, twl, msk);
 #pragma unroll
             for (int k2 = 0; k2 < 16; k2++) e[t + 16 * k2] = v[k2];  // natural order Z[k]
         }
@@ -278,13 +285,21 @@ template <class R, class In>
 __global__ void __launch_bounds__(128) k_segment_fft_single(const In *__restrict__ img, Geometry g,
                                                            const cpx<R> *__restrict__ tw_g, int slot,
                                                            cpx<R> *__restrict__ spec, cpx<R> *__restrict__ rspec) {
-    __shared__ cpx<R> tw[kP], twl[kP];
+    // split twiddles: tw, twl (FP64), or the FP32 form's tw4 table in the same bytes
+    __shared__ __align__(16) unsigned char twraw[2 * kP * sizeof(cpx<R>)];
+    cpx<R> *tw = reinterpret_cast<cpx<R> *>(twraw), *twl = tw + kP;
+    constexpr bool kF32 = std::is_same<R, float>::value;
+    static_assert(!kF32 || kTw4 * sizeof(float4) <= sizeof(twraw), "tw4 fits the twiddle bytes");
     __shared__ cpx<R> ex[8][kEx];
     const int G = g.G, nx = g.nx, ny = g.ny, NI = g.nrec, nkf = g.nkf;
     const int s = blockIdx.x, x0 = s * g.U;
-    for (int i = threadIdx.x; i < kP; i += blockDim.x) {
-        tw[i] = tw_g[i];
-        twl[i] = tw_g[kP + i];
+    if constexpr (kF32) {
+        fill_tw4(reinterpret_cast<float4 *>(twraw), reinterpret_cast<const float2 *>(tw_g));
+    } else {
+        for (int i = threadIdx.x; i < kP; i += blockDim.x) {
+            tw[i] = tw_g[i];
+            twl[i] = tw_g[kP + i];
+        }
     }
     __syncthreads();
     const int f = threadIdx.x >> 4, t = threadIdx.x & 15;  // 8 FFTs of row pairs
@@ -300,7 +315,8 @@ __global__ void __launch_bounds__(128) k_segment_fft_single(const In *__restrict
         v[jj] = {a, b};
     }
     cpx<R> *e = ex[f];
-    fft256(v, t, e, tw, twl, msk);
+    if constexpr (kF32) fft256f(v, t, e, reinterpret_cast<const float4 *>(twraw), msk);
+    else fft256(v, t, e, tw, twl, msk);
 #pragma unroll
     for (int k2 = 0; k2 < 16; k2++) e[t + 16 * k2] = v[k2];
     __syncwarp(msk);

@@ -29,14 +29,11 @@ constexpr int kMaxDBF = 4;  // background degree of the FFT route
 // Khat[(pq L + a) 128 + slot]: the 256-point DFTs of the stamp rows, 1/256 included
 __global__ void __launch_bounds__(256) k_kspec(const double *__restrict__ theta, const float2 *__restrict__ tw_g,
                                                int L, int nk, float2 *__restrict__ kspec) {
-    __shared__ cpx<float> tw[kP], twl[kP];
+    __shared__ float4 tw4[kTw4];
     __shared__ cpx<float> ex[16][kXEx];
     const int t = threadIdx.x, hw = t >> 4, lt = t & 15;
     const unsigned msk = (hw & 1) ? 0xffff0000u : 0x0000ffffu;
-    for (int m = t; m < kP; m += 256) {
-        tw[m] = {tw_g[m].x, tw_g[m].y};
-        twl[m] = {tw_g[kP + m].x, tw_g[kP + m].y};
-    }
+    fill_tw4(tw4, tw_g);
     __syncthreads();
     const int rows = nk * L;  // stamp rows, pq-major
     for (int pr = blockIdx.x * 16 + hw; 2 * pr < rows; pr += gridDim.x * 16) {
@@ -48,7 +45,7 @@ __global__ void __launch_bounds__(256) k_kspec(const double *__restrict__ theta,
             v[jj].re = m < L ? (float)theta[(size_t)r1 * L + m] : 0.f;
             v[jj].im = (m < L && r2 < rows) ? (float)theta[(size_t)r2 * L + m] : 0.f;
         }
-        fft256(v, lt, ex[hw], tw, twl, msk);
+        fft256f(v, lt, ex[hw], tw4, msk);
         unpack_pair(v, lt, ex[hw], kspec + (size_t)r1 * 128, r2 < rows ? kspec + (size_t)r2 * 128 : nullptr,
                     1.f / kP, msk);
     }
@@ -122,7 +119,7 @@ __global__ void __launch_bounds__(kSThreads, 1)
                    const float *__restrict__ ypow, In *__restrict__ diff) {
     using F = SF<H, NP>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    cpx<float> *tw = reinterpret_cast<cpx<float> *>(smem_raw + F::tw), *twl = tw + kP;
+    cpx<float> *tw = reinterpret_cast<cpx<float> *>(smem_raw + F::tw);
     float2 *spec = reinterpret_cast<float2 *>(smem_raw + F::spec);
     float *yq = reinterpret_cast<float *>(smem_raw + F::yq);
     float *bgc = reinterpret_cast<float *>(smem_raw + F::bgc);
@@ -131,10 +128,8 @@ __global__ void __launch_bounds__(kSThreads, 1)
     const int x0 = blockIdx.x * F::U, t = threadIdx.x, hw = t >> 4, lt = t & 15;
     const unsigned msk = (hw & 1) ? 0xffff0000u : 0x0000ffffu;
     cpx<float> *e = reinterpret_cast<cpx<float> *>(smem_raw + F::ex) + hw * kXEx;
-    for (int m = t; m < kP; m += kSThreads) {
-        tw[m] = {tw_g[m].x, tw_g[m].y};
-        twl[m] = {tw_g[kP + m].x, tw_g[kP + m].y};
-    }
+    float4 *tw4 = reinterpret_cast<float4 *>(tw);  // the FP32 FFT's table, in the tw / twl bytes
+    fill_tw4(tw4, tw_g);
     if (t < nb) bgc[t] = (float)theta[(size_t)F::NK * F::L * F::L + t];
     const int slot = t >> 1, jh = 16 * (t & 1);
     const bool packed = slot == 0;
@@ -190,7 +185,7 @@ __global__ void __launch_bounds__(kSThreads, 1)
 #pragma unroll
             for (int jj = 0; jj < 16; jj++) v[jj] = vn[jj];
             if (pr + 16 < NITEMS) load_item(pr + 16, vn);
-            fft256(v, lt, e, tw, twl, msk);
+            fft256f(v, lt, e, tw4, msk);
             const int p = pr / (F::NIN / 2), r1 = 2 * (pr - p * (F::NIN / 2));
             float2 *sp = spec + (size_t)p * F::NIN * 128;
             unpack_pair(v, lt, e, sp + r1 * 128, sp + (r1 + 1) * 128, 1.f, msk);
@@ -216,7 +211,7 @@ __global__ void __launch_bounds__(kSThreads, 1)
                 const float2 a = half_bin(Y1, n), b = half_bin(Y2, n);
                 v[jj] = {a.x - b.y, -(a.y + b.x)};
             }
-            fft256(v, lt, e, tw, twl, msk);
+            fft256f(v, lt, e, tw4, msk);
 #pragma unroll
             for (int k2 = 0; k2 < 16; k2++) {
                 const int i = lt + 16 * k2 - 2 * H, x = x0 + i;

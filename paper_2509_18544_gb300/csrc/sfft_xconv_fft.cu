@@ -88,7 +88,7 @@ __global__ void __launch_bounds__(kXThreads, XSmem<R>::bytes <= 113 * 1024 ? 2 :
     using F = XF<R>;
     using SM = XSmem<R>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    cpx<float> *tw = reinterpret_cast<cpx<float> *>(smem_raw + SM::tw), *twl = tw + kP;
+    cpx<float> *tw = reinterpret_cast<cpx<float> *>(smem_raw + SM::tw);
     float2 *ptab = reinterpret_cast<float2 *>(smem_raw + SM::ptab);
     float2 *spec = reinterpret_cast<float2 *>(smem_raw + SM::spec);
     const XJobF jb = blockIdx.z ? j1 : j0;
@@ -98,13 +98,15 @@ __global__ void __launch_bounds__(kXThreads, XSmem<R>::bytes <= 113 * 1024 ? 2 :
     const unsigned msk = (hw & 1) ? 0xffff0000u : 0x0000ffffu;
     const bool fft_lane = hw < kXFft;  // half-warps that run FFTs
     cpx<float> *e = reinterpret_cast<cpx<float> *>(smem_raw + SM::ex) + (hw % kXFft) * kXEx;
-    // split twiddles exp(-2 pi i m / 256) = tw[m] + twl[m]
-    for (int m = t; m < kP; m += kXThreads) {
+    // split twiddles exp(-2 pi i m / 256) = wh + wl of the FP32 FFT's per-(k1, lane) table
+    // (tw4 entry i holds m = (i / 16 + 1) (i mod 16)), in the tw / twl bytes
+    float4 *tw4 = reinterpret_cast<float4 *>(tw);
+    for (int i = t; i < kTw4; i += kXThreads) {
+        const int m = ((i >> 4) + 1) * (i & 15);
         double sn, cs;
         sincospi(-2.0 * m / kP, &sn, &cs);
         const float ch = (float)cs, sh = (float)sn;
-        tw[m] = {ch, sh};
-        twl[m] = {(float)(cs - (double)ch), (float)(sn - (double)sh)};
+        tw4[i] = make_float4(ch, sh, (float)(cs - (double)ch), (float)(sn - (double)sh));
     }
     __syncthreads();
     // 1. the stamp rows' spectra, with the inverse transform's 1/256
@@ -117,7 +119,7 @@ __global__ void __launch_bounds__(kXThreads, XSmem<R>::bytes <= 113 * 1024 ? 2 :
             v[jj].re = m < F::K ? jb.psf[a1 * F::K + m] : 0.f;
             v[jj].im = (m < F::K && a2 < F::K) ? jb.psf[a2 * F::K + m] : 0.f;
         }
-        fft256(v, lt, e, tw, twl, msk);
+        fft256f(v, lt, e, tw4, msk);
         unpack_pair(v, lt, e, ptab + a1 * 128, a2 < F::K ? ptab + a2 * 128 : nullptr, 1.f / kP, msk);
     }
     __syncthreads();
@@ -144,7 +146,7 @@ __global__ void __launch_bounds__(kXThreads, XSmem<R>::bytes <= 113 * 1024 ? 2 :
 #pragma unroll
             for (int jj = 0; jj < 16; jj++) v[jj] = vn[jj];
             if (pr + kXFft < NPAIR) load_rows(pr + kXFft, vn);
-            fft256(v, lt, e, tw, twl, msk);
+            fft256f(v, lt, e, tw4, msk);
             const int r1 = 2 * pr, r2 = r1 + 1;
             unpack_pair(v, lt, e, spec + r1 * 128, r2 < F::NIN ? spec + r2 * 128 : nullptr, 1.f, msk);
         }
@@ -170,7 +172,7 @@ __global__ void __launch_bounds__(kXThreads, XSmem<R>::bytes <= 113 * 1024 ? 2 :
                 const float2 a = half_bin(Y1, n), b = half_bin(Y2, n);
                 v[jj] = {a.x - b.y, -(a.y + b.x)};
             }
-            fft256(v, lt, e, tw, twl, msk);
+            fft256f(v, lt, e, tw4, msk);
 #pragma unroll
             for (int k2 = 0; k2 < 16; k2++) {
                 const int i = lt + 16 * k2 - 2 * R;
