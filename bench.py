@@ -372,7 +372,7 @@ def run_ours(args, world, rank, local):
     # DRAM bytes measured by ncu on one 2048^2 launch of each stage's kernel (dram__bytes_read.sum
     # + dram__bytes_write.sum, the profiles/ summaries), scaled by the pixel count; writes still
     # in L2 when a launch ends are not counted there
-    for key, rd, wr in (("segment_fft", 37.885e6, 130.419e6), ("ycorr", 191.347e6, 94.921e6),
+    for key, rd, wr in (("segment_fft", 37.878e6, 130.446e6), ("ycorr", 191.260e6, 94.586e6),
                         ("subtract", 36.672e6, 0.006e6)):
         hbm_stages[key]["traffic"] = round((rd + wr) * px / (2048.0 * 2048.0))
     pair_ms = plain_ms / (args.steps * args.pairs)
@@ -381,10 +381,10 @@ def run_ours(args, world, rank, local):
              "plain_frac": round(340.0 * px / (pair_ms * 1e-3) / 1e9 / hbm, 4),
              "batched_frac": round(340.0 * px / (ms / (args.steps * args.pairs) * 1e-3) / 1e9 / hbm, 4)}
     # the dominant GPU-wide kernel: the y correlation (k_ycorr_fft32); DRAM bytes of one
-    # launch from an ncu capture of this kernel on a 2048^2 pair (191.3 MB read + 94.9 MB
+    # launch from an ncu capture of this kernel on a 2048^2 pair (191.3 MB read + 94.6 MB
     # written), scaled to the frame by its pixel count (its traffic grows in proportion)
     yc = hbm_stages["ycorr"]
-    traffic = (191.347e6 + 94.921e6) * px / (2048.0 * 2048.0)
+    traffic = (191.260e6 + 94.586e6) * px / (2048.0 * 2048.0)
     ycorr_flops = 129 * g_nseg * (-(-NY // 108)) * ((2 * nk + nb + 1) * 2824.0 + (nk * (nk + 1) // 2 + nk * (nb + 1)) * 128 * 8.0)
     fp32_peak = sms * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
     roofline = {"bound": "hbm", "kernel": "k_ycorr_fft32 (y correlation: block FFTs + cross-spectra)",
