@@ -254,9 +254,9 @@ __device__ __forceinline__ void stage_ring(const void *__restrict__ tmpl, bool f
 // With mom_part, the kernel also writes this CTA's part of the residual's background
 // moments sum_u m(u) w_r(u) R(u) (r < nP(DB), in the monomial order): FP32 sums over a
 // thread's pixels of a row, FP64 across rows and warps; mom_part[cta nP(DB) + r].
-// NPM: the x powers the coefficient table holds per tap (np = DK + 1 <= NPM; EX: np == NPM).
-template <int LL, int NPM, bool EX>
-__global__ void __launch_bounds__(kThreadsR, NPM <= 4 ? 4 : 2)
+// NPM = DK + 1: the x powers of each tap's weight.
+template <int LL, int NPM>
+__global__ void __launch_bounds__(kThreadsR, 4)
     k_residual_x(const void *__restrict__ sci, const void *__restrict__ tmpl, bool f64, const uint8_t *__restrict__ mask,
                  Geometry g, int rows_per_chunk, const float *__restrict__ cexp, const float *__restrict__ xpow_g,
                  void *__restrict__ resid, double *__restrict__ mom_part) {
@@ -265,7 +265,7 @@ __global__ void __launch_bounds__(kThreadsR, NPM <= 4 ? 4 : 2)
     constexpr int h = W::h;
     constexpr int kRowBatch = (kBandR * W::WC + kThreadsR - 1) / kThreadsR;  // a band's new rows in one batch
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int np = EX ? NPM : g.dk + 1, nx = g.nx, ny = g.ny, db = g.db;
+    const int np = NPM, nx = g.nx, ny = g.ny, db = g.db;
     float *tpf = reinterpret_cast<float *>(smem_raw);
     const float4 *tp4 = reinterpret_cast<const float4 *>(smem_raw);
     float *cf = reinterpret_cast<float *>(smem_raw + Ly::cf);
@@ -386,8 +386,7 @@ __global__ void __launch_bounds__(kThreadsR, NPM <= 4 ? 4 : 2)
                     float2 m = make_float2(0.f, 0.f);
 #pragma unroll
                     for (int k = NPM - 1; k >= 1; k--) {
-                        if (EX && k == NPM - 1) m = e[k];
-                        else if (EX || k < np) m = __ffma2_rn(m, Zw[j], e[k]);
+                        m = k == NPM - 1 ? e[k] : __ffma2_rn(m, Zw[j], e[k]);
                     }
                     if (core_col && core_row) {
                         // the Z^0 term exactly: product split by FMA, sum by two-sum
@@ -493,10 +492,10 @@ __global__ void __launch_bounds__(kThreadsR, NPM <= 4 ? 4 : 2)
     }
 }
 
-template <int LL, int NPM, bool EX>
+template <int LL, int NPM>
 cudaError_t run_res(const Geometry &g, bool f64, const void *sci, const void *tmpl, const uint8_t *mask,
                     const float *cexp, const float *xpow, void *resid, double *mom_part, double *mom, cudaStream_t st) {
-    auto kern = k_residual_x<LL, NPM, EX>;
+    auto kern = k_residual_x<LL, NPM>;
     const size_t smem = RLayout<LL, NPM>::bytes(g.db);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess)
@@ -527,11 +526,11 @@ cudaError_t run_res_np(const Geometry &g, bool f64, const void *sci, const void 
                        const float *cexp, const float *xpow, void *resid, double *mom_part, double *mom,
                        cudaStream_t st) {
     switch (g.dk) {
-        case 0: return run_res<LL, 1, true>(g, f64, sci, tmpl, mask, cexp, xpow, resid, mom_part, mom, st);
-        case 1: return run_res<LL, 2, true>(g, f64, sci, tmpl, mask, cexp, xpow, resid, mom_part, mom, st);
-        case 2: return run_res<LL, 3, true>(g, f64, sci, tmpl, mask, cexp, xpow, resid, mom_part, mom, st);
-        case 3: return run_res<LL, 4, true>(g, f64, sci, tmpl, mask, cexp, xpow, resid, mom_part, mom, st);
-        default: return run_res<LL, 8, false>(g, f64, sci, tmpl, mask, cexp, xpow, resid, mom_part, mom, st);
+        case 0: return run_res<LL, 1>(g, f64, sci, tmpl, mask, cexp, xpow, resid, mom_part, mom, st);
+        case 1: return run_res<LL, 2>(g, f64, sci, tmpl, mask, cexp, xpow, resid, mom_part, mom, st);
+        case 2: return run_res<LL, 3>(g, f64, sci, tmpl, mask, cexp, xpow, resid, mom_part, mom, st);
+        case 3: return run_res<LL, 4>(g, f64, sci, tmpl, mask, cexp, xpow, resid, mom_part, mom, st);
+        default: return cudaErrorInvalidValue;  // plans take DK <= 3 (at most 256 work items per frequency)
     }
 }
 
@@ -545,7 +544,7 @@ int residual_ctas_max(const Geometry &g) {
 cudaError_t launch_residual_comp(const Geometry &g, int dtype, const void *sci, const void *tmpl,
                                  const uint8_t *mask, const double *coeffs, const void *xpow, void *cfold,
                                  void *resid, double *mom_part, double *mom, cudaStream_t st) {
-    if (g.dk > 7 || g.db > kMaxDBR) return cudaErrorInvalidValue;
+    if (g.dk > 3 || g.db > kMaxDBR) return cudaErrorInvalidValue;
     {
         const size_t nt = (size_t)g.ny * g.L * g.L + g.ny;
         note_launch();
