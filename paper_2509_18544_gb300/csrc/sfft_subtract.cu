@@ -89,15 +89,14 @@ template <class R> struct Tile {
 // 16-byte vectors, and a 4-word pad after every 32 words puts the 8 lanes of a quarter-warp
 // (starting 8 words apart) on distinct banks.  FP64: one pad word every 4 doubles puts the
 // 16 lanes of a half-warp on distinct bank pairs.
-// (VEC = false: FP32 windows read as scalars, one pad word every 8 floats.)
-template <class R, bool VEC = true>
+template <class R>
 __host__ __device__ constexpr int skew(int c) {
-    return sizeof(R) == 4 ? (VEC ? c + 4 * (c >> 5) : c + (c >> 3)) : c + (c >> 2);
+    return sizeof(R) == 4 ? c + 4 * (c >> 5) : c + (c >> 2);
 }
-template <class R, int LL, bool VEC = true> struct Win {
+template <class R, int LL> struct Win {
     static constexpr int h = LL / 2;
     static constexpr int WC = Tile<R>::kCols + 2 * h;                                           // window columns
-    static constexpr int WCS = sizeof(R) == 4 ? (VEC ? (WC + 4 * ((WC + 31) / 32) + 3) / 4 * 4 : WC + WC / 8 + 1)
+    static constexpr int WCS = sizeof(R) == 4 ? (WC + 4 * ((WC + 31) / 32) + 3) / 4 * 4
                                               : WC + WC / 4 + 1;                                 // padded row
     static constexpr int RING = kBand + 2 * h;                                                   // ring rows
     static constexpr int NW = Tile<R>::kRX + LL - 1;                                             // register window
@@ -125,10 +124,10 @@ __device__ __forceinline__ int wrapi(int v, int n) {
 //   xps  [npx][WC] R            xh^p of the window columns
 // Output-side rows use the kernel's skewed column index, so that a lane's run of kRX
 // consecutive columns is read without bank conflicts.
-template <class R, class In, int LL, bool VEC = true> struct Layout {
-    using W = Win<R, LL, VEC>;
+template <class R, class In, int LL> struct Layout {
+    using W = Win<R, LL>;
     static constexpr int kC = Tile<R>::kCols;
-    static constexpr int OC = (skew<R, VEC>(kC - 1) + 4) & ~3;
+    static constexpr int OC = (skew<R>(kC - 1) + 4) & ~3;
     __host__ __device__ static constexpr size_t al(size_t b) { return (b + 15) & ~(size_t)15; }
     __host__ __device__ static constexpr size_t cf(int np) { return al(sizeof(R) * (size_t)W::planes(np)); }
     __host__ __device__ static constexpr size_t xo(int np) {
@@ -181,25 +180,25 @@ __device__ __forceinline__ void split_input<float>(float v, float &hi, float &lo
 }
 
 // xh^p of the strip's output columns, p <= db: xo[p][skew(c)]
-template <class R, int LL, bool VEC>
+template <class R, int LL>
 __device__ __forceinline__ void fill_xo(const Geometry &g, const R *__restrict__ xpow_g, int x0, R *xo) {
-    using Ly = Layout<R, R, LL, VEC>;
+    using Ly = Layout<R, R, LL>;
     for (int e = threadIdx.x; e < (g.db + 1) * Ly::kC; e += blockDim.x) {
         const int p = e / Ly::kC, c = e % Ly::kC;
-        xo[p * Ly::OC + skew<R, VEC>(c)] = xpow_g[(size_t)p * g.nx + min(x0 + c, g.nx - 1)];
+        xo[p * Ly::OC + skew<R>(c)] = xpow_g[(size_t)p * g.nx + min(x0 + c, g.nx - 1)];
     }
 }
 
 // Science values of output rows yb .. yb + kBand - 1 (rows before yc1, columns inside the
 // frame), copied asynchronously: ss[r][skew(c)].
-template <class R, class In, int LL, bool VEC>
+template <class R, class In, int LL>
 __device__ __forceinline__ void async_sci(const In *__restrict__ sci, const Geometry &g, int x0, int yb, int yc1,
                                           In *ss) {
-    using Ly = Layout<R, In, LL, VEC>;
+    using Ly = Layout<R, In, LL>;
     constexpr int total = kBand * Ly::kC;
     for (int e = threadIdx.x; e < total; e += blockDim.x) {
         const int r = e / Ly::kC, c = e % Ly::kC, y = yb + r, x = x0 + c;
-        if (y < yc1 && x < g.nx) cp_async_elem(ss + r * Ly::OC + skew<R, VEC>(c), sci + (size_t)y * g.pitch + x);
+        if (y < yc1 && x < g.nx) cp_async_elem(ss + r * Ly::OC + skew<R>(c), sci + (size_t)y * g.pitch + x);
     }
 }
 
@@ -234,11 +233,11 @@ __device__ __forceinline__ unsigned long long load_flags(const unsigned char *p)
 // slots, as np planes xh^p T (T_m when `masked`).  Each thread first issues the loads of
 // kBatch elements, then forms and stores their planes, so a band costs a few load
 // latencies rather than one per element.
-template <class R, class In, int LL, bool VEC, int kBatch>
+template <class R, class In, int LL, int kBatch>
 __device__ __forceinline__ void stage_rows(const In *__restrict__ tmpl, const uint8_t *__restrict__ mask, bool masked,
                                            const Geometry &g, const R *xps, int x0, int ys0, int count,
                                            int ring_origin, R *Tp, unsigned char *sk) {
-    using W = Win<R, LL, VEC>;
+    using W = Win<R, LL>;
     constexpr int kC = Tile<R>::kCols;
     const int np = g.dk + 1, nx = g.nx, total = count * W::WC;
     for (int base = 0; base < total; base += kBatch * (int)blockDim.x) {
@@ -265,7 +264,7 @@ __device__ __forceinline__ void stage_rows(const In *__restrict__ tmpl, const ui
         for (int i = 0; i < kBatch; i++) {
             if (col[i] < 0) continue;
             const R t = bad[i] ? (R)0 : (R)tv[i];
-            R *dst = Tp + (size_t)slot[i] * W::WCS + skew<R, VEC>(col[i]);
+            R *dst = Tp + (size_t)slot[i] * W::WCS + skew<R>(col[i]);
             dst[0] = t;
             for (int p = 1; p < np; p++) dst[(size_t)p * W::RING * W::WCS] = t * xps[p * W::WC + col[i]];
             // the row's mask flags at the strip's output columns
@@ -276,13 +275,11 @@ __device__ __forceinline__ void stage_rows(const In *__restrict__ tmpl, const ui
 }
 
 // Folded coefficients c_p(d, y - dy) of output rows yb .. yb + kBand - 1 and their
-// background x-power sums, copied asynchronously.  PAIRED: rows ry and ry + kBand / 2
-// interleaved, so that one 16-byte load gives two lags' (row a, row b) operand pairs:
-// cf[((ry mod kBand/2) LL + dyi) np + p][2 LLP] with element 2 dxi + (ry >= kBand/2).
-template <class R, int LL, bool PAIRED = false>
+// background x-power sums, copied asynchronously: cf[(ry LL + dyi) np + p][LLP].
+template <class R, int LL>
 __device__ __forceinline__ void async_coeffs(const Geometry &g, const R *__restrict__ cfold, int yb, R *cf, R *byp) {
     using W = Win<R, LL>;
-    constexpr int h = LL / 2, kHalf = kBand / 2;
+    constexpr int h = LL / 2;
     const int np = g.dk + 1, ny = g.ny;
     // a warp per (row, dy): the np LL values of one source row and dy are contiguous
     const int nq = np * LL, lane = threadIdx.x & 31;
@@ -292,9 +289,7 @@ __device__ __forceinline__ void async_coeffs(const Geometry &g, const R *__restr
         const R *src = cfold + ((size_t)ys * LL + dyi) * nq;
         for (int q = lane; q < nq; q += 32) {
             const int p = q / LL, dxi = q - p * LL;
-            R *dst = PAIRED ? cf + (((ry % kHalf) * LL + dyi) * np + p) * 2 * W::LLP + 2 * dxi + ry / kHalf
-                            : cf + ((ry * LL + dyi) * np + p) * W::LLP + dxi;
-            cp_async_elem(dst, src + q);
+            cp_async_elem(cf + ((ry * LL + dyi) * np + p) * W::LLP + dxi, src + q);
         }
     }
     const R *bgf = cfold + (size_t)ny * LL * LL * np;
@@ -372,13 +367,13 @@ __global__ void __launch_bounds__(32 * kBand, 2) k_subtract(const In *__restrict
     const int cx = lane * kRX, ob = skew<R>(cx);  // skew(cx + r) = ob + r for r < kRX
 
     fill_xps<R, LL>(g, xpow_g, x0, npx, xps);
-    fill_xo<R, LL, true>(g, xpow_g, x0, xo);
+    fill_xo<R, LL>(g, xpow_g, x0, xo);
     __syncthreads();
     // every global load of a band happens in the staging phase before it: the coefficients
     // and science values as asynchronous copies that complete while the template rows load
     async_coeffs<R, LL>(g, cfold, yc0, cf, byp);
-    async_sci<R, In, LL, true>(sci, g, x0, yc0, yc1, ss);
-    stage_rows<R, In, LL, true, 8>(tmpl, mask, residual, g, xps, x0, yc0 - h, W::RING, ring_origin, Tp, sk);
+    async_sci<R, In, LL>(sci, g, x0, yc0, yc1, ss);
+    stage_rows<R, In, LL, 8>(tmpl, mask, residual, g, xps, x0, yc0 - h, W::RING, ring_origin, Tp, sk);
     cp_async_wait();
     for (int yb = yc0; yb < yc1; yb += kBand) {
         __syncthreads();
@@ -440,8 +435,8 @@ __global__ void __launch_bounds__(32 * kBand, 2) k_subtract(const In *__restrict
         // replace rows yb - h .. yb - h + kBand - 1, which no later band reads
         if (yb + kBand < yc1) {
             async_coeffs<R, LL>(g, cfold, yb + kBand, cf, byp);
-            async_sci<R, In, LL, true>(sci, g, x0, yb + kBand, yc1, ss);
-            stage_rows<R, In, LL, true, kRowBatch>(tmpl, mask, residual, g, xps, x0, yb + kBand + h, kBand,
+            async_sci<R, In, LL>(sci, g, x0, yb + kBand, yc1, ss);
+            stage_rows<R, In, LL, kRowBatch>(tmpl, mask, residual, g, xps, x0, yb + kBand + h, kBand,
                                                    ring_origin, Tp, sk);
             cp_async_wait();
         }
