@@ -62,3 +62,16 @@ def test_workspace_size_follows_the_tuning():
     sfft.sfft_tuning_set(d, _t(split=8))
     big = sfft.sfft_workspace_size(d)
     assert small <= base <= big and small < big
+
+
+def test_descriptor_limits():
+    """The kernel instantiations cover DK <= 3, DB <= 4 and odd L <= 15 (the streaming
+    residual and difference kernels, the y-correlation roles); the host rejects the rest
+    before any GPU work: DK = 4 needs more than 256 work items per frequency."""
+    for ny, nx, L, dk, db in ((64, 64, 1, 0, 0), (300, 280, 15, 3, 2), (128, 200, 5, 1, 4), (4088, 4088, 11, 2, 2)):
+        assert sfft.sfft_workspace_size(sfft.make_desc(ny, nx, L, dk, db)) > 0
+    for L, dk, db, what in ((11, 4, 0, "work items"), (11, 2, 5, "db=5"), (12, 2, 2, ""), (17, 1, 1, ""),
+                            (11, -1, 0, "")):
+        with pytest.raises(sfft.SfftError) as ei:
+            sfft.sfft_workspace_size(sfft.make_desc(256, 256, L, dk, db))
+        assert ei.value.status == sfft.ERR_INVALID_ARG and what in str(ei.value)
