@@ -19,6 +19,24 @@ __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
     e = (a - (s - bb)) + (b - bb);
 }
 
+// (ah + al)(bh + bl) as an unevaluated float pair (ph + pl), to about u^2: ah bh split
+// exactly by FMA, the cross terms added to its error, then a fast two-sum (|p| >= |e|)
+__device__ __forceinline__ void df_mul(float ah, float al, float bh, float bl, float &ph, float &pl) {
+    const float p = ah * bh;
+    float e = fmaf(ah, bh, -p);
+    e = fmaf(ah, bl, fmaf(al, bh, e));
+    ph = p + e;
+    pl = e - (ph - p);
+}
+
+// (sh, sl) += (ah + al)
+__device__ __forceinline__ void df_add(float &sh, float &sl, float ah, float al) {
+    float s, e;
+    two_sum(sh, ah, s, e);
+    sh = s;
+    sl += e + al;
+}
+
 template <class R>
 __device__ __forceinline__ R coordv(int i, int n) {
     return n > 1 ? (R)(2 * i - (n - 1)) / (R)(n - 1) : (R)0;
@@ -34,7 +52,8 @@ constexpr int kMomCols = 2;
 constexpr int kMomRowBatch = 8;
 template <class R, class In, int DB>
 __global__ void __launch_bounds__(256, 2) k_moments(const In *__restrict__ sci, const uint8_t *__restrict__ mask,
-                                                const R *__restrict__ ypow, Geometry g, double *__restrict__ part) {
+                                                const R *__restrict__ ypow, Geometry g, double inx,
+                                                double *__restrict__ part) {
     constexpr int NB2 = 2 * DB + 1, NB1 = DB + 1;
     __shared__ double red[8][64];
     // yh^b of the chunk's rows, b <= 2 DB (FP64 powers rounded once: the shared table)
@@ -126,9 +145,24 @@ __global__ void __launch_bounds__(256, 2) k_moments(const In *__restrict__ sci, 
             }
         }
     }
+    // x powers of this thread's columns, xh = (2 x - (nx - 1)) inx (inx = 1 / (nx - 1) from the
+    // host): FP64 on the FP64 path; on the FP32 path as double-float pairs, so that the
+    // epilogue runs on the FP32 pipe (GB300 issues FP64 at 1/64 of the FP32 rate) and
+    // converts to FP64 once per warp and moment
     double xh[kMomCols];
+    float pah[kMomCols][NB2], pal[kMomCols][NB2];
 #pragma unroll
-    for (int c = 0; c < kMomCols; c++) xh[c] = colok[c] ? coordv<double>(x0 + c, g.nx) : 0.0;
+    for (int c = 0; c < kMomCols; c++) {
+        const double xd = colok[c] ? (2.0 * (x0 + c) - (g.nx - 1)) * inx : 0.0;
+        xh[c] = xd;
+        if constexpr (sizeof(R) == 4) {
+            const float h = (float)xd, l = (float)(xd - (double)h);
+            pah[c][0] = 1.f;
+            pal[c][0] = 0.f;
+#pragma unroll
+            for (int a = 1; a < NB2; a++) df_mul(pah[c][a - 1], pal[c][a - 1], h, l, pah[c][a], pal[c][a]);
+        }
+    }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     constexpr int nmask = (2 * DB + 1) * (2 * DB + 2) / 2;
     constexpr int nmom = nmask + (DB + 1) * (DB + 2) / 2;
@@ -138,25 +172,55 @@ __global__ void __launch_bounds__(256, 2) k_moments(const In *__restrict__ sci, 
         double v = 0.0;
         if (j < nmask) mono_pq(j, a, b);
         else mono_pq(j - nmask, a, b);
+        if constexpr (sizeof(R) == 4) {
+            float vh = 0.f, vl = 0.f;
 #pragma unroll
-        for (int c = 0; c < kMomCols; c++) {
-            if (!colok[c]) continue;
-            double cs = 0.0;
-            if (j < nmask) {
+            for (int c = 0; c < kMomCols; c++) {
+                if (!colok[c]) continue;
+                float ch = 0.f, cl = 0.f, th = 1.f, tl = 0.f;
+                if (j < nmask) {
 #pragma unroll
-                for (int bb = 0; bb < NB2; bb++)
-                    if (bb == b) cs = (double)cmh[c][bb] + (double)cml[c][bb];
-            } else {
+                    for (int bb = 0; bb < NB2; bb++)
+                        if (bb == b) ch = cmh[c][bb], cl = cml[c][bb];
+                } else {
 #pragma unroll
-                for (int bb = 0; bb < NB1; bb++)
-                    if (bb == b) cs = (double)csh[c][bb] + (double)csl[c][bb];
+                    for (int bb = 0; bb < NB1; bb++)
+                        if (bb == b) ch = csh[c][bb], cl = csl[c][bb];
+                }
+#pragma unroll
+                for (int aa = 0; aa < NB2; aa++)
+                    if (aa == a) th = pah[c][aa], tl = pal[c][aa];
+                float ph, pl;
+                df_mul(th, tl, ch, cl, ph, pl);
+                df_add(vh, vl, ph, pl);
             }
-            double xa = 1.0;
-            for (int e = 0; e < a; e++) xa *= xh[c];
-            v += xa * cs;
-        }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            for (int o = 16; o > 0; o >>= 1) {
+                const float oh = __shfl_xor_sync(0xffffffffu, vh, o), ol = __shfl_xor_sync(0xffffffffu, vl, o);
+                df_add(vh, vl, oh, ol);
+            }
+            v = (double)vh + (double)vl;
+        } else {
+#pragma unroll
+            for (int c = 0; c < kMomCols; c++) {
+                if (!colok[c]) continue;
+                double cs = 0.0;
+                if (j < nmask) {
+#pragma unroll
+                    for (int bb = 0; bb < NB2; bb++)
+                        if (bb == b) cs = (double)cmh[c][bb] + (double)cml[c][bb];
+                } else {
+#pragma unroll
+                    for (int bb = 0; bb < NB1; bb++)
+                        if (bb == b) cs = (double)csh[c][bb] + (double)csl[c][bb];
+                }
+                double xa = 1.0;
+                for (int e = 0; e < a; e++) xa *= xh[c];
+                v += xa * cs;
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        }
         if (lane == 0) red[warp][j & 63] = v;
         if ((j & 63) == 63 || j == nmom - 1) {
             __syncthreads();
@@ -364,13 +428,14 @@ cudaError_t launch_moments_t(const Geometry &g, const void *sci, const uint8_t *
     dim3 grid((g.nx + 256 * kMomCols - 1) / (256 * kMomCols), (g.ny + g.mom_rows - 1) / g.mom_rows);
     const In *s = (const In *)sci;
     const R *yp = (const R *)ypow;
+    const double inx = g.nx > 1 ? 1.0 / (double)(g.nx - 1) : 0.0;
     note_launch();
     switch (g.db) {
-        case 0: k_moments<R, In, 0><<<grid, 256, 0, st>>>(s, mask, yp, g, mom_part); break;
-        case 1: k_moments<R, In, 1><<<grid, 256, 0, st>>>(s, mask, yp, g, mom_part); break;
-        case 2: k_moments<R, In, 2><<<grid, 256, 0, st>>>(s, mask, yp, g, mom_part); break;
-        case 3: k_moments<R, In, 3><<<grid, 256, 0, st>>>(s, mask, yp, g, mom_part); break;
-        case 4: k_moments<R, In, 4><<<grid, 256, 0, st>>>(s, mask, yp, g, mom_part); break;
+        case 0: k_moments<R, In, 0><<<grid, 256, 0, st>>>(s, mask, yp, g, inx, mom_part); break;
+        case 1: k_moments<R, In, 1><<<grid, 256, 0, st>>>(s, mask, yp, g, inx, mom_part); break;
+        case 2: k_moments<R, In, 2><<<grid, 256, 0, st>>>(s, mask, yp, g, inx, mom_part); break;
+        case 3: k_moments<R, In, 3><<<grid, 256, 0, st>>>(s, mask, yp, g, inx, mom_part); break;
+        case 4: k_moments<R, In, 4><<<grid, 256, 0, st>>>(s, mask, yp, g, inx, mom_part); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
