@@ -45,9 +45,10 @@ __device__ __forceinline__ R coordv(int i, int n) {
 constexpr int kMaxDB = 4;
 constexpr int kMaxMomRows = 128;  // rows of one moments CTA (the plan's mom_rows is at most this)
 
-// Column sums over a band of rows, folded into FP64 products with x powers, reduced per CTA.
-// Each thread sums kMomCols adjacent columns; DB is a template parameter so that every loop
-// over the powers unrolls without guards.
+// Column sums over a band of rows, multiplied by x powers and reduced per CTA (FP64 on the
+// FP64 path; double-float FP32 pairs on the FP32 path, converted to FP64 per warp).  Each
+// thread sums kMomCols adjacent columns; DB is a template parameter so that every loop over
+// the powers unrolls without guards.
 constexpr int kMomCols = 2;
 constexpr int kMomRowBatch = 8;
 template <class R, class In, int DB>
